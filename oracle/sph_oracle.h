@@ -1,0 +1,126 @@
+/*
+ * CPU FP64 oracle of the two-fluid spin-SPH time step (test infrastructure).
+ *
+ * This is the slow, obviously-correct reference that the CUDA library is
+ * checked against.  It is used only by the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark; the product path never calls it.  It
+ * shares no code, header or constant with the CUDA library.
+ *
+ * Every pair loop is a plain O(N^2) double loop over j = 0..n-1 in ascending
+ * order; there is no cell list, no blocking and no reordering.
+ *
+ * Species codes: 0 inviscid, 1 viscous, 2 inner wall, 3 outer wall.
+ * Arrays of vectors are xyz-interleaved (3n doubles).
+ *
+ * Parity status: every function below is pinned by tests/test_oracle_pins.py
+ * (kernel normalisation by quadrature, lattice rest density, momentum and
+ * angular-momentum conservation, rigid-rotation zero viscous force, continuum
+ * limit of the viscous/spin terms, energy conservation, brute-force neighbour
+ * sets against a k-d tree, time reversibility of the integrator).  The
+ * interfacial and local-interaction coefficients C_T and C_l follow a reading
+ * of Sec. 2.1 (the paper prints their continuum form only); their sign and
+ * antisymmetry are pinned, their magnitude is a free parameter.
+ */
+#ifndef SPH_ORACLE_H
+#define SPH_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ORC_TERM_P = 1u,       /* Tait pressure gradient                      */
+  ORC_TERM_T = 2u,       /* interfacial (temperature-gradient) force     */
+  ORC_TERM_SH = 4u,      /* central shear viscosity                      */
+  ORC_TERM_ROT = 8u,     /* transverse rotational viscosity with spin    */
+  ORC_TERM_SN = 16u,     /* local interaction force F_sn                 */
+  ORC_HPROJ = 32u,       /* interfacial force acts horizontally only     */
+  ORC_SN_LITERAL = 64u,  /* F_sn on plain v_ij (no spin coupling/torque) */
+  ORC_TERMS_ALL = 31u
+};
+
+typedef struct {
+  double dx, h, rho0;
+  double alpha_P, p0, beta_P;      /* Eq. 4: P = p0 (rho/rho0)^alpha_P - beta_P */
+  double eta_bar, eta_r, xi_bar;   /* shear, rotational, bulk viscosity (Eq. 2) */
+  double C_l;                      /* local interaction coefficient            */
+  double C_T;                      /* signed interfacial coefficient           */
+  double C_omega;                  /* recorded, not applied                    */
+  double mass_ratio;               /* m_s / m_n                                */
+  double inertia_coef;             /* I_i = inertia_coef m_i dx^2              */
+  double Omega, dt;
+  double Hz;                       /* z period                                 */
+  int periodic_z;
+  unsigned flags;
+} orc_params;
+
+typedef struct {
+  double mass, mass_s, mass_n;
+  double mom[3];
+  double L_orb[3], L_spin[3];
+  double E_kin, E_rot, E_int;
+  double T_wall[3];                /* torque of the walls on the fluid now     */
+  double J_wall[3];                /* time integral of T_wall                  */
+  double rho_min, rho_max, v_max;
+  int64_t n_pairs;                 /* ordered neighbour pairs (i != j)         */
+} orc_diag;
+
+/* Wendland C2 kernel W(r) and F(r) = -(1/r) dW/dr, support 2h. */
+double orc_W(const orc_params* p, double r);
+double orc_F(const orc_params* p, double r);
+/* Sum of W(|n| dx) over the integer lattice n in Z^3. */
+double orc_lattice_sum(const orc_params* p);
+/* Particle mass m_n = rho0 / lattice_sum; m_s = mass_ratio m_n; walls m_n. */
+double orc_mass(const orc_params* p, int species);
+
+/* Pair vector r_i - r_j with the minimum image in z when periodic. */
+void orc_pair_delta(const orc_params* p, const double* ri, const double* rj, double d[3]);
+
+/* Brute-force neighbour lists: j != i with r^2 < (2h)^2.  offsets has n+1
+ * entries; nbr receives at most cap indices; returns the total count. */
+int64_t orc_neighbors(const orc_params* p, int64_t n, const double* pos,
+                      int64_t* offsets, int64_t* nbr, int64_t cap);
+
+/* Density (summation, self included) and Tait pressure for the listed rows. */
+void orc_density(const orc_params* p, int64_t n, const double* pos,
+                 const uint8_t* species, const int64_t* rows, int64_t nrows,
+                 double* rho, double* P);
+
+/* Pair forces for the listed rows: acc = f/m, dspin = tau/I; wall_T receives
+ * the torque (orbital about the z axis + spin) exerted by wall neighbours.
+ * term_mag (optional, 5 doubles) accumulates sum_i |f_i^term| per term. */
+void orc_forces(const orc_params* p, int64_t n, const double* pos,
+                const double* vel, const double* spin, const uint8_t* species,
+                const double* rho, const double* P, const int64_t* rows,
+                int64_t nrows, double* acc, double* dspin, double* wall_T,
+                double* term_mag);
+
+/* Place the rigid walls at phase theta from their reference positions. */
+void orc_place_walls(const orc_params* p, int64_t n, const uint8_t* species,
+                     const double* wall_ref, double theta, double* pos,
+                     double* vel, double* spin);
+
+/* Initial evaluation: walls at theta, density, forces (a_0, alpha_0). */
+void orc_init(const orc_params* p, int64_t n, double* pos, double* vel,
+              double* spin, const uint8_t* species, const double* wall_ref,
+              double theta, double* rho, double* P, double* acc, double* dspin,
+              double* T_wall_sum);
+
+/* One kick-drift-kick velocity Verlet step (Algorithm 1 inner body). */
+void orc_step(const orc_params* p, int64_t n, double* pos, double* vel,
+              double* spin, const uint8_t* species, const double* wall_ref,
+              double* theta, double* rho, double* P, double* acc, double* dspin,
+              double* T_wall_sum, double* J_wall);
+
+/* FP64 conservation diagnostics over the fluid particles. */
+void orc_diagnostics(const orc_params* p, int64_t n, const double* pos,
+                     const double* vel, const double* spin,
+                     const uint8_t* species, const double* rho,
+                     const double* T_wall_sum, const double* J_wall,
+                     orc_diag* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

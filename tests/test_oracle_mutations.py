@@ -1,0 +1,51 @@
+"""The oracle pins discriminate: each plants one plausible mistake in a copy of
+the oracle's C source (on the CPU), rebuilds it, and checks that the pin suite
+fails against the broken copy."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
+
+MUTATIONS = {
+    "torque_sign": ("t[0] *= -0.5;", "t[0] *= 0.5;"),
+    "shear_coef_drops_0.6_eta_r": ("double A = 10.0 * (p->eta_bar - 0.6 * p->eta_r);",
+                                   "double A = 10.0 * p->eta_bar;"),
+    "rot_coef_halved": ("double B = 4.0 * p->eta_r;", "double B = 2.0 * p->eta_r;"),
+    "kernel_gradient_constant": ("return 5.0 * alpha_D(p)", "return 4.0 * alpha_D(p)"),
+    "pressure_not_symmetric": ("(Pri + P[j] / (rho[j] * rho[j]))", "(2.0 * Pri)"),
+    "spin_velocity_sign": ("double u[3] = {vij[0] + 0.5 * dxw[0]", "double u[3] = {vij[0] - 0.5 * dxw[0]"),
+    "local_interaction_sign": ("double s = -p->C_l * Vi * Vj * W;", "double s = p->C_l * Vi * Vj * W;"),
+    "interfacial_sign": ("double s = p->C_T * Vi * Vj * F;", "double s = -p->C_T * Vi * Vj * F;"),
+    "density_without_self": ("if (q2 < c2) r +=", "if (q2 < c2 && j != i) r +="),
+    "no_z_minimum_image": ("if (d[2] > half) d[2] -= p->Hz;", "if (d[2] > half) d[2] -= 0;"),
+    "spin_full_kick": ("spin[3 * i + a] += hdt * dspin[3 * i + a];\n    }\n  }\n  for",
+                       "spin[3 * i + a] += p->dt * dspin[3 * i + a];\n    }\n  }\n  for"),
+    "wall_rotation_sign": ("double y = s * x0 + c * y0;", "double y = -s * x0 + c * y0;"),
+    "wall_torque_without_spin": ("Tw[a] += o[a] + t[a];", "Tw[a] += o[a];"),
+    "half_drift": ("pos[3 * i + a] += p->dt * vel[3 * i + a];", "pos[3 * i + a] += 0.5 * p->dt * vel[3 * i + a];"),
+    "unit_vector_index": ("double e[3] = {d[0] / r, d[1] / r, d[2] / r};",
+                          "double e[3] = {d[0] / r, d[2] / r, d[1] / r};"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / "sph_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    hdr = os.path.join(ROOT, "oracle", "sph_oracle.h")
+    (tmp_path / "sph_oracle.h").write_text(open(hdr).read())
+    so = tmp_path / "liborc_mut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", "-o", str(so), str(mutated), "-lm"], check=True)
+    env = dict(os.environ, SPH_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -1,0 +1,436 @@
+"""Pins of the CPU FP64 oracle against what the paper and the mathematics fix.
+
+Each test pins one part of the oracle to something other than itself: a
+quadrature, a finite difference, a k-d tree, a closed-form lattice count, a
+conservation law the paper asserts (Sec. 2.1: total mass M = M_s + M_n; the
+interfacial forces of Eqs. 1-2 act in opposite directions on the two
+components; F_sn acts with its reaction on the other species; rigid rotation
+produces no rotational stress), the continuum limit of Eq. 2, or a property of
+the velocity Verlet integrator (Sec. 2.3).  A plausible slip in the oracle (a
+dropped term, a wrong sign, factor or index) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_03980_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(h_over_dx=1.3, periodic_z=1, Hz=20.0, **kw):
+    p = synth.workload_params(10.0, Hz, 0.1, h_over_dx=h_over_dx)
+    p.update(periodic_z=periodic_z, box_lo=(-50.0, -50.0, 0.0), box_hi=(50.0, 50.0, Hz))
+    p.update(kw)
+    return p
+
+
+def _lattice(n, spacing=1.0):
+    g = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    return (g.astype(np.float64) - (n - 1) / 2.0) * spacing
+
+
+# ---------------------------------------------------------------- kernel (M0)
+
+@pytest.mark.parametrize("h", [0.7, 1.3, 2.1])
+def test_kernel_normalised_by_quadrature(h):
+    from scipy.integrate import quad
+    p = oracle.make_params(_params(h_over_dx=h))
+    val, _ = quad(lambda r: 4.0 * math.pi * r * r * oracle.W(p, r), 0.0, 2.0 * h,
+                  epsabs=1e-14, epsrel=1e-13)
+    assert abs(val - 1.0) < 1e-12
+    assert oracle.W(p, 2.0 * h) == 0.0 and oracle.W(p, 2.0 * h * 1.0001) == 0.0
+
+
+def test_kernel_gradient_matches_finite_difference():
+    p = oracle.make_params(_params())
+    for r in np.linspace(0.05, 2.55, 37):
+        eps = 1e-6
+        dW = (oracle.W(p, r + eps) - oracle.W(p, r - eps)) / (2 * eps)
+        assert oracle.F(p, r) == pytest.approx(-dW / r, rel=1e-7, abs=1e-12)
+        assert oracle.F(p, r) >= 0.0
+
+
+def test_lattice_sum_golden_and_neighbour_count():
+    # Golden: sum_n W(|n| dx) on the unit cubic lattice at h = 1.3 dx, evaluated
+    # independently when the workload was specified (tests/golden/lattice_sum.txt).
+    with open(os.path.join(GOLDEN, "lattice_sum.txt")) as f:
+        golden = float([l for l in f if not l.startswith("#")][0])
+    p = oracle.make_params(_params())
+    assert oracle.lattice_sum(p) == pytest.approx(golden, rel=1e-14)
+    # closed form: integer points with |n|^2 < (2h)^2 = 6.76 -> 1+6+12+8+6+24+24 = 81
+    pos = _lattice(9)
+    off, nbr = oracle.neighbors(oracle.make_params(_params(periodic_z=0)), pos)
+    c = int(np.argmin((pos ** 2).sum(1)))
+    assert off[c + 1] - off[c] == 80
+
+
+def test_rest_density_on_unjittered_lattice():
+    """M1 with the lattice mass: interior particles have rho = rho0 exactly,
+    and the mass of a particle is rho0 / lattice sum (Sec. 2.1 equal volumes)."""
+    p = oracle.make_params(_params(periodic_z=0))
+    pos = _lattice(9)
+    sp = np.ones(len(pos), np.uint8)
+    rho, P = oracle.density(p, pos, sp)
+    interior = np.all(np.abs(pos) <= 1.0 + 1e-9, axis=1)
+    assert np.allclose(rho[interior], 1.0, rtol=0, atol=4e-15)
+    assert np.allclose(P[interior], 0.0, atol=1e-12 * p.p0)
+    # particles on the outer shell see fewer neighbours (no wall): lower density
+    shell = np.abs(pos).max(1) >= 4.0
+    assert rho[shell].max() < 1.0
+    # density with unequal species masses counts the mass of each neighbour
+    p2 = oracle.make_params(_params(periodic_z=0, mass_ratio=5.0))
+    sp2 = np.zeros(len(pos), np.uint8)
+    rho2, _ = oracle.density(p2, pos, sp2)
+    assert rho2[interior] == pytest.approx(5.0 * rho[interior], rel=1e-14)
+
+
+def test_neighbours_match_kdtree_with_periodic_z():
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(7)
+    Hz = 9.0
+    n = 600
+    pos = np.column_stack([rng.uniform(0, 8, n), rng.uniform(0, 8, n), rng.uniform(0, Hz, n)])
+    p = oracle.make_params(_params(Hz=Hz))
+    off, nbr = oracle.neighbors(p, pos)
+    tree = cKDTree(pos + np.array([100.0, 100.0, 0.0]), boxsize=[1000.0, 1000.0, Hz])
+    pairs = tree.query_pairs(2.0 * p.h, output_type="ndarray")
+    want = set(map(tuple, pairs)) | set((b, a) for a, b in pairs)
+    got = set((i, int(j)) for i in range(n) for j in nbr[off[i]:off[i + 1]])
+    assert got == want
+    # a pair exactly at the cutoff distance is not a neighbour (strict r < 2h)
+    two = np.array([[0.0, 0.0, 1.0], [2.0 * p.h, 0.0, 1.0]])
+    o2, _ = oracle.neighbors(p, two)
+    assert o2[-1] == 0
+
+
+def test_z_minimum_image():
+    p = oracle.make_params(_params(Hz=12.0))
+    a = np.array([[0.3, 0.1, 0.4], [0.9, -0.2, 11.5]])    # across z = 0 / H
+    b = a.copy()
+    b[:, 2] = [6.4, 5.5]                                   # same pair, interior
+    sp = np.array([0, 1], np.uint8)
+    ra, Pa = oracle.density(p, a, sp)
+    rb, Pb = oracle.density(p, b, sp)
+    assert np.allclose(ra, rb, rtol=1e-15)
+    v = np.array([[0.1, 0.0, 0.2], [-0.1, 0.3, 0.0]])
+    w = np.array([[0.0, 0.1, 0.0], [0.2, 0.0, -0.1]])
+    fa = oracle.forces(p, a, v, w, sp, ra, Pa)
+    fb = oracle.forces(p, b, v, w, sp, rb, Pb)
+    for x, y in zip(fa[:2], fb[:2]):
+        assert np.allclose(x, y, rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------ EOS (M2)
+
+def test_tait_eos_binomial_form():
+    """Eq. 4 with beta_P = p0 (Sec. 2.1): P(rho0) = 0 and
+    P = p0 * delta (7 + 21 d + 35 d^2 + 35 d^3 + 21 d^4 + 7 d^5 + d^6)."""
+    p = oracle.make_params(_params(periodic_z=0))
+    m = oracle.mass(p, 1)
+    for r in [0.4, 1.0, 1.7, 2.3]:
+        pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        sp = np.array([1, 1], np.uint8)
+        rho, P = oracle.density(p, pos, sp)
+        d = rho[0] / p.rho0 - 1.0
+        binom = p.p0 * d * (7 + d * (21 + d * (35 + d * (35 + d * (21 + d * (7 + d))))))
+        assert P[0] == pytest.approx(binom, rel=1e-10)
+        assert rho[0] == pytest.approx(m * (oracle.W(p, 0.0) + oracle.W(p, r)), rel=1e-15)
+    # outer walls keep the initial density and pressure
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    rho, P = oracle.density(p, pos, np.array([3, 2], np.uint8))
+    assert rho[0] == p.rho0 and P[0] == 0.0 and rho[1] != p.rho0
+
+
+# ------------------------------------------------------ pairwise forces (M3-M8)
+
+def _block(nx=6, ny=6, nz=6, seed=3, f_v=0.4):
+    return synth.periodic_block(nx, ny, nz, seed=seed, f_v=f_v, vel_sigma=0.2)
+
+
+def test_linear_momentum_zero_sum_periodic():
+    pos, vel, spin, sp = _block()
+    p = oracle.make_params(_params(Hz=6.0, C_T=0.3, C_l=0.7), flags=oracle.TERMS_ALL | oracle.HPROJ)
+    rho, P = oracle.density(p, pos, sp)
+    acc, dsp, _ = oracle.forces(p, pos, vel, spin, sp, rho, P)
+    m = np.where(sp == 0, oracle.mass(p, 0), oracle.mass(p, 1))[:, None]
+    tot = (m * acc).sum(0)
+    scale = np.abs(m * acc).sum()
+    assert np.all(np.abs(tot) < 1e-13 * scale)
+
+
+def _angular_residual(flags):
+    pos, vel, spin, sp = _block(seed=11)
+    pos = pos - pos.mean(0)
+    p = oracle.make_params(_params(periodic_z=0, C_T=0.3, C_l=0.7, mass_ratio=2.0), flags=flags)
+    rho, P = oracle.density(p, pos, sp)
+    acc, dsp, _ = oracle.forces(p, pos, vel, spin, sp, rho, P)
+    m = np.where(sp == 0, oracle.mass(p, 0), oracle.mass(p, 1))[:, None]
+    I = p.inertia_coef * m * p.dx ** 2
+    orb = np.cross(pos, m * acc).sum(0)
+    spn = (I * dsp).sum(0)
+    scale = np.abs(np.cross(pos, m * acc)).sum()
+    return orb + spn, scale
+
+
+def test_angular_momentum_orbital_plus_spin_free_cluster():
+    res, scale = _angular_residual(oracle.TERMS_ALL)
+    assert np.all(np.abs(res) < 1e-12 * scale)
+    # the horizontal projection of the interfacial force keeps only L_z
+    res, scale = _angular_residual(oracle.TERMS_ALL | oracle.HPROJ)
+    assert abs(res[2]) < 1e-12 * scale
+    assert np.abs(res[:2]).max() > 1e-6 * scale
+
+
+def test_angular_momentum_constant_over_kdk_steps():
+    pos, vel, spin, sp = _block(5, 5, 5, seed=5)
+    pos = pos - pos.mean(0)
+    prm = _params(periodic_z=0, C_T=0.3, C_l=0.5, dt=0.01)
+    s = oracle.Sim(prm, pos, vel, spin, sp, flags=oracle.TERMS_ALL)
+    d0 = s.diagnostics()
+    L0 = np.add(d0["L_orb"], d0["L_spin"])
+    s.step(60)
+    d1 = s.diagnostics()
+    L1 = np.add(d1["L_orb"], d1["L_spin"])
+    scale = np.abs(d0["L_orb"]).max() + 1.0
+    assert np.all(np.abs(L1 - L0) < 1e-11 * scale)
+    assert np.allclose(d1["mom"], d0["mom"], atol=1e-11)
+    assert d1["mass"] == d0["mass"]
+    assert d0["mass"] == pytest.approx(d0["mass_s"] + d0["mass_n"], rel=1e-15)
+
+
+def test_rigid_rotation_has_no_viscous_or_local_force():
+    """Rigid co-rotation (curl u = 2 w0) gives no rotational stress (Sec. 2.1);
+    the shear, rotational and local-interaction pair terms all vanish."""
+    c = synth.workload("cyl_8960")
+    Om = np.array([0.0, 0.0, 0.37])
+    vel = np.cross(Om, c.pos)
+    spin = np.tile(Om, (c.n, 1))
+    prm = dict(c.params, C_l=2.0)
+    p = oracle.make_params(prm, flags=oracle.TERM_SH | oracle.TERM_ROT | oracle.TERM_SN)
+    rho, P = oracle.density(p, c.pos, c.species)
+    rows = np.arange(0, c.n, 7)
+    acc, dsp, _ = oracle.forces(p, c.pos, vel, spin, c.species, rho, P, rows=rows)
+    # same configuration with the rigid rotation broken gives O(1) forces
+    acc2, dsp2, _ = oracle.forces(p, c.pos, vel, np.zeros_like(spin), c.species, rho, P, rows=rows)
+    ref = np.abs(acc2[rows]).max() + np.abs(dsp2[rows]).max()
+    assert ref > 1e-3
+    assert np.abs(acc[rows]).max() < 1e-12 * ref * 1e3
+    assert np.abs(dsp[rows]).max() < 1e-12 * ref * 1e3
+
+
+@pytest.fixture(scope="module")
+def lattice21():
+    pos = _lattice(21)
+    c = int(np.argmin((pos ** 2).sum(1)))
+    return pos, c
+
+
+def _visc_density(lattice, eta, etar, v, w, flags=oracle.TERM_SH | oracle.TERM_ROT):
+    pos, c = lattice
+    prm = _params(h_over_dx=2.6, periodic_z=0, eta_bar=eta, eta_r=etar)
+    p = oracle.make_params(prm, flags=flags)
+    sp = np.ones(len(pos), np.uint8)
+    rho, P = oracle.density(p, pos, sp)
+    a, b, _ = oracle.forces(p, pos, v, w, sp, rho, P, rows=[c])
+    m = oracle.mass(p, 1)
+    V = m / rho[c]
+    return a[c] * m / V, b[c] * p.inertia_coef * m * p.dx ** 2 / V
+
+
+def test_viscous_terms_reproduce_eq2_continuum(lattice21):
+    """M5 + M6 -> (eta + eta_r) lap v + 2 eta_r curl w for div v = 0, and the
+    spin torque -> 2 eta_r (curl v - 2 w): the third and fifth terms of Eq. 2
+    and the rigid-rotation strain of Sec. 2.1.  Smooth fields on a fine
+    unjittered lattice; the lattice error at h = 2.6 dx is below 0.6 %."""
+    pos, c = lattice21
+    x, y, z = pos.T
+    zero = np.zeros_like(pos)
+    tol = 1.5e-2
+    # shear only and rotational only, v = (y^2, 0, 0): lap v = (2, 0, 0)
+    v = np.column_stack([y * y, 0 * x, 0 * x])
+    for eta, etar in [(1.0, 0.0), (0.0, 1.0), (0.7, 0.3)]:
+        f, _ = _visc_density(lattice21, eta, etar, v, zero)
+        assert f[0] == pytest.approx(2.0 * (eta + etar), rel=tol)
+        assert abs(f[1]) + abs(f[2]) < 1e-10
+    v = np.column_stack([z * z, x * x, y * y])
+    f, _ = _visc_density(lattice21, 1.0, 1.0, v, zero)
+    assert np.allclose(f, 4.0, rtol=tol)
+    # spin gradient: w = (0, 0, x) -> curl w = (0, -1, 0) -> force 2 eta_r (0, -1, 0)
+    w = np.column_stack([0 * x, 0 * x, x])
+    f, tq = _visc_density(lattice21, 1.0, 0.8, zero, w)
+    assert f[1] == pytest.approx(-1.6, rel=tol) and abs(f[0]) + abs(f[2]) < 1e-10
+    # torque: v = s(-y, x, 0), w = (0, 0, w0) -> 2 eta_r (2 s - 2 w0) z
+    s, w0 = 0.3, 0.1
+    v = np.column_stack([-s * y, s * x, 0 * x])
+    w = np.column_stack([0 * x, 0 * x, w0 + 0 * x])
+    f, tq = _visc_density(lattice21, 1.0, 0.8, v, w)
+    assert tq[2] == pytest.approx(2 * 0.8 * (2 * s - 2 * w0), rel=tol)
+    assert np.abs(f).max() < 1e-10
+
+
+def test_dissipative_terms_never_raise_energy():
+    """Shear, rotational and local-interaction terms are dissipative: the
+    kinetic + spin energy decreases monotonically without pressure."""
+    pos, vel, spin, sp = _block(6, 6, 6, seed=9)
+    prm = _params(Hz=6.0, C_l=0.5, dt=0.005, eta_bar=0.3, eta_r=0.2)
+    s = oracle.Sim(prm, pos, vel, spin, sp,
+                   flags=oracle.TERM_SH | oracle.TERM_ROT | oracle.TERM_SN)
+    e = []
+    for _ in range(12):
+        d = s.diagnostics()
+        e.append(d["E_kin"] + d["E_rot"])
+        s.step(1)
+    de = np.diff(e)
+    assert np.all(de < 0.0)
+    assert e[-1] < 0.97 * e[0]
+
+
+def test_pressure_energy_conserved_to_second_order():
+    """Pressure-only WCSPH is Hamiltonian: E_kin + E_int is conserved by the
+    velocity Verlet integrator up to O(dt^2)."""
+    pos, vel, spin, sp = _block(6, 6, 6, seed=4)
+    vel *= 0.05
+
+    def drift(dt, T):
+        prm = _params(Hz=6.0, dt=dt)
+        prm["p0"] = prm["beta_P"] = 2.0
+        s = oracle.Sim(prm, pos, vel, spin, sp, flags=oracle.TERM_P)
+        d = s.diagnostics()
+        e0 = d["E_kin"] + d["E_int"]
+        err = 0.0
+        for _ in range(int(round(T / dt))):
+            s.step(1)
+            d = s.diagnostics()
+            err = max(err, abs(d["E_kin"] + d["E_int"] - e0))
+        return err, e0
+
+    e1, _ = drift(0.04, 1.6)
+    e2, _ = drift(0.02, 1.6)
+    assert 3.0 < e1 / e2 < 5.5
+
+
+def test_interfacial_force_sign_projection_and_reaction():
+    """Eqs. 1-2: +/- rho_s sigma grad T act oppositely on the two components,
+    only in the horizontal plane (Sec. 2.1); C_T > 0 pushes unlike species
+    apart; like species feel nothing."""
+    p = oracle.make_params(_params(periodic_z=0, C_T=1.0), flags=oracle.TERM_T | oracle.HPROJ)
+    pos = np.array([[0.0, 0.0, 0.0], [0.9, 0.4, 0.7]])
+    zero = np.zeros_like(pos)
+    for sp, expect in [([0, 1], True), ([1, 0], True), ([0, 0], False), ([1, 1], False),
+                       ([0, 2], True)]:
+        sp = np.array(sp, np.uint8)
+        rho, P = oracle.density(p, pos, sp)
+        acc, _, _ = oracle.forces(p, pos, zero, zero, sp, rho, P)
+        m = np.where(sp == 0, oracle.mass(p, 0), oracle.mass(p, 1))[:, None]
+        f = m * acc
+        if not expect:
+            assert np.all(f == 0.0)
+            continue
+        d = pos[0] - pos[1]
+        assert f[0, 2] == 0.0
+        assert np.dot(f[0, :2], d[:2]) > 0.0            # repulsive
+        if sp[1] < 2:
+            assert np.allclose(f[0], -f[1], rtol=1e-15)  # reaction
+    # without the projection the force lies along r_ij
+    p.flags = oracle.TERM_T
+    sp = np.array([0, 1], np.uint8)
+    rho, P = oracle.density(p, pos, sp)
+    acc, _, _ = oracle.forces(p, pos, zero, zero, sp, rho, P)
+    assert np.allclose(np.cross(acc[0], pos[0] - pos[1]), 0.0, atol=1e-15)
+
+
+def test_local_interaction_opposes_relative_velocity():
+    """F_sn = C_l v_sn acts between unlike species with its reaction on the
+    other species (Sec. 2.1), decelerating their relative motion."""
+    p = oracle.make_params(_params(periodic_z=0, C_l=1.0),
+                           flags=oracle.TERM_SN | oracle.SN_LITERAL)
+    pos = np.array([[0.0, 0.0, 0.0], [1.1, 0.3, -0.2]])
+    vel = np.array([[0.5, -0.2, 0.1], [-0.1, 0.3, 0.0]])
+    zero = np.zeros_like(pos)
+    sp = np.array([0, 1], np.uint8)
+    rho, P = oracle.density(p, pos, sp)
+    acc, dsp, _ = oracle.forces(p, pos, vel, zero, sp, rho, P)
+    m = oracle.mass(p, 0)
+    f = m * acc
+    vrel = vel[0] - vel[1]
+    assert np.allclose(np.cross(f[0], vrel), 0.0, atol=1e-15) and np.dot(f[0], vrel) < 0
+    assert np.allclose(f[0], -f[1], rtol=1e-15)
+    assert np.all(dsp == 0.0)                              # literal: no torque
+    # ratio at two distances follows the kernel W (local average weight)
+    pos2 = pos.copy()
+    pos2[1] *= 1.4
+    rho2, P2 = oracle.density(p, pos2, sp)
+    acc2, _, _ = oracle.forces(p, pos2, vel, zero, sp, rho2, P2)
+    r1, r2 = np.linalg.norm(pos[1]), np.linalg.norm(pos2[1])
+    ratio = (np.linalg.norm(acc[0]) * rho[0] * rho[1]) / (np.linalg.norm(acc2[0]) * rho2[0] * rho2[1])
+    assert ratio == pytest.approx(oracle.W(p, r1) / oracle.W(p, r2), rel=1e-12)
+    same = np.array([1, 1], np.uint8)
+    acc3, _, _ = oracle.forces(p, pos, vel, zero, same, rho, P)
+    assert np.all(acc3 == 0.0)
+
+
+def test_pressure_sign():
+    """Compressed fluid (rho > rho0, P > 0) pushes outwards; a dilute cluster
+    (P < 0) pulls inwards."""
+    p = oracle.make_params(_params(periodic_z=0), flags=oracle.TERM_P)
+    for spacing, outward in [(0.7, True), (1.6, False)]:
+        pos = _lattice(5, spacing)
+        sp = np.ones(len(pos), np.uint8)
+        rho, P = oracle.density(p, pos, sp)
+        zero = np.zeros_like(pos)
+        acc, _, _ = oracle.forces(p, pos, zero, zero, sp, rho, P)
+        corner = int(np.argmax(pos.sum(1)))
+        radial = np.dot(acc[corner], pos[corner])
+        assert (P[len(pos) // 2] > 0) == outward
+        assert (radial > 0) == outward
+
+
+# ------------------------------------------------------- integrator, walls (M9)
+
+def test_kdk_is_time_reversible():
+    pos, vel, spin, sp = _block(5, 5, 5, seed=2)
+    prm = _params(Hz=5.0, dt=0.02)
+    prm["p0"] = prm["beta_P"] = 1.5
+    s = oracle.Sim(prm, pos, vel * 0.3, spin, sp, flags=oracle.TERM_P | oracle.TERM_T)
+    x0, v0 = s.pos.copy(), s.vel.copy()
+    s.step(25)
+    assert np.abs(s.pos - x0).max() > 1e-2
+    s.vel *= -1.0
+    s.acc *= 1.0
+    s.step(25)
+    dz = s.pos - x0
+    dz[:, 2] -= 5.0 * np.round(dz[:, 2] / 5.0)
+    assert np.abs(dz).max() < 1e-9
+    assert np.abs(s.vel + v0).max() < 1e-9
+
+
+def test_rotating_walls_and_angular_momentum_budget():
+    c = synth.workload("cyl_8960")
+    s = oracle.Sim(c.params, c.pos, c.vel, c.spin, c.species)
+    ref = s.wall_ref.copy()
+    d0 = s.diagnostics()
+    s.step(3)
+    th = 0.0
+    for _ in range(3):
+        th += c.params["Omega"] * c.params["dt"]
+    assert s.theta.value == th
+    w = c.species >= 2
+    ct, st = math.cos(th), math.sin(th)
+    want = np.column_stack([ct * ref[w, 0] - st * ref[w, 1], st * ref[w, 0] + ct * ref[w, 1], ref[w, 2]])
+    assert np.array_equal(s.pos[w], want)
+    assert np.allclose(s.vel[w], np.cross([0, 0, c.params["Omega"]], s.pos[w]), rtol=1e-15)
+    assert np.all(s.rho[c.species == 3] == 1.0) and np.all(s.P[c.species == 3] == 0.0)
+    inner = c.species == 2
+    assert np.all(s.rho[inner] != 1.0)
+    d1 = s.diagnostics()
+    # L_z(t) - L_z(0) equals the torque impulse of the walls (internal pair
+    # forces and spin torques cancel), to round-off
+    dL = (d1["L_orb"][2] + d1["L_spin"][2]) - (d0["L_orb"][2] + d0["L_spin"][2])
+    assert dL == pytest.approx(d1["J_wall"][2], rel=1e-9, abs=1e-9 * abs(d0["L_orb"][2]))
+    assert d1["mass"] == d0["mass"]
+    fl = c.species < 2
+    assert np.all(s.pos[fl, 2] >= 0.0) and np.all(s.pos[fl, 2] < c.H)
