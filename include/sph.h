@@ -1,0 +1,203 @@
+/*
+ * sph.h -- C ABI of the GB300 two-fluid spin-SPH time step.
+ *
+ * One explicit weakly-compressible SPH step of the two-fluid model with spin
+ * angular momentum (Sec. 2.1, Eqs. 1, 2 and 4; Algorithm 1 of Sec. 2.3) for a
+ * vertical cylinder rotating about z (Sec. 3): cell-list neighbour build,
+ * density summation + Tait pressure, one fused pairwise force pass, kick-drift-
+ * kick velocity Verlet, rigid rotating walls.  Several independent cylinders
+ * ("instances") can be advanced together by one set of launches.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns sph_status: 0 = SPH_OK, < 0 an error.  No entry
+ *    point aborts, prints, or calls cudaMalloc / cudaFree.
+ *  - Device memory is owned by the caller: sph_init receives one state buffer
+ *    and one workspace buffer (sizes from sph_state_bytes / sph_workspace_bytes)
+ *    and keeps pointers into them until sph_destroy.  The caller must keep both
+ *    alive and untouched for the context's lifetime.
+ *  - Array arguments may be host or device pointers (cudaPointerGetAttributes
+ *    decides).  Vectors are xyz-interleaved, 3 doubles per particle.
+ *  - Particle order at the interface is the caller's input order (for a batch,
+ *    the concatenation of the instances in order).  Internally particles are
+ *    re-sorted by cell every step.
+ *  - sph_init, sph_build_cells, sph_density, sph_forces and sph_step enqueue
+ *    work on the context's stream and return without synchronising.
+ *    sph_diagnostics, sph_get_state, sph_get_neighbors and sph_check
+ *    synchronise that stream.
+ *  - Errors detected on the device (a particle leaving the grid, a non-finite
+ *    value, a neighbour list overflow) are latched in device memory, never
+ *    trapped; the next synchronising call returns them.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPH_API __attribute__((visibility("default")))
+#else
+#define SPH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_ERR_ARG = -1,          /* invalid argument or parameter                 */
+  SPH_ERR_CUDA = -2,         /* a CUDA runtime call failed                    */
+  SPH_ERR_WORKSPACE = -3,    /* state/workspace buffer too small or misaligned */
+  SPH_ERR_GRID_OVERFLOW = -4,/* cell grid too large for 32-bit cell indices    */
+  SPH_ERR_ESCAPED = -5,      /* a particle left the cell grid (clamped)        */
+  SPH_ERR_NONFINITE = -6,    /* NaN or Inf in the state                        */
+  SPH_ERR_TIMEOUT = -7,      /* a bounded device wait gave up                  */
+  SPH_ERR_STATE = -8,        /* call out of order (e.g. step before init)      */
+  SPH_ERR_NEIGHBORS = -9     /* a neighbour list exceeded nbr_cap (truncated)  */
+} sph_status;
+
+/* Particle species (Sec. 2.1 two components; Sec. 3 wall and dummy particles). */
+typedef enum {
+  SPH_INVISCID = 0,          /* inviscid ("superfluid") component            */
+  SPH_VISCOUS = 1,           /* viscous ("normal fluid") component           */
+  SPH_WALL_INNER = 2,        /* wall layer: density/pressure by summation     */
+  SPH_WALL_OUTER = 3         /* dummy layer: keeps rho0 and P(rho0)           */
+} sph_species;
+
+/* Term switches of the pair pass (all on by default). */
+enum {
+  SPH_TERM_P = 1u,           /* Tait pressure gradient                        */
+  SPH_TERM_T = 2u,           /* interfacial (temperature-gradient) force      */
+  SPH_TERM_SH = 4u,          /* central shear viscosity                       */
+  SPH_TERM_ROT = 8u,         /* transverse rotational viscosity + spin torque  */
+  SPH_TERM_SN = 16u,         /* local interaction force F_sn                  */
+  SPH_HPROJ = 32u,           /* interfacial force horizontal only (Sec. 2.1)  */
+  SPH_SN_LITERAL = 64u,      /* F_sn on plain v_ij: no spin coupling, no torque */
+  SPH_FLAGS_DEFAULT = 63u
+};
+
+enum { SPH_FP64 = 0, SPH_MIXED = 1 };
+
+/* Parameters of one instance, in the paper's variables (dimensionless). */
+typedef struct sph_params {
+  double dx;            /* lattice spacing; particle volume scale            */
+  double h;             /* smoothing length; Wendland C2 support is 2h        */
+  double rho0;          /* Eq. 4 reference density rho_0                      */
+  double alpha_P;       /* Eq. 4 exponent alpha_P; must be an integer 1..16   */
+  double p0;            /* Eq. 4 p_0                                          */
+  double beta_P;        /* Eq. 4 beta_P (= p_0 gives P(rho0) = 0)             */
+  double eta_bar;       /* Eq. 2 shear viscosity                              */
+  double eta_r;         /* Eq. 2 rotational viscosity                         */
+  double xi_bar;        /* Eq. 2 bulk viscosity: its term vanishes (div v = 0) */
+  double C_l;           /* local interaction coefficient, F_sn = C_l v_sn     */
+  double C_T;           /* signed interfacial coefficient, -rho_s sigma dT    */
+  double C_omega;       /* recorded only (Sec. 3); not applied                */
+  double mass_ratio;    /* m_s / m_n                                          */
+  double inertia_coef;  /* spin inertia I = inertia_coef m dx^2               */
+  double Omega;         /* vessel angular velocity about +z                   */
+  double dt;            /* time step                                          */
+  double box_lo[3];     /* cell grid covers [box_lo, box_hi]; z is periodic   */
+  double box_hi[3];     /*   with period box_hi[2] - box_lo[2] if periodic_z  */
+  int32_t periodic_z;   /* 1: periodic top/bottom (slip, Sec. 3); 0: open     */
+  int32_t precision;    /* SPH_FP64 or SPH_MIXED (same for a whole batch)     */
+  uint32_t flags;       /* SPH_TERM_* | SPH_HPROJ | SPH_SN_LITERAL            */
+  int32_t nbr_cap;      /* neighbour slots per particle, 0 = 160 (max 1024)   */
+} sph_params;
+
+/* FP64 conservation diagnostics of one instance (sums over fluid particles). */
+typedef struct sph_diag {
+  double mass, mass_s, mass_n;      /* M = M_s + M_n (Sec. 2.1)             */
+  double mom[3];                    /* linear momentum                        */
+  double L_orb[3], L_spin[3];       /* orbital and spin angular momentum      */
+  double E_kin, E_rot, E_int;       /* kinetic, spin and Tait internal energy */
+  double T_wall[3];                 /* torque of the walls on the fluid now   */
+  double J_wall[3];                 /* trapezoidal time integral of T_wall    */
+  double rho_min, rho_max, v_max;
+  int64_t n_pairs;                  /* ordered neighbour pairs of fluid rows  */
+  int64_t step;                     /* steps taken                            */
+  double theta;                     /* wall phase (FP64, += Omega dt per step) */
+} sph_diag;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Fill *p with the library defaults for a cylinder of radius R, H layers and
+ * rotation Omega (c_s = 10 Omega R, p0 = beta_P = rho0 c_s^2 / 7, Re = 100,
+ * dt = 0.25 h / c_s).  Returns SPH_ERR_ARG for non-positive sizes. */
+SPH_API sph_status sph_params_default(sph_params* p, double R, double H, double Omega);
+
+/* Bytes of the caller-owned device buffers for a batch of n_inst instances
+ * with counts[k] particles each (256-byte aligned base required).  Returns 0
+ * if the parameters are invalid. */
+SPH_API size_t sph_state_bytes(int32_t n_inst, const sph_params* params, const int64_t* counts);
+SPH_API size_t sph_workspace_bytes(int32_t n_inst, const sph_params* params, const int64_t* counts);
+
+/* Create a context for one instance of n particles and evaluate the initial
+ * density and forces (a_0, alpha_0) with the walls at phase 0.
+ * pos/vel/spin: 3n doubles; species: n bytes (sph_species).  Wall particles
+ * are given at their phase-0 positions; their velocity and spin are replaced
+ * by the rigid rotation.  dev_state/dev_workspace: caller-owned device memory
+ * of at least sph_state_bytes / sph_workspace_bytes.  stream: a cudaStream_t
+ * (NULL = legacy default stream).  On error *ctx is NULL. */
+SPH_API sph_status sph_init(sph_ctx** ctx, const sph_params* params, int64_t n,
+                    const double* pos, const double* vel, const double* spin,
+                    const uint8_t* species, void* dev_state, size_t state_bytes,
+                    void* dev_workspace, size_t workspace_bytes, void* stream);
+
+/* Same for n_inst independent instances advanced together; particle arrays
+ * are the concatenation of the instances (counts[k] particles each). */
+SPH_API sph_status sph_init_batch(sph_ctx** ctx, int32_t n_inst, const sph_params* params,
+                          const int64_t* counts, const double* pos, const double* vel,
+                          const double* spin, const uint8_t* species, void* dev_state,
+                          size_t state_bytes, void* dev_workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Neighbour-list build (Algorithm 1, "construct/register NPLs"): cell keys,
+ * counting sort by (cell, particle id), reorder of the state, cell ranges. */
+SPH_API sph_status sph_build_cells(sph_ctx* ctx);
+
+/* Density summation and Tait pressure (Algorithm 1, density/pressure lines;
+ * Eq. 4), which also records each particle's neighbour list. */
+SPH_API sph_status sph_density(sph_ctx* ctx);
+
+/* Pair-force pass (Algorithm 1, pressure-gradient, temperature-gradient,
+ * viscosity and local-interaction lines; Eqs. 1-2) writing the acceleration
+ * and spin angular acceleration of every fluid particle. */
+SPH_API sph_status sph_forces(sph_ctx* ctx);
+
+/* Advance nsteps kick-drift-kick steps (Algorithm 1 inner body), each one
+ * kick+drift, wall rotation, sph_build_cells, sph_density, sph_forces, kick.
+ * The step is replayed from CUDA graphs captured on the first call. */
+SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
+
+/* FP64 diagnostics of instance inst (synchronises). */
+SPH_API sph_status sph_diagnostics(sph_ctx* ctx, int32_t inst, sph_diag* out);
+
+/* Copy the state out in input order (synchronises).  Any pointer may be NULL.
+ * pos, vel, spin, acc, dspin: 3n doubles; rho, P: n doubles. */
+SPH_API sph_status sph_get_state(sph_ctx* ctx, double* pos, double* vel, double* spin,
+                         double* rho, double* P, double* acc, double* dspin);
+
+/* Neighbour lists of the last density pass in input order (synchronises):
+ * offsets[n+1] (host), nbr[cap] (host) receives input indices, ascending
+ * within each particle.  Outer-wall particles have empty lists.  Returns
+ * SPH_ERR_ARG if cap is smaller than the total (offsets still filled). */
+SPH_API sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* offsets, int64_t* nbr, int64_t cap);
+
+/* Synchronise and return the latched device error, if any. */
+SPH_API sph_status sph_check(sph_ctx* ctx);
+
+/* Number of kernel launches one sph_step(ctx, 1) enqueues. */
+SPH_API int32_t sph_launches_per_step(const sph_ctx* ctx);
+
+/* Release the context (host memory, graphs, internal stream).  The caller
+ * frees its own device buffers afterwards. */
+SPH_API sph_status sph_destroy(sph_ctx* ctx);
+
+SPH_API const char* sph_status_string(sph_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,501 @@
+// FP64 form of the two-fluid spin-SPH step (every stored field and every
+// arithmetic operation in double precision).
+//
+// Model (Sec. 2.1, Eqs. 1, 2, 4; Algorithm 1; Sec. 3 boundary set-up):
+//   density   rho_i = sum_j m_j W_ij (self included), Wendland C2, support 2h,
+//             for fluid and inner-wall particles; outer walls keep rho0;
+//   pressure  Eq. 4, P = p0 (rho/rho0)^alpha_P - beta_P;
+//   pair pass per neighbour j of a fluid particle i, r_ij = r_i - r_j,
+//             F = -(1/r) dW/dr, V = m/rho, e = r_ij / r:
+//     pressure      m_i m_j (P_i/rho_i^2 + P_j/rho_j^2) F r_ij
+//     interfacial   C_T V_i V_j F (x_ij, y_ij, 0)        unlike species only
+//     shear         -10 (eta - 0.6 eta_r) V_i V_j F (e.v_ij) e  neither inviscid
+//     rotational    -4 eta_r V_i V_j F (I - ee) u_ij,       neither inviscid
+//                   u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
+//     F_sn          -C_l V_i V_j W u_ij                    unlike species only
+//     spin torque   -1/2 r_ij x (rotational + F_sn), I_i dw_i/dt = tau_i;
+//   integrator kick-drift-kick velocity Verlet, rigid walls rotating at Omega,
+//   periodic z (slip top/bottom).  Walls count as the viscous species.
+#include <math.h>
+
+#include "sph_kernels.h"
+
+namespace sphgb {
+namespace {
+
+__device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
+  if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
+}
+
+__device__ __forceinline__ bool finite3(double a, double b, double c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Cell of a position.  A particle outside the interior cell range (or with a
+// non-finite coordinate) is clamped into it and ERR_ESCAPED is latched, so
+// every later access stays inside the cell arrays.
+__device__ __forceinline__ uint32_t cell_key(const InstDev& P, double x, double y, double z,
+                                             uint32_t* err) {
+  int c[3];
+  const double r[3] = {x, y, z};
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double t = floor((r[a] - P.lo[a]) * P.inv_cell[a]);
+    if (a == 2 && P.periodic_z) {
+      // z was wrapped into [lo, lo + Hz); rounding may give nz for z just
+      // below the top, which belongs to the last cell
+      bad |= !(r[a] >= P.lo[a] && r[a] < P.lo[a] + P.Hz);
+      c[a] = (t >= 0.0) ? ((t <= (double)(P.nz - 1)) ? (int)t : P.nz - 1) : 0;
+    } else if (t >= (double)P.clo[a] && t <= (double)P.chi[a]) {
+      c[a] = (int)t;
+    } else {
+      bad = true;
+      c[a] = (t > (double)P.chi[a]) ? P.chi[a] : P.clo[a];  // NaN -> clo
+    }
+  }
+  if (bad) latch(err, ERR_ESCAPED);
+  return (uint32_t)(P.cell_base + c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2]));
+}
+
+inline int grid_for(int64_t n, int threads, int sm_count, int per_sm) {
+  int64_t g = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- integrator
+
+__global__ void k_kick_drift_fp64(int64_t n, Fp64Buf b, Fp64Fields f,
+                                  const InstDev* __restrict__ inst,
+                                  const InstState* __restrict__ ist, CellWs cw,
+                                  uint32_t* err, int mode) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = b.inst[i];
+    const InstDev& P = inst[k];
+    dvec4 p = b.pos[i];
+    dvec4 v = b.vel[i];
+    dvec4 w = b.spin[i];
+    const int sp = (int)p.w;
+    if (sp < 2) {
+      if (mode == 1) {
+        const dvec4 a = f.acc[i];
+        const dvec4 al = f.dspin[i];
+        v.x += P.hdt * a.x;
+        v.y += P.hdt * a.y;
+        v.z += P.hdt * a.z;
+        w.x += P.hdt * al.x;
+        w.y += P.hdt * al.y;
+        w.z += P.hdt * al.z;
+        p.x += P.dt * v.x;
+        p.y += P.dt * v.y;
+        p.z += P.dt * v.z;
+        if (P.periodic_z) {
+          if (p.z >= P.Hz + P.lo[2]) p.z -= P.Hz;
+          else if (p.z < P.lo[2]) p.z += P.Hz;
+        }
+        b.vel[i] = v;
+        b.spin[i] = w;
+        b.pos[i] = p;
+      }
+      if (!finite3(p.x, p.y, p.z) || !finite3(v.x, v.y, v.z) || !finite3(w.x, w.y, w.z))
+        latch(err, ERR_NONFINITE);
+    } else {
+      // rigid vessel: phase theta_n (mode 0) or theta_n + Omega dt (mode 1)
+      double th = ist[k].theta;
+      if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
+      double s, c;
+      sincos(th, &s, &c);
+      const dvec2 r0 = b.ref[i];
+      p.x = __dsub_rn(__dmul_rn(c, r0.x), __dmul_rn(s, r0.y));
+      p.y = __dadd_rn(__dmul_rn(s, r0.x), __dmul_rn(c, r0.y));
+      v.x = -P.Omega * p.y;
+      v.y = P.Omega * p.x;
+      v.z = 0.0;
+      w.x = 0.0;
+      w.y = 0.0;
+      w.z = P.Omega;
+      b.pos[i] = p;
+      b.vel[i] = v;
+      b.spin[i] = w;
+    }
+    const uint32_t key = cell_key(P, p.x, p.y, p.z, err);
+    cw.key[i] = key;
+    cw.slot[i] = atomicAdd(&cw.count[key], 1u);
+  }
+}
+
+__global__ void k_kick_fp64(int64_t n, Fp64Buf b, Fp64Fields f,
+                            const InstDev* __restrict__ inst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double spw = b.pos[i].w;
+    if (spw >= 2.0) continue;
+    const double hdt = inst[b.inst[i]].hdt;
+    const dvec4 a = f.acc[i];
+    const dvec4 al = f.dspin[i];
+    dvec4 v = b.vel[i];
+    dvec4 w = b.spin[i];
+    v.x += hdt * a.x;
+    v.y += hdt * a.y;
+    v.z += hdt * a.z;
+    w.x += hdt * al.x;
+    w.y += hdt * al.y;
+    w.z += hdt * al.z;
+    b.vel[i] = v;
+    b.spin[i] = w;
+  }
+}
+
+// -------------------------------------------------------------------- reorder
+
+__global__ void k_reorder_fp64(int64_t n, Fp64Buf src, Fp64Buf dst, CellWs cw, NbrWs nw) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = cw.perm[k];
+    const dvec4 p = src.pos[j];
+    dst.pos[k] = p;
+    dst.vel[k] = src.vel[j];
+    dst.spin[k] = src.spin[j];
+    dst.ref[k] = src.ref[j];
+    dst.id[k] = src.id[j];
+    dst.inst[k] = src.inst[j];
+    cw.skey[k] = cw.key[j];
+    nw.posf[k] = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
+  }
+}
+
+// -------------------------------------------------------------------- density
+
+__device__ __forceinline__ double ipow(double x, int e) {
+  double r = 1.0;
+  for (int t = 0; t < e; ++t) r *= x;
+  return r;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
+               CellWs cw, NbrWs nw, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = inst[b.inst[i]];
+  const dvec4 pi = b.pos[i];
+  const int sp = (int)pi.w;
+  const double m_i = sp == 0 ? P.m_s : P.m_n;
+  double rho;
+  uint32_t cnt = 0;
+  if (sp == 3) {
+    rho = P.rho0;
+  } else {
+    const float4 pf = nw.posf[i];
+    const int64_t c = (int64_t)cw.skey[i] - P.cell_base;
+    const int cx = (int)(c % P.nx);
+    const int cy = (int)((c / P.nx) % P.ny);
+    const int cz = (int)(c / ((int64_t)P.nx * P.ny));
+    const uint32_t cap = (uint32_t)nw.cap;
+    const float cut2f = P.cut2f_margin;
+    // phase 1: FP32 prefilter over the 27 neighbour cells (9 contiguous runs,
+    // x is the fastest cell index) into the provisional neighbour list
+    for (int dz = -1; dz <= 1; ++dz) {
+      int z2 = cz + dz;
+      if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int64_t row = P.cell_base + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2);
+        const uint32_t s = cw.start[row + cx - 1];
+        const uint32_t e = cw.start[row + cx + 2];
+        for (uint32_t j = s; j < e; ++j) {
+          if (j == (uint32_t)i) continue;
+          const float4 q = nw.posf[j];
+          float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
+          if (P.periodic_z) {
+            if (ddz > P.half_Hzf) ddz -= P.Hzf;
+            else if (ddz < -P.half_Hzf) ddz += P.Hzf;
+          }
+          const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2f < cut2f) {
+            if (cnt < cap) nw.list[(int64_t)cnt * n + i] = j;
+            ++cnt;
+          }
+        }
+      }
+    }
+    if (cnt > cap) {
+      latch(err, ERR_NEIGHBORS);
+      cnt = cap;
+    }
+    // phase 2: exact FP64 cutoff (no fused multiply-add in r^2, strict <),
+    // compaction of the list in place, and the density sum
+    rho = m_i * P.aD;  // self term W(0)
+    uint32_t w = 0;
+    for (uint32_t t = 0; t < cnt; ++t) {
+      const uint32_t j = nw.list[(int64_t)t * n + i];
+      const dvec4 pj = b.pos[j];
+      const double dx = __dsub_rn(pi.x, pj.x);
+      const double dy = __dsub_rn(pi.y, pj.y);
+      double dz = __dsub_rn(pi.z, pj.z);
+      if (P.periodic_z) {
+        if (dz > P.half_Hz) dz = __dsub_rn(dz, P.Hz);
+        else if (dz < -P.half_Hz) dz = __dadd_rn(dz, P.Hz);
+      }
+      const double r2 =
+          __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      if (r2 < P.cut2) {
+        nw.list[(int64_t)w * n + i] = j;
+        ++w;
+        const double q = sqrt(r2) * P.inv_h;
+        const double t1 = 1.0 - 0.5 * q;
+        const double t2 = t1 * t1;
+        const double m_j = pj.w == 0.0 ? P.m_s : P.m_n;
+        rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
+      }
+    }
+    cnt = w;
+  }
+  nw.count[i] = cnt;
+  const double Pres = P.p0 * ipow(rho * P.inv_rho0, P.alphaP) - P.beta_P;
+  f.rho[i] = rho;
+  f.P[i] = Pres;
+  b.vel[i].w = m_i / rho;
+  b.spin[i].w = Pres / (rho * rho);
+  if (!isfinite(rho) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------------ pair pass
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
+              NbrWs nw, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const dvec4 pi = b.pos[i];
+  const int sp_i = (int)pi.w;
+  if (sp_i >= 2) {
+    const dvec4 z = {0.0, 0.0, 0.0, 0.0};
+    f.acc[i] = z;
+    f.dspin[i] = z;
+    f.tw[i] = z;
+    return;
+  }
+  const InstDev& P = inst[b.inst[i]];
+  const dvec4 vi = b.vel[i];   // w = V_i
+  const dvec4 wi = b.spin[i];  // w = P_i / rho_i^2
+  const double m_i = sp_i == 0 ? P.m_s : P.m_n;
+  const double inv_I = sp_i == 0 ? P.inv_I_s : P.inv_I_n;
+  const uint32_t fl = P.flags;
+  // per-particle coefficients with the term switches folded in
+  const double cP = (fl & SPH_TERM_P) ? m_i : 0.0;
+  const double cT = (fl & SPH_TERM_T) ? P.C_T * vi.w : 0.0;
+  const double cSH = (fl & SPH_TERM_SH) ? -P.A * vi.w : 0.0;
+  const double cR = (fl & SPH_TERM_ROT) ? -P.B * vi.w : 0.0;
+  const double cSN = (fl & SPH_TERM_SN) ? -P.C_l * vi.w : 0.0;
+  const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
+  const bool literal = (fl & SPH_SN_LITERAL) != 0;
+  const bool inv_i = sp_i == 0;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  double tx = 0.0, ty = 0.0, tz = 0.0;
+  double wx = 0.0, wy = 0.0, wz = 0.0;
+  const uint32_t cnt = nw.count[i];
+  for (uint32_t t = 0; t < cnt; ++t) {
+    const uint32_t j = nw.list[(int64_t)t * n + i];
+    const dvec4 pj = b.pos[j];
+    const dvec4 vj = b.vel[j];
+    const dvec4 wj = b.spin[j];
+    const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+    double dz = pi.z - pj.z;
+    if (P.periodic_z) {
+      if (dz > P.half_Hz) dz -= P.Hz;
+      else if (dz < -P.half_Hz) dz += P.Hz;
+    }
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0.0)) continue;  // coincident particles: density only
+    const double inv_r = rsqrt(r2);
+    const double r = r2 * inv_r;
+    const double q = r * P.inv_h;
+    const double t1 = 1.0 - 0.5 * q;
+    const double t2 = t1 * t1;
+    const double F = P.cF * t2 * t1;
+    const double W = P.aD * t2 * t2 * (2.0 * q + 1.0);
+    const bool inv_j = pj.w == 0.0;
+    const double mX = (inv_i != inv_j) ? 1.0 : 0.0;
+    const double mV = (!inv_i && !inv_j) ? 1.0 : 0.0;
+    const double m_j = inv_j ? P.m_s : P.m_n;
+    const double Vj = vj.w;
+    // relative and spin-corrected velocity
+    const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+    const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
+    const double ux = vx + 0.5 * (dy * sz - dz * sy);
+    const double uy = vy + 0.5 * (dz * sx - dx * sz);
+    const double uz = vz + 0.5 * (dx * sy - dy * sx);
+    const double ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+    const double ev = ex * vx + ey * vy + ez * vz;
+    const double eu = ex * ux + ey * uy + ez * uz;
+    // scalar coefficients of the five terms
+    const double sP = cP * m_j * (wi.w + wj.w) * F;
+    const double sT = cT * Vj * F * mX;
+    const double sSH = cSH * Vj * F * ev * mV;
+    const double sR = cR * Vj * F * mV;
+    const double sSN = cSN * Vj * W * mX;
+    // rotational viscosity (transverse part of u) and F_sn
+    const double frx = sR * (ux - eu * ex);
+    const double fry = sR * (uy - eu * ey);
+    const double frz = sR * (uz - eu * ez);
+    const double gx = literal ? vx : ux, gy = literal ? vy : uy, gz = literal ? vz : uz;
+    const double fnx = sSN * gx, fny = sSN * gy, fnz = sSN * gz;
+    const double pfx = sP * dx + sT * dx + sSH * ex + frx + fnx;
+    const double pfy = sP * dy + sT * dy + sSH * ey + fry + fny;
+    const double pfz = sP * dz + hz * sT * dz + sSH * ez + frz + fnz;
+    fx += pfx;
+    fy += pfy;
+    fz += pfz;
+    // spin torque -1/2 r_ij x (f_rot + f_sn)
+    const double kx = frx + (literal ? 0.0 : fnx);
+    const double ky = fry + (literal ? 0.0 : fny);
+    const double kz = frz + (literal ? 0.0 : fnz);
+    const double qx = -0.5 * (dy * kz - dz * ky);
+    const double qy = -0.5 * (dz * kx - dx * kz);
+    const double qz = -0.5 * (dx * ky - dy * kx);
+    tx += qx;
+    ty += qy;
+    tz += qz;
+    if (pj.w >= 2.0) {  // torque exerted by the wall on particle i
+      wx += pi.y * pfz - pi.z * pfy + qx;
+      wy += pi.z * pfx - pi.x * pfz + qy;
+      wz += pi.x * pfy - pi.y * pfx + qz;
+    }
+  }
+  const double inv_m = 1.0 / m_i;
+  f.acc[i] = dvec4{fx * inv_m, fy * inv_m, fz * inv_m, 0.0};
+  f.dspin[i] = dvec4{tx * inv_I, ty * inv_I, tz * inv_I, 0.0};
+  f.tw[i] = dvec4{wx, wy, wz, 0.0};
+  if (!finite3(fx, fy, fz) || !finite3(tx, ty, tz)) latch(err, ERR_NONFINITE);
+}
+
+// ----------------------------------------------------------- load / unload
+
+__global__ void k_load_fp64(int64_t n, Fp64Buf b, const double* __restrict__ pos,
+                            const double* __restrict__ vel, const double* __restrict__ spin,
+                            const uint8_t* __restrict__ sp, const uint32_t* __restrict__ inst_of) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = (double)sp[i];
+    b.pos[i] = dvec4{pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], s};
+    b.vel[i] = dvec4{vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0};
+    b.spin[i] = dvec4{spin[3 * i], spin[3 * i + 1], spin[3 * i + 2], 0.0};
+    b.ref[i] = dvec2{pos[3 * i], pos[3 * i + 1]};
+    b.id[i] = (uint32_t)i;
+    b.inst[i] = inst_of[i];
+  }
+}
+
+__global__ void k_unsort_fp64(int64_t n, Fp64Buf b, Fp64Fields f, double* pos, double* vel,
+                              double* spin, double* rho, double* P, double* acc,
+                              double* dspin) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b.id[k];
+    if (pos) {
+      const dvec4 p = b.pos[k];
+      pos[3 * o] = p.x;
+      pos[3 * o + 1] = p.y;
+      pos[3 * o + 2] = p.z;
+    }
+    if (vel) {
+      const dvec4 v = b.vel[k];
+      vel[3 * o] = v.x;
+      vel[3 * o + 1] = v.y;
+      vel[3 * o + 2] = v.z;
+    }
+    if (spin) {
+      const dvec4 w = b.spin[k];
+      spin[3 * o] = w.x;
+      spin[3 * o + 1] = w.y;
+      spin[3 * o + 2] = w.z;
+    }
+    if (rho) rho[o] = f.rho[k];
+    if (P) P[o] = f.P[k];
+    if (acc) {
+      const dvec4 a = f.acc[k];
+      acc[3 * o] = a.x;
+      acc[3 * o + 1] = a.y;
+      acc[3 * o + 2] = a.z;
+    }
+    if (dspin) {
+      const dvec4 a = f.dspin[k];
+      dspin[3 * o] = a.x;
+      dspin[3 * o + 1] = a.y;
+      dspin[3 * o + 2] = a.z;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_kick_drift_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                   const InstDev* inst, const InstState* ist,
+                                   const CellWs& cw, uint32_t* err, int mode,
+                                   cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  k_kick_drift_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, ist, cw,
+                                                                       err, mode);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_fp64(int64_t n, const Fp64Buf& src, const Fp64Buf& dst,
+                                const CellWs& cw, const NbrWs& nw, cudaStream_t s,
+                                const LaunchCfg& lc, int* launches) {
+  k_reorder_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, cw, nw);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                                int* launches) {
+  (void)lc;
+  constexpr int B = 128;
+  k_density_fp64<B><<<(unsigned)((n + B - 1) / B), B, 0, s>>>(n, b, f, inst, cw, nw, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                               const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                               cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  (void)lc;
+  constexpr int B = 128;
+  k_forces_fp64<B><<<(unsigned)((n + B - 1) / B), B, 0, s>>>(n, b, f, inst, nw, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                             const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
+                             int* launches) {
+  k_kick_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                               double* pos, double* vel, double* spin, double* rho,
+                               double* P, double* acc, double* dspin, cudaStream_t s,
+                               const LaunchCfg& lc) {
+  k_unsort_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, pos, vel, spin, rho,
+                                                                   P, acc, dspin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
+                             const double* vel, const double* spin, const uint8_t* sp,
+                             const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc) {
+  k_load_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, pos, vel, spin, sp,
+                                                                 inst_of);
+  return cudaGetLastError();
+}
+
+}  // namespace sphgb

@@ -1,0 +1,696 @@
+// Host side of the C ABI: parameter validation, the layout of the caller-owned
+// device buffers, the step pipeline and its capture into CUDA graphs.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sph_kernels.h"
+
+using namespace sphgb;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kAlign = 256;
+
+// Bump allocator over one caller buffer (or a null base to measure sizes).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(int64_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+    return p;
+  }
+};
+
+bool is_int(double v) { return v == floor(v); }
+
+// Sum of the Wendland C2 kernel over the integer lattice (host copy used for
+// the particle mass m = rho0 / sum).
+double lattice_kernel_sum(double dx, double h) {
+  const double aD = 21.0 / (16.0 * kPi * h * h * h);
+  const int m = (int)ceil(2.0 * h / dx) + 1;
+  double s = 0.0;
+  for (int a = -m; a <= m; ++a)
+    for (int b = -m; b <= m; ++b)
+      for (int c = -m; c <= m; ++c) {
+        const double r = dx * sqrt((double)(a * a + b * b + c * c));
+        const double q = r / h;
+        if (!(q < 2.0)) continue;
+        const double t = 1.0 - 0.5 * q;
+        s += aD * t * t * t * t * (2.0 * q + 1.0);
+      }
+  return s;
+}
+
+sph_status derive(const sph_params& p, InstDev& d) {
+  if (!(p.dx > 0) || !(p.h > 0) || !(p.rho0 > 0) || !(p.dt > 0) || !(p.p0 >= 0) ||
+      !(p.inertia_coef > 0) || !(p.mass_ratio > 0) || !isfinite(p.Omega) ||
+      !isfinite(p.beta_P) || !isfinite(p.eta_bar) || !isfinite(p.eta_r) ||
+      !isfinite(p.C_l) || !isfinite(p.C_T))
+    return SPH_ERR_ARG;
+  if (!(p.alpha_P >= 1 && p.alpha_P <= 16 && is_int(p.alpha_P))) return SPH_ERR_ARG;
+  if (p.precision != SPH_FP64 && p.precision != SPH_MIXED) return SPH_ERR_ARG;
+  if (p.flags & ~127u) return SPH_ERR_ARG;
+  memset(&d, 0, sizeof d);
+  const double h = p.h;
+  d.h = h;
+  d.inv_h = 1.0 / h;
+  d.cut2 = (2.0 * h) * (2.0 * h);
+  d.aD = 21.0 / (16.0 * kPi * h * h * h);
+  d.cF = 5.0 * d.aD / (h * h);
+  const double S = lattice_kernel_sum(p.dx, h);
+  d.m_n = p.rho0 / S;
+  d.m_s = p.mass_ratio * d.m_n;
+  d.inv_I_n = 1.0 / (p.inertia_coef * d.m_n * p.dx * p.dx);
+  d.inv_I_s = 1.0 / (p.inertia_coef * d.m_s * p.dx * p.dx);
+  d.rho0 = p.rho0;
+  d.inv_rho0 = 1.0 / p.rho0;
+  d.p0 = p.p0;
+  d.beta_P = p.beta_P;
+  d.A = 10.0 * (p.eta_bar - 0.6 * p.eta_r);
+  d.B = 4.0 * p.eta_r;
+  d.C_l = p.C_l;
+  d.C_T = p.C_T;
+  d.Omega = p.Omega;
+  d.dt = p.dt;
+  d.hdt = 0.5 * p.dt;
+  d.alphaP = (int32_t)p.alpha_P;
+  d.flags = p.flags;
+  d.periodic_z = p.periodic_z ? 1 : 0;
+  const double side = 2.0 * h;
+  double xmax = 0.0;
+  int32_t n[3];
+  for (int a = 0; a < 3; ++a) {
+    const double L = p.box_hi[a] - p.box_lo[a];
+    if (!(L > 0) || !isfinite(L)) return SPH_ERR_ARG;
+    const double ncell = floor(L / side);
+    const bool per = (a == 2 && d.periodic_z);
+    if (per) {
+      if (ncell < 3) return SPH_ERR_ARG;  // the 27-cell stencil needs 3 z cells
+      if (ncell > 1 << 20) return SPH_ERR_GRID_OVERFLOW;
+      n[a] = (int32_t)ncell;
+      d.cell[a] = L / ncell;
+      d.lo[a] = p.box_lo[a];
+      d.clo[a] = 0;
+      d.chi[a] = n[a] - 1;
+    } else {
+      const double ni = ncell < 1 ? 1 : ncell;
+      if (ni > 1 << 20) return SPH_ERR_GRID_OVERFLOW;
+      n[a] = (int32_t)ni + 2;  // ghost cell on both sides
+      d.cell[a] = L / ni;
+      d.lo[a] = p.box_lo[a] - d.cell[a];
+      d.clo[a] = 1;
+      d.chi[a] = n[a] - 2;
+    }
+    d.inv_cell[a] = 1.0 / d.cell[a];
+    xmax = fmax(xmax, fmax(fabs(p.box_lo[a]), fabs(p.box_hi[a])) + d.cell[a]);
+  }
+  d.nx = n[0];
+  d.ny = n[1];
+  d.nz = n[2];
+  const double Hz = p.box_hi[2] - p.box_lo[2];
+  d.Hz = Hz;
+  d.half_Hz = 0.5 * Hz;
+  d.Hzf = (float)Hz;
+  d.half_Hzf = (float)(0.5 * Hz);
+  // FP32 prefilter bound: with coordinates rounded to float (|x| <= xmax) the
+  // float r^2 of every true neighbour stays below cut2 + margin.
+  const double eps = (2.0 * xmax + 2.0 * side) * ldexp(1.0, -24);
+  const double margin = 4.0 * (2.0 * sqrt(3.0) * side * eps + 3.0 * eps * eps +
+                               6.0 * d.cut2 * ldexp(1.0, -24));
+  d.cut2f_margin = nextafterf((float)(d.cut2 + margin), INFINITY);
+  return SPH_OK;
+}
+
+}  // namespace
+
+struct sph_ctx {
+  int32_t n_inst = 0;
+  int64_t n = 0;
+  int32_t precision = SPH_FP64;
+  int32_t cap = 160;
+  std::vector<InstDev> inst_h;
+  InstDev* inst = nullptr;
+  InstState* ist = nullptr;
+  uint32_t* err = nullptr;
+  Fp64Buf buf[2];
+  int cur = 0;
+  Fp64Fields f;
+  CellWs cw;
+  NbrWs nw;
+  int64_t total_chunks = 0;
+  double* part_tw = nullptr;
+  double* part_diag = nullptr;
+  double* diag_out = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool forces_valid = false;
+  bool lists_valid = false;      // neighbour lists of the current sorted order
+  int launches_per_step = 0;
+  LaunchCfg lc;
+};
+
+namespace {
+
+struct Carved {
+  Fp64Buf buf[2];
+  Fp64Fields f;
+  CellWs cw;
+  NbrWs nw;
+  InstDev* inst;
+  InstState* ist;
+  uint32_t* err;
+  double *part_tw, *part_diag, *diag_out;
+  size_t state_bytes, ws_bytes;
+};
+
+void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
+           int64_t total_chunks, int32_t cap, Carved& c) {
+  Carver s(state);
+  c.inst = s.take<InstDev>(n_inst);
+  c.ist = s.take<InstState>(n_inst);
+  c.err = s.take<uint32_t>(4);
+  for (int b = 0; b < 2; ++b) {
+    c.buf[b].pos = s.take<dvec4>(n);
+    c.buf[b].vel = s.take<dvec4>(n);
+    c.buf[b].spin = s.take<dvec4>(n);
+    c.buf[b].ref = s.take<dvec2>(n);
+    c.buf[b].id = s.take<uint32_t>(n);
+    c.buf[b].inst = s.take<uint32_t>(n);
+  }
+  c.f.acc = s.take<dvec4>(n);
+  c.f.dspin = s.take<dvec4>(n);
+  c.f.tw = s.take<dvec4>(n);
+  c.f.rho = s.take<double>(n);
+  c.f.P = s.take<double>(n);
+  c.state_bytes = s.off + kAlign;
+
+  Carver w(ws);
+  c.cw.key = w.take<uint32_t>(n);
+  c.cw.slot = w.take<uint32_t>(n);
+  c.cw.perm = w.take<uint32_t>(n);
+  c.cw.skey = w.take<uint32_t>(n);
+  c.cw.count = w.take<uint32_t>(n_cells);
+  c.cw.start = w.take<uint32_t>(n_cells + 1);
+  c.cw.n_cells = n_cells;
+  c.cw.n_scan_blocks = (n_cells + kScanChunk - 1) / kScanChunk;
+  c.cw.bsum = w.take<uint32_t>(c.cw.n_scan_blocks + 1);
+  c.nw.list = w.take<uint32_t>((int64_t)cap * n);
+  c.nw.count = w.take<uint32_t>(n);
+  c.nw.posf = w.take<float4>(n);
+  c.nw.cap = cap;
+  c.part_tw = w.take<double>(3 * total_chunks);
+  c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
+  c.diag_out = w.take<double>((int64_t)kDiagFields * n_inst);
+  c.ws_bytes = w.off + kAlign;
+}
+
+struct Plan {
+  std::vector<InstDev> inst;
+  int64_t n = 0, n_cells = 0, total_chunks = 0;
+  int32_t cap = 160;
+  int32_t precision = SPH_FP64;
+};
+
+sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts, Plan& pl) {
+  if (n_inst < 1 || n_inst > kMaxInst || !params || !counts) return SPH_ERR_ARG;
+  pl.inst.resize(n_inst);
+  pl.precision = params[0].precision;
+  pl.cap = params[0].nbr_cap ? params[0].nbr_cap : 160;
+  if (pl.cap < 64 || pl.cap > 1024) return SPH_ERR_ARG;
+  int64_t pb = 0, cb = 0, kb = 0;
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (params[k].precision != pl.precision) return SPH_ERR_ARG;
+    if ((params[k].nbr_cap ? params[k].nbr_cap : 160) != pl.cap) return SPH_ERR_ARG;
+    if (counts[k] < 1) return SPH_ERR_ARG;
+    sph_status st = derive(params[k], pl.inst[k]);
+    if (st != SPH_OK) return st;
+    InstDev& d = pl.inst[k];
+    d.cell_base = cb;
+    d.p_begin = pb;
+    d.p_end = pb + counts[k];
+    d.chunk_base = kb;
+    d.n_chunks = (counts[k] + kReduceChunk - 1) / kReduceChunk;
+    cb += (int64_t)d.nx * d.ny * d.nz;
+    pb += counts[k];
+    kb += d.n_chunks;
+  }
+  if (pb >= (int64_t)0xFFFFFFF0ll || cb >= (int64_t)0xFFFFFFF0ll) return SPH_ERR_GRID_OVERFLOW;
+  pl.n = pb;
+  pl.n_cells = cb;
+  pl.total_chunks = kb;
+  return SPH_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define CK(x)                                       \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return SPH_ERR_CUDA;     \
+  } while (0)
+
+sph_status decode_err(uint32_t e) {
+  if (e & ERR_NONFINITE) return SPH_ERR_NONFINITE;
+  if (e & ERR_ESCAPED) return SPH_ERR_ESCAPED;
+  if (e & ERR_NEIGHBORS) return SPH_ERR_NEIGHBORS;
+  if (e & ERR_TIMEOUT) return SPH_ERR_TIMEOUT;
+  return SPH_OK;
+}
+
+// ---- pipeline pieces (enqueue only) -----------------------------------------
+
+sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches) {
+  const Fp64Buf& src = c->buf[c->cur];
+  const Fp64Buf& dst = c->buf[1 - c->cur];
+  CK(cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s));
+  CK(launch_kick_drift_fp64(c->n, src, c->f, c->inst, c->ist, c->cw, c->err, mode, s, c->lc,
+                            launches));
+  CK(launch_scan(c->cw, s, launches));
+  CK(launch_scatter_sort(c->cw, src.id, c->n, s, c->lc, launches));
+  CK(launch_reorder_fp64(c->n, src, dst, c->cw, c->nw, s, c->lc, launches));
+  return SPH_OK;
+}
+
+sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches) {
+  CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
+                         launches));
+  c->lists_valid = true;
+  return SPH_OK;
+}
+
+sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches) {
+  CK(launch_forces_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->nw, c->err, s, c->lc,
+                        launches));
+  if (advance) CK(launch_kick_fp64(c->n, c->buf[c->cur], c->f, c->inst, s, c->lc, launches));
+  CK(launch_wall_torque_fp64(c->n_inst, c->total_chunks, c->inst, c->ist, c->buf[c->cur], c->f,
+                             c->part_tw, advance, s, launches));
+  return SPH_OK;
+}
+
+// One kick-drift-kick step; flips c->cur (the reorder target becomes current).
+sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches) {
+  sph_status st = enqueue_cells(c, s, 1, launches);
+  if (st != SPH_OK) return st;
+  c->cur = 1 - c->cur;
+  st = enqueue_density(c, s, launches);
+  if (st != SPH_OK) return st;
+  return enqueue_forces(c, s, 1, launches);
+}
+
+sph_status capture_graphs(sph_ctx* c) {
+  const int saved = c->cur;
+  for (int g = 0; g < 2; ++g) {
+    c->cur = (saved + g) & 1;
+    const int start_cur = c->cur;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    sph_status st = enqueue_step(c, c->cap_stream, &launches);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != SPH_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      c->cur = saved;
+      return st != SPH_OK ? st : SPH_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->cur = saved;
+      return SPH_ERR_CUDA;
+    }
+    c->graph[start_cur] = exec;
+    c->launches_per_step = launches;
+  }
+  c->cur = saved;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sph_status_string(sph_status s) {
+  switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA runtime error";
+    case SPH_ERR_WORKSPACE: return "state or workspace buffer too small or misaligned";
+    case SPH_ERR_GRID_OVERFLOW: return "cell grid or particle count too large";
+    case SPH_ERR_ESCAPED: return "a particle left the cell grid";
+    case SPH_ERR_NONFINITE: return "non-finite value in the state";
+    case SPH_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case SPH_ERR_STATE: return "call out of order";
+    case SPH_ERR_NEIGHBORS: return "neighbour list overflow (raise nbr_cap)";
+  }
+  return "unknown status";
+}
+
+sph_status sph_params_default(sph_params* p, double R, double H, double Omega) {
+  if (!p || !(R > 0) || !(H > 0) || !(Omega > 0)) return SPH_ERR_ARG;
+  memset(p, 0, sizeof *p);
+  const double dx = 1.0, h = 1.3 * dx, rho0 = 1.0, gamma = 7.0;
+  const double cs = 10.0 * Omega * R;
+  p->dx = dx;
+  p->h = h;
+  p->rho0 = rho0;
+  p->alpha_P = gamma;
+  p->p0 = rho0 * cs * cs / gamma;
+  p->beta_P = p->p0;
+  p->eta_bar = rho0 * Omega * R * R / 100.0;
+  p->eta_r = p->eta_bar;
+  p->C_l = 1e-3 * rho0 * Omega;
+  p->C_T = 0.01 * p->p0;
+  p->C_omega = 0.016;
+  p->mass_ratio = 1.0;
+  p->inertia_coef = 0.1;
+  p->Omega = Omega;
+  p->dt = 0.25 * h / cs;
+  const double ext = R + 2.0 * dx + 2.0 * h;
+  p->box_lo[0] = p->box_lo[1] = -ext;
+  p->box_hi[0] = p->box_hi[1] = ext;
+  p->box_lo[2] = 0.0;
+  p->box_hi[2] = H;
+  p->periodic_z = 1;
+  p->precision = SPH_FP64;
+  p->flags = SPH_FLAGS_DEFAULT;
+  p->nbr_cap = 160;
+  return SPH_OK;
+}
+
+size_t sph_state_bytes(int32_t n_inst, const sph_params* params, const int64_t* counts) {
+  Plan pl;
+  if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
+  Carved c;
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, c);
+  return c.state_bytes;
+}
+
+size_t sph_workspace_bytes(int32_t n_inst, const sph_params* params, const int64_t* counts) {
+  Plan pl;
+  if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
+  Carved c;
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, c);
+  return c.ws_bytes;
+}
+
+sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* params,
+                          const int64_t* counts, const double* pos, const double* vel,
+                          const double* spin, const uint8_t* species, void* dev_state,
+                          size_t state_bytes, void* dev_workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (!out) return SPH_ERR_ARG;
+  *out = nullptr;
+  if (!pos || !vel || !spin || !species || !dev_state || !dev_workspace) return SPH_ERR_ARG;
+  Plan pl;
+  sph_status st = plan(n_inst, params, counts, pl);
+  if (st != SPH_OK) return st;
+  if (pl.precision != SPH_FP64) return SPH_ERR_ARG;  // mixed form: separate entry
+  if (((uintptr_t)dev_state % kAlign) || ((uintptr_t)dev_workspace % kAlign))
+    return SPH_ERR_WORKSPACE;
+  Carved cv;
+  carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, cv);
+  if (state_bytes < cv.state_bytes || workspace_bytes < cv.ws_bytes) return SPH_ERR_WORKSPACE;
+
+  sph_ctx* c = new (std::nothrow) sph_ctx();
+  if (!c) return SPH_ERR_ARG;
+  c->n_inst = n_inst;
+  c->n = pl.n;
+  c->precision = pl.precision;
+  c->cap = pl.cap;
+  c->inst_h = pl.inst;
+  c->inst = cv.inst;
+  c->ist = cv.ist;
+  c->err = cv.err;
+  c->buf[0] = cv.buf[0];
+  c->buf[1] = cv.buf[1];
+  c->f = cv.f;
+  c->cw = cv.cw;
+  c->nw = cv.nw;
+  c->total_chunks = pl.total_chunks;
+  c->part_tw = cv.part_tw;
+  c->part_diag = cv.part_diag;
+  c->diag_out = cv.diag_out;
+  c->staging = cv.nw.list;
+  c->staging_bytes = sizeof(uint32_t) * (size_t)pl.cap * (size_t)pl.n;
+  c->stream = (cudaStream_t)stream;
+  int dev = 0;
+  auto fail = [&](sph_status s) {
+    sph_destroy(c);
+    return s;
+  };
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(SPH_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&c->lc.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+  c->lc.block_density = 128;
+  c->lc.block_forces = 128;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+
+  cudaStream_t s = c->stream;
+  const int64_t n = pl.n;
+  // inputs: device pointers are used in place, host pointers go through the
+  // staging area (the neighbour-list region, unused until the first density)
+  char* stg = (char*)c->staging;
+  size_t off = 0;
+  auto stage = [&](const void* src, size_t bytes, const void** dst) -> sph_status {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    if (off + bytes > c->staging_bytes) return SPH_ERR_WORKSPACE;
+    if (is_device_ptr(src)) {
+      *dst = src;
+      return SPH_OK;
+    }
+    if (cudaMemcpyAsync(stg + off, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return SPH_ERR_CUDA;
+    *dst = stg + off;
+    off += bytes;
+    return SPH_OK;
+  };
+  const void *dpos, *dvel, *dspin, *dsp, *dinst;
+  std::vector<uint32_t> inst_of((size_t)n);
+  for (int32_t k = 0; k < n_inst; ++k)
+    for (int64_t i = pl.inst[k].p_begin; i < pl.inst[k].p_end; ++i) inst_of[(size_t)i] = k;
+  if ((st = stage(pos, sizeof(double) * 3 * n, &dpos)) != SPH_OK) return fail(st);
+  if ((st = stage(vel, sizeof(double) * 3 * n, &dvel)) != SPH_OK) return fail(st);
+  if ((st = stage(spin, sizeof(double) * 3 * n, &dspin)) != SPH_OK) return fail(st);
+  if ((st = stage(species, (size_t)n, &dsp)) != SPH_OK) return fail(st);
+  if ((st = stage(inst_of.data(), sizeof(uint32_t) * n, &dinst)) != SPH_OK) return fail(st);
+  if (cudaMemcpyAsync(c->inst, pl.inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+  if (cudaMemsetAsync(c->ist, 0, sizeof(InstState) * n_inst, s) != cudaSuccess ||
+      cudaMemsetAsync(c->err, 0, sizeof(uint32_t) * 4, s) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+  if (launch_load_fp64(n, c->buf[0], (const double*)dpos, (const double*)dvel,
+                       (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst, s,
+                       c->lc) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+  c->cur = 0;
+  // initial evaluation: walls at phase 0, cells, density, forces (a_0, alpha_0)
+  if ((st = enqueue_cells(c, s, 0, nullptr)) != SPH_OK) return fail(st);
+  c->cur = 1;
+  if ((st = enqueue_density(c, s, nullptr)) != SPH_OK) return fail(st);
+  if ((st = enqueue_forces(c, s, 0, nullptr)) != SPH_OK) return fail(st);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SPH_ERR_CUDA);
+  c->forces_valid = true;
+  uint32_t e = 0;
+  if (cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(SPH_ERR_CUDA);
+  if (e) return fail(decode_err(e));
+  *out = c;
+  return SPH_OK;
+}
+
+sph_status sph_init(sph_ctx** ctx, const sph_params* params, int64_t n, const double* pos,
+                    const double* vel, const double* spin, const uint8_t* species,
+                    void* dev_state, size_t state_bytes, void* dev_workspace,
+                    size_t workspace_bytes, void* stream) {
+  return sph_init_batch(ctx, 1, params, &n, pos, vel, spin, species, dev_state, state_bytes,
+                        dev_workspace, workspace_bytes, stream);
+}
+
+sph_status sph_build_cells(sph_ctx* c) {
+  if (!c) return SPH_ERR_ARG;
+  sph_status st = enqueue_cells(c, c->stream, 0, nullptr);
+  if (st != SPH_OK) return st;
+  c->cur = 1 - c->cur;
+  c->forces_valid = false;
+  c->lists_valid = false;
+  return SPH_OK;
+}
+
+sph_status sph_density(sph_ctx* c) {
+  if (!c) return SPH_ERR_ARG;
+  return enqueue_density(c, c->stream, nullptr);
+}
+
+sph_status sph_forces(sph_ctx* c) {
+  if (!c) return SPH_ERR_ARG;
+  if (!c->lists_valid) return SPH_ERR_STATE;  // needs sph_density first
+  sph_status st = enqueue_forces(c, c->stream, 0, nullptr);
+  if (st == SPH_OK) c->forces_valid = true;
+  return st;
+}
+
+sph_status sph_step(sph_ctx* c, int32_t nsteps) {
+  if (!c || nsteps < 0) return SPH_ERR_ARG;
+  if (nsteps == 0) return SPH_OK;
+  if (!c->forces_valid) {
+    // a standalone cell build reordered the particles: re-evaluate a and alpha
+    sph_status st = enqueue_density(c, c->stream, nullptr);
+    if (st == SPH_OK) st = enqueue_forces(c, c->stream, 0, nullptr);
+    if (st != SPH_OK) return st;
+    c->forces_valid = true;
+  }
+  if (!c->graph[0]) {
+    sph_status st = capture_graphs(c);
+    if (st != SPH_OK) return st;
+  }
+  for (int32_t t = 0; t < nsteps; ++t) {
+    CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+    c->cur = 1 - c->cur;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_check(sph_ctx* c) {
+  if (!c) return SPH_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  uint32_t e = 0;
+  CK(cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
+  return decode_err(e);
+}
+
+sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
+  if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
+  CK(launch_diag_fp64(c->n_inst, c->total_chunks, c->inst, c->buf[c->cur], c->f, c->nw,
+                      c->part_diag, c->diag_out, c->stream));
+  double d[kDiagFields];
+  InstState s;
+  CK(cudaMemcpyAsync(d, c->diag_out + (int64_t)inst * kDiagFields, sizeof d,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&s, c->ist + inst, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+  sph_status st = sph_check(c);
+  memset(out, 0, sizeof *out);
+  out->mass = d[0];
+  out->mass_s = d[1];
+  out->mass_n = d[2];
+  for (int a = 0; a < 3; ++a) {
+    out->mom[a] = d[3 + a];
+    out->L_orb[a] = d[6 + a];
+    out->L_spin[a] = d[9 + a];
+    out->T_wall[a] = s.T_wall[a];
+    out->J_wall[a] = s.J_wall[a];
+  }
+  out->E_kin = d[12];
+  out->E_rot = d[13];
+  out->E_int = d[14];
+  out->n_pairs = (int64_t)d[15];
+  out->rho_min = d[16];
+  out->rho_max = d[17];
+  out->v_max = d[18];
+  out->step = s.step;
+  out->theta = s.theta;
+  return st;
+}
+
+sph_status sph_get_state(sph_ctx* c, double* pos, double* vel, double* spin, double* rho,
+                         double* P, double* acc, double* dspin) {
+  if (!c) return SPH_ERR_ARG;
+  const int64_t n = c->n;
+  double* outs[7] = {pos, vel, spin, rho, P, acc, dspin};
+  const int width[7] = {3, 3, 3, 1, 1, 3, 3};
+  double* dev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t off = 0;
+  char* stg = (char*)c->staging;
+  for (int k = 0; k < 7; ++k) {
+    if (!outs[k]) continue;
+    if (is_device_ptr(outs[k])) {
+      dev[k] = outs[k];
+    } else {
+      const size_t bytes = sizeof(double) * (size_t)width[k] * (size_t)n;
+      off = (off + kAlign - 1) / kAlign * kAlign;
+      if (off + bytes > c->staging_bytes) return SPH_ERR_WORKSPACE;
+      dev[k] = (double*)(stg + off);
+      off += bytes;
+    }
+  }
+  CK(launch_unsort_fp64(n, c->buf[c->cur], c->f, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
+                        dev[6], c->stream, c->lc));
+  for (int k = 0; k < 7; ++k)
+    if (outs[k] && dev[k] != outs[k])
+      CK(cudaMemcpyAsync(outs[k], dev[k], sizeof(double) * (size_t)width[k] * (size_t)n,
+                         cudaMemcpyDeviceToHost, c->stream));
+  sph_status st = sph_check(c);
+  // host outputs were staged in the neighbour-list region; a, alpha, rho and P
+  // are intact but the lists must be rebuilt by the next density pass
+  if (off > 0) c->lists_valid = false;
+  return st;
+}
+
+sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t cap) {
+  if (!c || !offsets) return SPH_ERR_ARG;
+  if (!c->lists_valid) return SPH_ERR_STATE;
+  const int64_t n = c->n;
+  std::vector<uint32_t> cnt((size_t)n), id((size_t)n), list((size_t)c->cap * (size_t)n);
+  CK(cudaMemcpyAsync(cnt.data(), c->nw.count, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(id.data(), c->buf[c->cur].id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(list.data(), c->nw.list, sizeof(uint32_t) * list.size(),
+                     cudaMemcpyDeviceToHost, c->stream));
+  sph_status st = sph_check(c);
+  std::vector<int64_t> where((size_t)n);
+  for (int64_t k = 0; k < n; ++k) where[id[k]] = k;
+  int64_t tot = 0;
+  for (int64_t o = 0; o < n; ++o) {
+    offsets[o] = tot;
+    tot += cnt[(size_t)where[o]];
+  }
+  offsets[n] = tot;
+  if (!nbr || cap < tot) return st != SPH_OK ? st : SPH_ERR_ARG;
+  std::vector<int64_t> tmp;
+  for (int64_t o = 0; o < n; ++o) {
+    const int64_t k = where[o];
+    tmp.clear();
+    for (uint32_t t = 0; t < cnt[(size_t)k]; ++t) tmp.push_back(id[list[(size_t)t * n + k]]);
+    std::sort(tmp.begin(), tmp.end());
+    for (size_t t = 0; t < tmp.size(); ++t) nbr[offsets[o] + (int64_t)t] = tmp[t];
+  }
+  return st;
+}
+
+int32_t sph_launches_per_step(const sph_ctx* c) { return c ? c->launches_per_step : 0; }
+
+sph_status sph_destroy(sph_ctx* c) {
+  if (!c) return SPH_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+  return SPH_OK;
+}
+
+}  // extern "C"

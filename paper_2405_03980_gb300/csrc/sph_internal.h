@@ -1,0 +1,107 @@
+// Internal data layout shared by the host driver and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph.h"
+
+namespace sphgb {
+
+// 32-byte aligned four-double record (one particle's xyz + one scalar) and a
+// 16-byte pair; own types so that the alignment is explicit.
+struct alignas(32) dvec4 {
+  double x, y, z, w;
+};
+struct alignas(16) dvec2 {
+  double x, y;
+};
+
+constexpr int kScanChunk = 4096;       // elements per block of the cell-count scan
+constexpr int kReduceChunk = 32768;    // particles per partial of the FP64 reductions
+constexpr int kDiagFields = 24;        // doubles per diagnostics partial
+constexpr int kMaxInst = 65535;
+
+// Error bits latched on the device.
+enum : uint32_t {
+  ERR_ESCAPED = 1u,
+  ERR_NONFINITE = 2u,
+  ERR_NEIGHBORS = 4u,
+  ERR_TIMEOUT = 8u,
+};
+
+// Derived per-instance constants (host computed, read-only on the device).
+struct InstDev {
+  double h, inv_h, cut2;          // smoothing length, 1/h, (2h)^2
+  double aD, cF;                  // Wendland C2: W = aD t^4 (2q+1), F = cF t^3
+  double m_s, m_n;                // particle masses (inviscid, viscous/wall)
+  double inv_I_s, inv_I_n;        // 1 / spin inertia
+  double rho0, inv_rho0, p0, beta_P;
+  double A, B;                    // shear 10(eta - 0.6 eta_r), rotational 4 eta_r
+  double C_l, C_T;
+  double Omega, dt, hdt;
+  double Hz, half_Hz;             // z period
+  double lo[3], inv_cell[3];      // grid origin (ghost cells included), 1 / side
+  double cell[3];                 // cell side per axis (>= 2h)
+  float cut2f_margin;             // FP32 prefilter bound (>= every FP64 neighbour)
+  float Hzf, half_Hzf;
+  int32_t nx, ny, nz;             // cells per axis (ghost ring except periodic z)
+  int32_t clo[3], chi[3];         // interior cell range per axis (inclusive)
+  int32_t alphaP;                 // integer Tait exponent
+  uint32_t flags;
+  int32_t periodic_z;
+  int64_t cell_base;              // first global cell index of the instance
+  int64_t p_begin, p_end;         // particle range (fixed across sorts)
+  int64_t chunk_base;             // first reduction chunk of the instance
+  int64_t n_chunks;
+};
+
+// Mutable per-instance scalars that live on the device.
+struct InstState {
+  double theta;                   // wall phase
+  double T_wall[3];               // wall torque of the last force evaluation
+  double J_wall[3];               // trapezoidal impulse of T_wall
+  int64_t step;
+  int64_t pad;
+};
+
+// One copy of the sorted FP64 particle state (double-buffered for the reorder).
+// pos.w holds the species code; vel.w and spin.w receive V = m/rho and
+// Pr = P/rho^2 from the density pass so that the pair pass gathers a
+// neighbour with three 32-byte loads.
+struct Fp64Buf {
+  dvec4* pos;         // x, y, z, species
+  dvec4* vel;         // vx, vy, vz, V
+  dvec4* spin;        // wx, wy, wz, Pr
+  dvec2* ref;         // wall reference (phase-0) x, y
+  uint32_t* id;         // input index
+  uint32_t* inst;       // instance index
+};
+
+struct Fp64Fields {
+  dvec4* acc;         // acceleration (w unused)
+  dvec4* dspin;       // spin angular acceleration (w unused)
+  double* rho;
+  double* P;
+  dvec4* tw;          // torque of wall neighbours on each fluid particle
+};
+
+struct CellWs {
+  uint32_t* key;        // global cell of each particle (pre-sort order)
+  uint32_t* slot;       // arrival slot within the cell (atomic order)
+  uint32_t* perm;       // sorted position -> pre-sort index
+  uint32_t* skey;       // key in sorted order
+  uint32_t* count;      // particles per cell
+  uint32_t* start;      // exclusive scan of count, n_cells + 1 entries
+  uint32_t* bsum;       // per-chunk sums of the scan
+  int64_t n_cells;
+  int64_t n_scan_blocks;
+};
+
+struct NbrWs {
+  uint32_t* list;       // [cap][n] column-major neighbour indices (sorted space)
+  uint32_t* count;      // neighbours per particle
+  float4* posf;         // FP32 copy of sorted positions (prefilter)
+  int32_t cap;
+};
+
+}  // namespace sphgb

@@ -1,0 +1,63 @@
+// Host-side launchers of the device kernels (one translation unit each).
+#pragma once
+#include "sph_internal.h"
+
+namespace sphgb {
+
+struct LaunchCfg {
+  int sm_count;          // multiprocessors of the device
+  int block_density;     // threads per block of the density pass
+  int block_forces;      // threads per block of the pair pass
+};
+
+// ---- cell build (sph_cells.cu) --------------------------------------------
+// Exclusive scan of cw.count into cw.start (n_cells + 1 entries).
+cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, int* launches);
+// perm[start[key[i]] + slot[i]] = i, then sort each cell by particle id.
+cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
+                                cudaStream_t s, const LaunchCfg& lc, int* launches);
+
+// ---- FP64 path (sph_fp64.cu) ------------------------------------------------
+// mode 0: initial placement (walls at the current phase, no kick/drift);
+// mode 1: half kick + drift + wall rotation to the next phase.
+cudaError_t launch_kick_drift_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                   const InstDev* inst, const InstState* ist,
+                                   const CellWs& cw, uint32_t* err, int mode,
+                                   cudaStream_t s, const LaunchCfg& lc, int* launches);
+cudaError_t launch_reorder_fp64(int64_t n, const Fp64Buf& src, const Fp64Buf& dst,
+                                const CellWs& cw, const NbrWs& nw, cudaStream_t s,
+                                const LaunchCfg& lc, int* launches);
+cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                                int* launches);
+cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                               const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                               cudaStream_t s, const LaunchCfg& lc, int* launches);
+cudaError_t launch_kick_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                             const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
+                             int* launches);
+// Gather the sorted state back to input order into device arrays (any may be null).
+cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                               double* pos, double* vel, double* spin, double* rho,
+                               double* P, double* acc, double* dspin, cudaStream_t s,
+                               const LaunchCfg& lc);
+// Scatter AoS input (input order) into the sorted-buffer layout (identity order).
+cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
+                             const double* vel, const double* spin, const uint8_t* sp,
+                             const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc);
+
+// ---- FP64 reductions (sph_reduce.cu) -----------------------------------------
+// Per-instance wall torque of the last force pass; then
+// J += dt/2 (T_old + T_new), T = T_new, and (advance) theta += Omega dt, step++.
+cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks,
+                                    const InstDev* inst, InstState* ist,
+                                    const Fp64Buf& b, const Fp64Fields& f,
+                                    double* partials, int advance, cudaStream_t s,
+                                    int* launches);
+// Per-instance diagnostics partials, then final sums into out[n_inst * kDiagFields].
+cudaError_t launch_diag_fp64(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                             const Fp64Buf& b, const Fp64Fields& f, const NbrWs& nw,
+                             double* partials, double* out, cudaStream_t s);
+
+}  // namespace sphgb

@@ -1,0 +1,82 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds for
+sm_103a, loads, exports every function that include/sph.h declares, and its
+host-only sizing/validation logic behaves."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2405_03980_gb300 import _binding as B
+from paper_2405_03980_gb300 import build as Bld
+from paper_2405_03980_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sph.h")).read()
+    return sorted(set(re.findall(r"SPH_API[^;(]*?\b(sph_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    Bld.build()
+    return B.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.exported_symbols()) == names
+
+
+def test_status_strings(lib):
+    for st in range(-9, 1):
+        assert B.sph_status_string(st) != "unknown status"
+
+
+def test_params_default_matches_workload_recipe(lib):
+    p = B.sph_params_default(10.0, 20.0, 0.1)
+    w = synth.workload_params(10.0, 20, 0.1)
+    for k in ("dx", "h", "rho0", "alpha_P", "p0", "beta_P", "eta_bar", "eta_r", "C_l",
+              "C_T", "C_omega", "mass_ratio", "inertia_coef", "Omega", "dt"):
+        assert getattr(p, k) == pytest.approx(w[k], rel=1e-15), k
+    assert list(p.box_lo) == pytest.approx(list(w["box_lo"]))
+    assert list(p.box_hi) == pytest.approx(list(w["box_hi"]))
+
+
+def test_buffer_sizes_scale_and_validate(lib):
+    c = synth.workload("cyl_8960")
+    p = B.params_from_dict(c.params)
+    s1 = B.sph_state_bytes(p, [c.n])
+    w1 = B.sph_workspace_bytes(p, [c.n])
+    assert s1 > 200 * c.n and w1 > 160 * 4 * c.n
+    s2 = B.sph_state_bytes([p, p], [c.n, c.n])
+    assert s2 > 1.9 * s1
+    bad = B.params_from_dict(dict(c.params, h=-1.0))
+    assert B.sph_state_bytes(bad, [c.n]) == 0
+    bad = B.params_from_dict(dict(c.params, alpha_P=7.5))
+    assert B.sph_workspace_bytes(bad, [c.n]) == 0
+    bad = B.params_from_dict(c.params, nbr_cap=8)
+    assert B.sph_workspace_bytes(bad, [c.n]) == 0
+    # a periodic z period shorter than three cells of side 2h is rejected
+    bad = B.params_from_dict(dict(c.params, box_hi=(c.params["box_hi"][0], c.params["box_hi"][1], 6.0)))
+    assert B.sph_state_bytes(bad, [c.n]) == 0
+    # mixed precision within one batch is rejected
+    q = B.params_from_dict(c.params, precision=B.SPH_MIXED)
+    assert B.sph_state_bytes([p, q], [c.n, c.n]) == 0
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
+    c = synth.workload("cyl_8960")
+    p = B.params_from_dict(c.params)
+    ctx = C.c_void_p()
+    # null pointers are rejected before any CUDA call
+    st = lib.sph_init(C.byref(ctx), C.byref(p), c.n, None, None, None, None, None, 0, None, 0, None)
+    assert st == -1 and not ctx.value
+    assert lib.sph_step(None, 1) == -1
+    assert lib.sph_destroy(None) == 0
