@@ -1,0 +1,396 @@
+"""Benchmark: particle-steps/s of the two-fluid spin-SPH step on one GB300.
+
+Default workload: the 20,100,112-particle rotating cylinder (R = 146 dx,
+H = 292 layers, 19.55M fluid + 0.55M wall particles; the 19.6M resolution of
+Sec. 3), synthetic jittered-lattice input (paper_2405_03980_gb300.synth).
+A "step" is one full kick-drift-kick time step: cell keys, counting sort,
+reorder, density + Tait pressure, the fused pair pass, kick, wall-torque
+reduction.  Inputs (~6 GB of state) are far larger than L2 (129 MB), so no L2
+flush is needed between steps.
+
+Forms timed: the FP64 form (and the mixed FP32 form once available); the
+headline `value` is the fastest form that is built.  Under torchrun every rank
+advances its own replica of the cylinder (no exchange: weak scaling).
+
+`--impl reference` times the CPU FP64 oracle (O(N^2), all host cores) on a
+bounded sample of the same workload: a compact cluster of fluid particles
+whose density, pressure and pair forces are evaluated against all N particles.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 19.6M particles"
+UNIT = "particle-steps/s"
+
+# FP64 operations per neighbour pair of the pair pass, counted from the kernel
+# source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
+# work of one force launch is this times the number of fluid neighbour pairs.
+FORCE_FLOPS_PER_PAIR_FP64 = 124
+DENSITY_FLOPS_PER_PAIR_FP64 = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cyl_20100112")
+    ap.add_argument("--forms", default="fp64")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="fluid particles in the oracle sample (0 = size for ~15 s)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(c, target_s: float = 15.0, n_sample: int = 0):
+    """Bounded oracle sample: a compact cluster S of fluid particles near
+    mid-radius and every particle R within 2h (+1 dx) of its bounding box.
+    One sample step = oracle density+pressure for R and pair forces for S,
+    each evaluated against all N particles (the oracle is O(N) per row)."""
+    import oracle
+    p = oracle.make_params(c.params)
+    fluid = np.nonzero(c.species < 2)[0]
+    centre = np.array([0.5 * c.R, 0.0, 0.5 * c.H])
+    d = np.abs(c.pos[fluid] - centre).max(1)
+    order = fluid[np.argsort(d, kind="stable")]
+
+    def rows_for(k):
+        S = np.sort(order[:k])
+        lo = c.pos[S].min(0) - (2 * p.h + 1.0)
+        hi = c.pos[S].max(0) + (2 * p.h + 1.0)
+        inside = np.all((c.pos >= lo) & (c.pos <= hi), axis=1)
+        return S, np.nonzero(inside)[0]
+
+    def run(S, R):
+        t = time.perf_counter()
+        rho, P = oracle.density(p, c.pos, c.species, rows=R)
+        oracle.forces(p, c.pos, c.vel, c.spin, c.species, rho, P, rows=S)
+        return time.perf_counter() - t
+
+    if n_sample:
+        S, R = rows_for(n_sample)
+        return p, S, R, run, run(S, R)
+    # calibrate the cost per evaluated row on a small cluster, then size the
+    # cluster so that one sample step costs about target_s seconds
+    S, R = rows_for(32)
+    t = run(S, R)
+    rows_per_s = len(R) / max(t, 1e-4)
+    want = target_s * rows_per_s
+    k = 32
+    while k < len(order):
+        k2 = min(len(order), int(k * 1.5) + 1)
+        _, R2 = rows_for(k2)
+        if len(R2) > want:
+            break
+        k = k2
+    S, R = rows_for(k)
+    t = run(S, R)
+    return p, S, R, run, t
+
+
+def cores_used() -> int:
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    return int(os.environ.get("OMP_NUM_THREADS", n))
+
+
+def cpu_baseline(c, n_sample=0):
+    _, S, R, run, _t = oracle_sample(c, target_s=10.0, n_sample=n_sample)
+    t = min(run(S, R) for _ in range(2))
+    return {"value": len(S) / t, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+            "sample": (f"{len(S)} fluid particles of the {c.n}-particle cylinder: oracle "
+                       f"density+pressure for the {len(R)} particles within 2h of them and "
+                       f"pair forces for the {len(S)}, each against all {c.n} particles "
+                       f"(O(N) per row); best of 2, {t:.2f} s per sample step")}
+
+
+def run_reference(args, dist):
+    from paper_2405_03980_gb300 import synth
+    if dist.rank != 0:
+        return
+    c = synth.workload(args.workload)
+    target = min(10.0, max(1.0, 90.0 / max(1, args.steps + args.warmup)))
+    _, S, R, run, _ = oracle_sample(c, target_s=target, n_sample=args.cpu_sample)
+    for _ in range(args.warmup):
+        run(S, R)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run(S, R)
+    dt = time.perf_counter() - t0
+    v = len(S) * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": c.n,
+                       "sample_particles": int(len(S)), "sample_rows": int(len(R)),
+                       "l2": "inputs larger than L2 (not applicable on CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": cores_used(),
+                             "sample": f"{len(S)} of {c.n} particles per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def time_form(c, precision, args, dist, dev):
+    import torch
+    from paper_2405_03980_gb300 import _binding as B
+    from paper_2405_03980_gb300.sim import Simulation
+
+    sim = Simulation(c, precision=precision, device=f"cuda:{dev}")
+    stream = sim.stream
+    sim.step(args.warmup)
+    sim.check()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    ck = clocks.stop()
+    sim.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = dist.max(ms)
+    diag = sim.diagnostics()
+    stages = sim.profile(args.profile_steps)
+    launches = sim.launches_per_step()
+    out = {"ms_per_step": ms, "diag": diag, "stages": stages, "clocks": ck,
+           "launches_per_step": launches, "sim": sim}
+    return out
+
+
+def e2e_buffers(c):
+    """Pinned host copies of the inputs and of the state read back."""
+    import torch
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t
+
+    pos, vel, spin = pinned(c.pos), pinned(c.vel), pinned(c.spin)
+    sp = pinned(c.species)
+    out_pos, out_vel, out_spin = (torch.empty((c.n, 3), dtype=torch.float64).pin_memory()
+                                  for _ in range(3))
+    return pos, vel, spin, sp, out_pos, out_vel, out_spin
+
+
+def run_ours(args, dist):
+    import torch
+    from paper_2405_03980_gb300 import _binding as B
+    from paper_2405_03980_gb300 import synth
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    B.lib(build_if_missing=True)
+    c = synth.workload(args.workload, seed=0)
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    prec = {"fp64": B.SPH_FP64, "mixed": B.SPH_MIXED}
+    results = {}
+    for f in forms:
+        results[f] = time_form(c, prec[f], args, dist, dev)
+    best = min(results, key=lambda f: results[f]["ms_per_step"])
+    r = results[best]
+    n_total = c.n * dist.world
+    value = n_total / (r["ms_per_step"] * 1e-3)
+    pairs = r["diag"]["n_pairs"]
+
+    # roofline of the dominant kernel (the pair pass), timed with CUDA events
+    # on the library's stream inside the profiled steps
+    st = r["stages"]
+    dom = max(st, key=st.get)
+    peak64 = B.sph_fma_peak(B.SPH_FP64, 1 << 15)
+    t_forces = st["forces"] * 1e-3
+    achieved = FORCE_FLOPS_PER_PAIR_FP64 * pairs / t_forces / 1e12
+    roof = {"kernel": "k_forces_fp64", "bound": "alu", "achieved": achieved, "peak": peak64,
+            "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": None,
+            "peak_source": "measured FP64 FMA-chain rate (sph_fma_peak)",
+            "work": f"{FORCE_FLOPS_PER_PAIR_FP64} FP64 flop x {pairs} fluid neighbour pairs"}
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        sim = r["sim"]
+        pos, vel, spin, sp, opos, ovel, ospin = e2e_buffers(c)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim.reinit(pos, vel, spin, sp)
+        for _ in range(args.steps):
+            sim.step(1)
+            sim.diagnostics()
+        B.sph_get_state(sim.ctx, opos, ovel, ospin)
+        t = time.perf_counter() - t0
+        t = dist.max(t)
+        h2d = c.n * (3 * 3 * 8 + 1)
+        d2h = args.steps * 8 * 33 + c.n * 3 * 3 * 8
+        e2e = {"value": n_total * args.steps / t, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "sph_init from pinned host state (initial density+forces), "
+                           "K x (sph_step + sph_diagnostics read-back), sph_get_state"}
+    for f in results:
+        results[f]["sim"].close()
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(c, n_sample=args.cpu_sample)
+
+    if dist.rank == 0:
+        forms_out = {f: {"ms_per_step": results[f]["ms_per_step"],
+                         "particle_steps_per_s": n_total / (results[f]["ms_per_step"] * 1e-3),
+                         "pair_interactions_per_s":
+                             results[f]["diag"]["n_pairs"] * dist.world /
+                             (results[f]["ms_per_step"] * 1e-3),
+                         "stage_ms": results[f]["stages"]} for f in results}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if best == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "particles": c.n, "fluid": c.n_fluid,
+                       "R": c.R, "H": c.H, "form": best, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (~6 GB state), no flush"},
+            "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
+            "forms": forms_out,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": r["clocks"],
+            "gpu_launches": r["launches_per_step"] * args.steps,
+            "dominant_stage": dom,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        # the CPU oracle runs on rank 0 only; other ranks exit without work
+        run_reference(args, dist)
+        return
+    dist.init("nccl")
+    try:
+        run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

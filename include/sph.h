@@ -188,8 +188,22 @@ SPH_API sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* offsets, int64_t* nb
 /* Synchronise and return the latched device error, if any. */
 SPH_API sph_status sph_check(sph_ctx* ctx);
 
+/* Run nsteps steps eagerly (without the graph) and time each stage with CUDA
+ * events on the context's stream; stage_ms[k] receives the mean milliseconds
+ * per step of stage k (n_stages >= sph_stage_count()).  The state advances
+ * exactly as with sph_step.  Synchronises. */
+SPH_API sph_status sph_profile_steps(sph_ctx* ctx, int32_t nsteps, double* stage_ms,
+                                     int32_t n_stages);
+SPH_API int32_t sph_stage_count(void);
+SPH_API const char* sph_stage_name(int32_t stage);
+
 /* Number of kernel launches one sph_step(ctx, 1) enqueues. */
 SPH_API int32_t sph_launches_per_step(const sph_ctx* ctx);
+
+/* Measure the device's FP64 (SPH_FP64) or FP32 (SPH_MIXED) FMA throughput in
+ * TFLOP/s with independent dependent-FMA chains (iters FMAs per chain, >= 64):
+ * the pipe peak against which the pair passes are reported.  Synchronises. */
+SPH_API sph_status sph_fma_peak(int32_t precision, int32_t iters, double* tflops);
 
 /* Release the context (host memory, graphs, internal stream).  The caller
  * frees its own device buffers afterwards. */

@@ -400,13 +400,15 @@ void orc_diagnostics(const orc_params* p, int64_t n, const double* pos,
   }
   int64_t pairs = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : pairs)
-  for (int64_t i = 0; i < n; ++i)
+  for (int64_t i = 0; i < n; ++i) {
+    if (species[i] >= 2) continue; /* pairs of the fluid rows (force pass) */
     for (int64_t j = 0; j < n; ++j) {
       if (j == i) continue;
       double d[3];
       orc_pair_delta(p, pos + 3 * i, pos + 3 * j, d);
       if (norm2(d) < c2) ++pairs;
     }
+  }
   out->n_pairs = pairs;
   for (int a = 0; a < 3; ++a) {
     out->T_wall[a] = T_wall_sum ? T_wall_sum[a] : 0.0;

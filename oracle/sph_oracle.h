@@ -63,7 +63,7 @@ typedef struct {
   double T_wall[3];                /* torque of the walls on the fluid now     */
   double J_wall[3];                /* time integral of T_wall                  */
   double rho_min, rho_max, v_max;
-  int64_t n_pairs;                 /* ordered neighbour pairs (i != j)         */
+  int64_t n_pairs;                 /* ordered pairs (i fluid, j != i, r < 2h)  */
 } orc_diag;
 
 /* Wendland C2 kernel W(r) and F(r) = -(1/r) dW/dr, support 2h. */

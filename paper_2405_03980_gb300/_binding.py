@@ -91,6 +91,10 @@ def lib(build_if_missing: bool = True):
                 "sph_get_neighbors": (C.c_int, [vp, i64p, i64p, C.c_int64]),
                 "sph_check": (C.c_int, [vp]),
                 "sph_launches_per_step": (C.c_int32, [vp]),
+                "sph_profile_steps": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.c_int32]),
+                "sph_stage_count": (C.c_int32, []),
+                "sph_stage_name": (C.c_char_p, [C.c_int32]),
+                "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_destroy": (C.c_int, [vp]),
                 "sph_status_string": (C.c_char_p, [C.c_int]),
             }
@@ -107,7 +111,8 @@ def exported_symbols() -> list[str]:
     return ["sph_params_default", "sph_state_bytes", "sph_workspace_bytes", "sph_init",
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_get_state", "sph_get_neighbors", "sph_check",
-            "sph_launches_per_step", "sph_destroy", "sph_status_string"]
+            "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
+            "sph_fma_peak", "sph_destroy", "sph_status_string"]
 
 
 def _ck(st: int, where: str):
@@ -240,6 +245,19 @@ def sph_check(ctx):
 
 def sph_launches_per_step(ctx) -> int:
     return int(lib().sph_launches_per_step(ctx))
+
+
+def sph_profile_steps(ctx, nsteps: int) -> dict:
+    k = int(lib().sph_stage_count())
+    ms = (C.c_double * k)()
+    _ck(lib().sph_profile_steps(ctx, int(nsteps), ms, k), "sph_profile_steps")
+    return {lib().sph_stage_name(i).decode(): ms[i] for i in range(k)}
+
+
+def sph_fma_peak(precision: int, iters: int = 1 << 16) -> float:
+    t = C.c_double()
+    _ck(lib().sph_fma_peak(int(precision), int(iters), C.byref(t)), "sph_fma_peak")
+    return t.value
 
 
 def sph_destroy(ctx):

@@ -280,42 +280,69 @@ sph_status decode_err(uint32_t e) {
 
 // ---- pipeline pieces (enqueue only) -----------------------------------------
 
-sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches) {
+// Optional stage markers: an event is recorded before each stage and after
+// the last one, so that consecutive events bracket one stage.
+struct Marks {
+  cudaEvent_t* ev = nullptr;
+  int k = 0;
+};
+
+inline void mark(Marks* m, cudaStream_t s) {
+  if (m) cudaEventRecord(m->ev[m->k++], s);
+}
+
+constexpr int kStages = 8;
+const char* const kStageNames[kStages] = {"kick_drift_keys", "cell_scan", "scatter_cell_sort",
+                                          "reorder",         "density",   "forces",
+                                          "kick",            "wall_torque"};
+
+sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
+                         Marks* m = nullptr) {
   const Fp64Buf& src = c->buf[c->cur];
   const Fp64Buf& dst = c->buf[1 - c->cur];
+  mark(m, s);
   CK(cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s));
   CK(launch_kick_drift_fp64(c->n, src, c->f, c->inst, c->ist, c->cw, c->err, mode, s, c->lc,
                             launches));
+  mark(m, s);
   CK(launch_scan(c->cw, s, launches));
+  mark(m, s);
   CK(launch_scatter_sort(c->cw, src.id, c->n, s, c->lc, launches));
+  mark(m, s);
   CK(launch_reorder_fp64(c->n, src, dst, c->cw, c->nw, s, c->lc, launches));
   return SPH_OK;
 }
 
-sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches) {
+sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
+  mark(m, s);
   CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
                          launches));
   c->lists_valid = true;
   return SPH_OK;
 }
 
-sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches) {
+sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches,
+                          Marks* m = nullptr) {
+  mark(m, s);
   CK(launch_forces_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->nw, c->err, s, c->lc,
                         launches));
+  mark(m, s);
   if (advance) CK(launch_kick_fp64(c->n, c->buf[c->cur], c->f, c->inst, s, c->lc, launches));
+  mark(m, s);
   CK(launch_wall_torque_fp64(c->n_inst, c->total_chunks, c->inst, c->ist, c->buf[c->cur], c->f,
                              c->part_tw, advance, s, launches));
+  mark(m, s);
   return SPH_OK;
 }
 
 // One kick-drift-kick step; flips c->cur (the reorder target becomes current).
-sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches) {
-  sph_status st = enqueue_cells(c, s, 1, launches);
+sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
+  sph_status st = enqueue_cells(c, s, 1, launches, m);
   if (st != SPH_OK) return st;
   c->cur = 1 - c->cur;
-  st = enqueue_density(c, s, launches);
+  st = enqueue_density(c, s, launches, m);
   if (st != SPH_OK) return st;
-  return enqueue_forces(c, s, 1, launches);
+  return enqueue_forces(c, s, 1, launches, m);
 }
 
 sph_status capture_graphs(sph_ctx* c) {
@@ -679,6 +706,45 @@ sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t
     for (size_t t = 0; t < tmp.size(); ++t) nbr[offsets[o] + (int64_t)t] = tmp[t];
   }
   return st;
+}
+
+sph_status sph_profile_steps(sph_ctx* c, int32_t nsteps, double* stage_ms, int32_t n_stages) {
+  if (!c || nsteps < 1 || !stage_ms || n_stages < kStages) return SPH_ERR_ARG;
+  if (!c->forces_valid) {
+    sph_status st = enqueue_density(c, c->stream, nullptr);
+    if (st == SPH_OK) st = enqueue_forces(c, c->stream, 0, nullptr);
+    if (st != SPH_OK) return st;
+    c->forces_valid = true;
+  }
+  std::vector<cudaEvent_t> ev((size_t)nsteps * (kStages + 1), nullptr);
+  sph_status st = SPH_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) st = SPH_ERR_CUDA;
+  for (int32_t t = 0; t < nsteps && st == SPH_OK; ++t) {
+    Marks m;
+    m.ev = ev.data() + (size_t)t * (kStages + 1);
+    st = enqueue_step(c, c->stream, nullptr, &m);
+  }
+  if (st == SPH_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = SPH_ERR_CUDA;
+  for (int k = 0; k < n_stages; ++k) stage_ms[k] = 0.0;
+  for (int32_t t = 0; t < nsteps && st == SPH_OK; ++t)
+    for (int k = 0; k < kStages; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[(size_t)t * (kStages + 1) + k],
+                               ev[(size_t)t * (kStages + 1) + k + 1]) != cudaSuccess)
+        st = SPH_ERR_CUDA;
+      stage_ms[k] += ms / nsteps;
+    }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st != SPH_OK) return st;
+  return sph_check(c);
+}
+
+int32_t sph_stage_count(void) { return kStages; }
+
+const char* sph_stage_name(int32_t stage) {
+  return (stage >= 0 && stage < kStages) ? kStageNames[stage] : "";
 }
 
 int32_t sph_launches_per_step(const sph_ctx* c) { return c ? c->launches_per_step : 0; }

@@ -39,12 +39,20 @@ class Simulation:
         self.ws_bytes = B.sph_workspace_bytes(self.params, self.counts)
         if self.state_bytes == 0 or self.ws_bytes == 0:
             raise B.SphError(-1, "sph_state_bytes/sph_workspace_bytes")
+        self.ctx = None
         with torch.cuda.device(self.device):
             self.state = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
             self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.ctx = B.sph_init_batch(self.params, self.counts, pos, vel, spin, sp, self.state,
-                                        self.state_bytes, self.ws, self.ws_bytes,
+        self.reinit(pos, vel, spin, sp)
+
+    def reinit(self, pos, vel, spin, species):
+        """(Re)initialise on the already-allocated device buffers from arrays in
+        input order (numpy / pinned host memory or device tensors)."""
+        self.close()
+        with self.torch.cuda.device(self.device):
+            self.ctx = B.sph_init_batch(self.params, self.counts, pos, vel, spin, species,
+                                        self.state, self.state_bytes, self.ws, self.ws_bytes,
                                         self.stream.cuda_stream)
 
     # -- stepping ---------------------------------------------------------
@@ -78,6 +86,9 @@ class Simulation:
 
     def neighbors(self):
         return B.sph_get_neighbors(self.ctx, self.n)
+
+    def profile(self, nsteps: int) -> dict:
+        return B.sph_profile_steps(self.ctx, nsteps)
 
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)

@@ -82,7 +82,8 @@ def test_initial_evaluation_matches_oracle():
     print("t=0 errors", errs)
     d = sim.diagnostics()
     od = o.diagnostics()
-    assert d["mass"] == pytest.approx(od["mass"], rel=1e-14)
+    # FP64 sums over 6,320 fluid particles in another order: 1e-12 relative
+    assert d["mass"] == pytest.approx(od["mass"], rel=1e-12)
     assert d["n_pairs"] == od["n_pairs"]
     for k in ("E_kin", "E_int"):
         assert d[k] == pytest.approx(od[k], rel=1e-12)
@@ -113,7 +114,7 @@ def test_ten_steps_match_oracle():
     od = o.diagnostics()
     assert d["step"] == 10
     assert d["theta"] == pytest.approx(o.theta.value, rel=0, abs=0)
-    assert d["mass"] == pytest.approx(od["mass"], rel=1e-14)
+    assert d["mass"] == pytest.approx(od["mass"], rel=1e-12)
     for a in range(3):
         assert d["L_orb"][a] + d["L_spin"][a] == pytest.approx(
             od["L_orb"][a] + od["L_spin"][a], rel=1e-11, abs=1e-9)
