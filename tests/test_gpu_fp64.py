@@ -196,16 +196,18 @@ def test_rerun_is_deterministic():
 
 def test_device_errors_are_latched_not_trapped():
     c = synth.workload("cyl_8960")
-    # a particle far outside the cell grid: clamped, reported as escaped
+    fluid = np.nonzero(c.species < 2)[0]
+    # a fluid particle far outside the cell grid: clamped, reported as escaped
     pos = c.pos.copy()
-    pos[5] = [1e3, 0.0, 1.0]
+    pos[fluid[5]] = [1e3, 0.0, 1.0]
     bad = synth.Cylinder(**{**c.__dict__, "pos": pos})
     with pytest.raises(B.SphError) as e:
         sim_of(bad)
     assert e.value.status == -5
-    # a NaN velocity: reported as non-finite after the next step
+    # a NaN velocity of a fluid particle: reported as non-finite (the initial
+    # force evaluation already propagates it)
     vel = c.vel.copy()
-    vel[7, 1] = np.nan
+    vel[fluid[7], 1] = np.nan
     bad = synth.Cylinder(**{**c.__dict__, "vel": vel})
     sim = None
     with pytest.raises(B.SphError) as e:
