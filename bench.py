@@ -38,8 +38,7 @@ UNIT = "particle-steps/s"
 # FP64 operations per neighbour pair of the pair pass, counted from the kernel
 # source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
 # work of one force launch is this times the number of fluid neighbour pairs.
-FORCE_FLOPS_PER_PAIR_FP64 = 124
-DENSITY_FLOPS_PER_PAIR_FP64 = 20
+FORCE_FLOPS_PER_PAIR = {"fp64": 124, "mixed": 142}   # mixed adds Kahan and cell offsets
 
 
 def parse():
@@ -49,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cyl_20100112")
-    ap.add_argument("--forms", default="fp64")
+    ap.add_argument("--forms", default="mixed,fp64")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -315,13 +314,23 @@ def run_ours(args, dist):
     # on the library's stream inside the profiled steps
     st = r["stages"]
     dom = max(st, key=st.get)
-    peak64 = B.sph_fma_peak(B.SPH_FP64, 1 << 15)
-    t_forces = st["forces"] * 1e-3
-    achieved = FORCE_FLOPS_PER_PAIR_FP64 * pairs / t_forces / 1e12
-    roof = {"kernel": "k_forces_fp64", "bound": "alu", "achieved": achieved, "peak": peak64,
-            "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": None,
-            "peak_source": "measured FP64 FMA-chain rate (sph_fma_peak)",
-            "work": f"{FORCE_FLOPS_PER_PAIR_FP64} FP64 flop x {pairs} fluid neighbour pairs"}
+    peaks = {"fp64": B.sph_fma_peak(B.SPH_FP64, 1 << 15),
+             "mixed": B.sph_fma_peak(B.SPH_MIXED, 1 << 20)}
+    roofs = {}
+    for f in results:
+        t_forces = results[f]["stages"]["forces"] * 1e-3
+        fpp = FORCE_FLOPS_PER_PAIR[f]
+        pr = results[f]["diag"]["n_pairs"]
+        ach = fpp * pr / t_forces / 1e12
+        roofs[f] = {"kernel": f"k_forces_{f}", "bound": "alu", "achieved": ach,
+                    "peak": peaks[f], "unit": "TFLOP/s", "frac": ach / peaks[f],
+                    "traffic": None,
+                    "peak_source": ("measured FP64" if f == "fp64" else "measured FP32")
+                    + " FMA-chain rate of this GPU (sph_fma_peak), of measured",
+                    "work": f"{fpp} {'FP64' if f == 'fp64' else 'FP32'} flop x {pr} "
+                            "fluid neighbour pairs per launch",
+                    "launch_ms": results[f]["stages"]["forces"]}
+    roof = roofs[best]
 
     # end-to-end through the C ABI with host buffers
     e2e = None
@@ -369,6 +378,7 @@ def run_ours(args, dist):
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,
             "roofline": roof,
+            "roofline_by_form": roofs,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": r["clocks"],

@@ -128,6 +128,42 @@ sph_status derive(const sph_params& p, InstDev& d) {
   const double margin = 4.0 * (2.0 * sqrt(3.0) * side * eps + 3.0 * eps * eps +
                                6.0 * d.cut2 * ldexp(1.0, -24));
   d.cut2f_margin = nextafterf((float)(d.cut2 + margin), INFINITY);
+
+  // FP32 constants of the mixed form
+  if (p.precision == SPH_MIXED &&
+      (d.nx > (1 << kCellBitsX) || d.ny > (1 << kCellBitsY) || d.nz > (1 << kCellBitsZ)))
+    return SPH_ERR_GRID_OVERFLOW;
+  for (int a = 0; a < 3; ++a) d.cellf[a] = (float)d.cell[a];
+  d.cut2_f = (float)d.cut2;
+  d.inv_h_f = (float)d.inv_h;
+  d.aD_f = (float)d.aD;
+  d.cF_f = (float)d.cF;
+  const double m[2] = {d.m_s, d.m_n};
+  const double invI[2] = {d.inv_I_s, d.inv_I_n};
+  for (int k = 0; k < 2; ++k) {
+    d.m_f[k] = (float)m[k];
+    d.mr_f[k] = (float)(m[k] / p.rho0);
+    d.inv_m_f[k] = (float)(1.0 / m[k]);
+    d.inv_I_f[k] = (float)invI[k];
+    const double self = m[k] * d.aD / p.rho0 - 1.0;
+    d.self_hi[k] = (float)self;
+    d.self_lo[k] = (float)(self - (double)d.self_hi[k]);
+  }
+  d.p0_f = (float)p.p0;
+  d.p0mb_f = (float)(p.p0 - p.beta_P);
+  double binom = 1.0;
+  for (int k = 0; k <= 16; ++k) {
+    d.binom[k] = (k <= d.alphaP) ? (float)binom : 0.f;
+    binom = binom * (double)(d.alphaP - k) / (double)(k + 1);
+  }
+  d.rho0_f = (float)p.rho0;
+  d.A_f = (float)d.A;
+  d.B_f = (float)d.B;
+  d.C_l_f = (float)p.C_l;
+  d.C_T_f = (float)p.C_T;
+  d.dt_f = (float)p.dt;
+  d.hdt_f = (float)(0.5 * p.dt);
+  d.Omega_f = (float)p.Omega;
   return SPH_OK;
 }
 
@@ -142,9 +178,11 @@ struct sph_ctx {
   InstDev* inst = nullptr;
   InstState* ist = nullptr;
   uint32_t* err = nullptr;
-  Fp64Buf buf[2];
-  int cur = 0;
+  Fp64Buf buf[2];    // FP64 form
   Fp64Fields f;
+  MixBuf mbuf[2];    // mixed form
+  MixFields mf;
+  int cur = 0;
   CellWs cw;
   NbrWs nw;
   int64_t total_chunks = 0;
@@ -167,6 +205,8 @@ namespace {
 struct Carved {
   Fp64Buf buf[2];
   Fp64Fields f;
+  MixBuf mbuf[2];
+  MixFields mf;
   CellWs cw;
   NbrWs nw;
   InstDev* inst;
@@ -177,24 +217,42 @@ struct Carved {
 };
 
 void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
-           int64_t total_chunks, int32_t cap, Carved& c) {
+           int64_t total_chunks, int32_t cap, int32_t precision, Carved& c) {
+  memset(&c, 0, sizeof c);
   Carver s(state);
   c.inst = s.take<InstDev>(n_inst);
   c.ist = s.take<InstState>(n_inst);
   c.err = s.take<uint32_t>(4);
-  for (int b = 0; b < 2; ++b) {
-    c.buf[b].pos = s.take<dvec4>(n);
-    c.buf[b].vel = s.take<dvec4>(n);
-    c.buf[b].spin = s.take<dvec4>(n);
-    c.buf[b].ref = s.take<dvec2>(n);
-    c.buf[b].id = s.take<uint32_t>(n);
-    c.buf[b].inst = s.take<uint32_t>(n);
+  if (precision == SPH_FP64) {
+    for (int b = 0; b < 2; ++b) {
+      c.buf[b].pos = s.take<dvec4>(n);
+      c.buf[b].vel = s.take<dvec4>(n);
+      c.buf[b].spin = s.take<dvec4>(n);
+      c.buf[b].ref = s.take<dvec2>(n);
+      c.buf[b].id = s.take<uint32_t>(n);
+      c.buf[b].inst = s.take<uint32_t>(n);
+    }
+    c.f.acc = s.take<dvec4>(n);
+    c.f.dspin = s.take<dvec4>(n);
+    c.f.tw = s.take<dvec4>(n);
+    c.f.rho = s.take<double>(n);
+    c.f.P = s.take<double>(n);
+  } else {
+    for (int b = 0; b < 2; ++b) {
+      c.mbuf[b].cell = s.take<uint32_t>(n);
+      c.mbuf[b].off = s.take<float4>(n);
+      c.mbuf[b].vel = s.take<float4>(n);
+      c.mbuf[b].spin = s.take<float4>(n);
+      c.mbuf[b].ref = s.take<dvec2>(n);
+      c.mbuf[b].id = s.take<uint32_t>(n);
+      c.mbuf[b].inst = s.take<uint32_t>(n);
+    }
+    c.mf.acc = s.take<float4>(n);
+    c.mf.dspin = s.take<float4>(n);
+    c.mf.tw = s.take<float4>(n);
+    c.mf.delta = s.take<float>(n);
+    c.mf.P = s.take<float>(n);
   }
-  c.f.acc = s.take<dvec4>(n);
-  c.f.dspin = s.take<dvec4>(n);
-  c.f.tw = s.take<dvec4>(n);
-  c.f.rho = s.take<double>(n);
-  c.f.P = s.take<double>(n);
   c.state_bytes = s.off + kAlign;
 
   Carver w(ws);
@@ -209,7 +267,7 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.cw.bsum = w.take<uint32_t>(c.cw.n_scan_blocks + 1);
   c.nw.list = w.take<uint32_t>((int64_t)cap * n);
   c.nw.count = w.take<uint32_t>(n);
-  c.nw.posf = w.take<float4>(n);
+  c.nw.posf = precision == SPH_FP64 ? w.take<float4>(n) : nullptr;
   c.nw.cap = cap;
   c.part_tw = w.take<double>(3 * total_chunks);
   c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
@@ -296,41 +354,67 @@ const char* const kStageNames[kStages] = {"kick_drift_keys", "cell_scan", "scatt
                                           "reorder",         "density",   "forces",
                                           "kick",            "wall_torque"};
 
+bool mixed(const sph_ctx* c) { return c->precision == SPH_MIXED; }
+
 sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
                          Marks* m = nullptr) {
-  const Fp64Buf& src = c->buf[c->cur];
-  const Fp64Buf& dst = c->buf[1 - c->cur];
+  const int a = c->cur, b = 1 - c->cur;
   mark(m, s);
   CK(cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s));
-  CK(launch_kick_drift_fp64(c->n, src, c->f, c->inst, c->ist, c->cw, c->err, mode, s, c->lc,
-                            launches));
+  if (mixed(c))
+    CK(launch_kick_drift_mixed(c->n, c->mbuf[a], c->mf, c->inst, c->ist, c->cw, c->err, mode, s,
+                               c->lc, launches));
+  else
+    CK(launch_kick_drift_fp64(c->n, c->buf[a], c->f, c->inst, c->ist, c->cw, c->err, mode, s,
+                              c->lc, launches));
   mark(m, s);
   CK(launch_scan(c->cw, s, launches));
   mark(m, s);
-  CK(launch_scatter_sort(c->cw, src.id, c->n, s, c->lc, launches));
+  CK(launch_scatter_sort(c->cw, mixed(c) ? c->mbuf[a].id : c->buf[a].id, c->n, s, c->lc,
+                         launches));
   mark(m, s);
-  CK(launch_reorder_fp64(c->n, src, dst, c->cw, c->nw, s, c->lc, launches));
+  if (mixed(c))
+    CK(launch_reorder_mixed(c->n, c->mbuf[a], c->mbuf[b], c->cw, s, c->lc, launches));
+  else
+    CK(launch_reorder_fp64(c->n, c->buf[a], c->buf[b], c->cw, c->nw, s, c->lc, launches));
   return SPH_OK;
 }
 
 sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
   mark(m, s);
-  CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
-                         launches));
+  if (mixed(c))
+    CK(launch_density_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->cw, c->nw, c->err, s,
+                            c->lc, launches));
+  else
+    CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
+                           launches));
   c->lists_valid = true;
   return SPH_OK;
 }
 
 sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches,
                           Marks* m = nullptr) {
+  const int k = c->cur;
   mark(m, s);
-  CK(launch_forces_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->nw, c->err, s, c->lc,
-                        launches));
+  if (mixed(c))
+    CK(launch_forces_mixed(c->n, c->mbuf[k], c->mf, c->inst, c->nw, c->err, s, c->lc,
+                           launches));
+  else
+    CK(launch_forces_fp64(c->n, c->buf[k], c->f, c->inst, c->nw, c->err, s, c->lc, launches));
   mark(m, s);
-  if (advance) CK(launch_kick_fp64(c->n, c->buf[c->cur], c->f, c->inst, s, c->lc, launches));
+  if (advance) {
+    if (mixed(c))
+      CK(launch_kick_mixed(c->n, c->mbuf[k], c->mf, c->inst, s, c->lc, launches));
+    else
+      CK(launch_kick_fp64(c->n, c->buf[k], c->f, c->inst, s, c->lc, launches));
+  }
   mark(m, s);
-  CK(launch_wall_torque_fp64(c->n_inst, c->total_chunks, c->inst, c->ist, c->buf[c->cur], c->f,
-                             c->part_tw, advance, s, launches));
+  if (mixed(c))
+    CK(launch_wall_torque_mixed(c->n_inst, c->total_chunks, c->inst, c->ist, c->mbuf[k], c->mf,
+                                c->part_tw, advance, s, launches));
+  else
+    CK(launch_wall_torque_fp64(c->n_inst, c->total_chunks, c->inst, c->ist, c->buf[k], c->f,
+                               c->part_tw, advance, s, launches));
   mark(m, s);
   return SPH_OK;
 }
@@ -430,7 +514,7 @@ size_t sph_state_bytes(int32_t n_inst, const sph_params* params, const int64_t* 
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision, c);
   return c.state_bytes;
 }
 
@@ -438,7 +522,7 @@ size_t sph_workspace_bytes(int32_t n_inst, const sph_params* params, const int64
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision, c);
   return c.ws_bytes;
 }
 
@@ -453,11 +537,11 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   Plan pl;
   sph_status st = plan(n_inst, params, counts, pl);
   if (st != SPH_OK) return st;
-  if (pl.precision != SPH_FP64) return SPH_ERR_ARG;  // mixed form: separate entry
   if (((uintptr_t)dev_state % kAlign) || ((uintptr_t)dev_workspace % kAlign))
     return SPH_ERR_WORKSPACE;
   Carved cv;
-  carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, cv);
+  carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
+        cv);
   if (state_bytes < cv.state_bytes || workspace_bytes < cv.ws_bytes) return SPH_ERR_WORKSPACE;
 
   sph_ctx* c = new (std::nothrow) sph_ctx();
@@ -473,6 +557,9 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->buf[0] = cv.buf[0];
   c->buf[1] = cv.buf[1];
   c->f = cv.f;
+  c->mbuf[0] = cv.mbuf[0];
+  c->mbuf[1] = cv.mbuf[1];
+  c->mf = cv.mf;
   c->cw = cv.cw;
   c->nw = cv.nw;
   c->total_chunks = pl.total_chunks;
@@ -529,10 +616,16 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   if (cudaMemsetAsync(c->ist, 0, sizeof(InstState) * n_inst, s) != cudaSuccess ||
       cudaMemsetAsync(c->err, 0, sizeof(uint32_t) * 4, s) != cudaSuccess)
     return fail(SPH_ERR_CUDA);
-  if (launch_load_fp64(n, c->buf[0], (const double*)dpos, (const double*)dvel,
-                       (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst, s,
-                       c->lc) != cudaSuccess)
-    return fail(SPH_ERR_CUDA);
+  cudaError_t le;
+  if (mixed(c))
+    le = launch_load_mixed(n, c->mbuf[0], c->inst, (const double*)dpos, (const double*)dvel,
+                           (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst,
+                           c->err, s, c->lc);
+  else
+    le = launch_load_fp64(n, c->buf[0], (const double*)dpos, (const double*)dvel,
+                          (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst, s,
+                          c->lc);
+  if (le != cudaSuccess) return fail(SPH_ERR_CUDA);
   c->cur = 0;
   // initial evaluation: walls at phase 0, cells, density, forces (a_0, alpha_0)
   if ((st = enqueue_cells(c, s, 0, nullptr)) != SPH_OK) return fail(st);
@@ -611,8 +704,12 @@ sph_status sph_check(sph_ctx* c) {
 
 sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
   if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
-  CK(launch_diag_fp64(c->n_inst, c->total_chunks, c->inst, c->buf[c->cur], c->f, c->nw,
-                      c->part_diag, c->diag_out, c->stream));
+  if (mixed(c))
+    CK(launch_diag_mixed(c->n_inst, c->total_chunks, c->inst, c->mbuf[c->cur], c->mf, c->nw,
+                         c->part_diag, c->diag_out, c->stream));
+  else
+    CK(launch_diag_fp64(c->n_inst, c->total_chunks, c->inst, c->buf[c->cur], c->f, c->nw,
+                        c->part_diag, c->diag_out, c->stream));
   double d[kDiagFields];
   InstState s;
   CK(cudaMemcpyAsync(d, c->diag_out + (int64_t)inst * kDiagFields, sizeof d,
@@ -663,8 +760,12 @@ sph_status sph_get_state(sph_ctx* c, double* pos, double* vel, double* spin, dou
       off += bytes;
     }
   }
-  CK(launch_unsort_fp64(n, c->buf[c->cur], c->f, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
-                        dev[6], c->stream, c->lc));
+  if (mixed(c))
+    CK(launch_unsort_mixed(n, c->mbuf[c->cur], c->mf, c->inst, dev[0], dev[1], dev[2], dev[3],
+                           dev[4], dev[5], dev[6], c->stream, c->lc));
+  else
+    CK(launch_unsort_fp64(n, c->buf[c->cur], c->f, dev[0], dev[1], dev[2], dev[3], dev[4],
+                          dev[5], dev[6], c->stream, c->lc));
   for (int k = 0; k < 7; ++k)
     if (outs[k] && dev[k] != outs[k])
       CK(cudaMemcpyAsync(outs[k], dev[k], sizeof(double) * (size_t)width[k] * (size_t)n,
@@ -683,7 +784,8 @@ sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t
   std::vector<uint32_t> cnt((size_t)n), id((size_t)n), list((size_t)c->cap * (size_t)n);
   CK(cudaMemcpyAsync(cnt.data(), c->nw.count, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
                      c->stream));
-  CK(cudaMemcpyAsync(id.data(), c->buf[c->cur].id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(id.data(), mixed(c) ? c->mbuf[c->cur].id : c->buf[c->cur].id,
+                     sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
                      c->stream));
   CK(cudaMemcpyAsync(list.data(), c->nw.list, sizeof(uint32_t) * list.size(),
                      cudaMemcpyDeviceToHost, c->stream));

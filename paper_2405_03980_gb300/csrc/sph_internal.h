@@ -53,6 +53,18 @@ struct InstDev {
   int64_t p_begin, p_end;         // particle range (fixed across sorts)
   int64_t chunk_base;             // first reduction chunk of the instance
   int64_t n_chunks;
+  // ---- FP32 copies for the mixed form ----
+  float cellf[3];                 // cell side per axis
+  float cut2_f;                   // (2h)^2 rounded to float (strict < test)
+  float inv_h_f, aD_f, cF_f;
+  float m_f[2];                   // particle mass: [0] inviscid, [1] viscous/wall
+  float mr_f[2];                  // m / rho0
+  float inv_m_f[2], inv_I_f[2];
+  float self_hi[2], self_lo[2];   // m aD / rho0 - 1 as an unevaluated float sum
+  float p0_f, p0mb_f;             // p0 and p0 - beta_P
+  float binom[17];                // binomial coefficients C(alpha_P, k)
+  float rho0_f, A_f, B_f, C_l_f, C_T_f;
+  float dt_f, hdt_f, Omega_f;
 };
 
 // Mutable per-instance scalars that live on the device.
@@ -84,6 +96,30 @@ struct Fp64Fields {
   double* P;
   dvec4* tw;          // torque of wall neighbours on each fluid particle
 };
+
+// One copy of the sorted mixed-precision state: an integer cell plus an FP32
+// offset inside the cell for the position, FP32 everything else.
+// off.w holds the species code; vel.w and spin.w receive V = m/rho and
+// Pr = P/rho^2 from the density pass.
+struct MixBuf {
+  uint32_t* cell;       // cx | cy << 11 | cz << 22 (cell coordinates in the instance)
+  float4* off;          // offset in [0, cell side) per axis, species
+  float4* vel;          // vx, vy, vz, V
+  float4* spin;         // wx, wy, wz, Pr
+  dvec2* ref;           // wall reference (phase-0) x, y in FP64
+  uint32_t* id;
+  uint32_t* inst;
+};
+
+struct MixFields {
+  float4* acc;
+  float4* dspin;
+  float4* tw;           // torque of wall neighbours on each fluid particle
+  float* delta;         // rho / rho0 - 1
+  float* P;
+};
+
+constexpr uint32_t kCellBitsX = 11, kCellBitsY = 11, kCellBitsZ = 10;
 
 struct CellWs {
   uint32_t* key;        // global cell of each particle (pre-sort order)

@@ -47,7 +47,41 @@ cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
                              const double* vel, const double* spin, const uint8_t* sp,
                              const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc);
 
+// ---- mixed-precision path (sph_mixed.cu) -------------------------------------
+cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                    const InstDev* inst, const InstState* ist, const CellWs& cw,
+                                    uint32_t* err, int mode, cudaStream_t s, const LaunchCfg& lc,
+                                    int* launches);
+cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
+                                 const CellWs& cw, cudaStream_t s, const LaunchCfg& lc,
+                                 int* launches);
+cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                                 int* launches);
+cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                cudaStream_t s, const LaunchCfg& lc, int* launches);
+cudaError_t launch_kick_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                              const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
+                              int* launches);
+cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, const double* pos,
+                              const double* vel, const double* spin, const uint8_t* sp,
+                              const uint32_t* inst_of, uint32_t* err, cudaStream_t s,
+                              const LaunchCfg& lc);
+cudaError_t launch_unsort_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                const InstDev* inst, double* pos, double* vel, double* spin,
+                                double* rho, double* P, double* acc, double* dspin,
+                                cudaStream_t s, const LaunchCfg& lc);
+
 // ---- FP64 reductions (sph_reduce.cu) -----------------------------------------
+cudaError_t launch_wall_torque_mixed(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                                     InstState* ist, const MixBuf& b, const MixFields& f,
+                                     double* partials, int advance, cudaStream_t s,
+                                     int* launches);
+cudaError_t launch_diag_mixed(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                              const MixBuf& b, const MixFields& f, const NbrWs& nw,
+                              double* partials, double* out, cudaStream_t s);
 // Per-instance wall torque of the last force pass; then
 // J += dt/2 (T_old + T_new), T = T_new, and (advance) theta += Omega dt, step++.
 cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks,

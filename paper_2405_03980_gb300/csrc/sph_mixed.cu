@@ -1,0 +1,559 @@
+// Mixed-precision form of the two-fluid spin-SPH step.
+//
+// Same model as the FP64 form (density summation + Eq. 4 Tait pressure, the
+// fused pair pass of Eqs. 1-2 with the spin torque, kick-drift-kick with
+// rigid rotating walls, Algorithm 1), stored and computed differently:
+//  - a position is an integer cell (the neighbour-grid cell, side >= 2h) plus
+//    an FP32 offset inside that cell; pair vectors are formed as
+//    (c_i - c_j) L + (o_i - o_j), exactly antisymmetric, with the cell
+//    difference folded into {-1, 0, 1} (periodic z included);
+//  - velocities, spins, density deviation delta = rho/rho0 - 1, pressure and
+//    all pair arithmetic are FP32; the pair terms are written so that
+//    f_ji == -f_ij bit for bit, and every per-particle sum is Kahan-compensated;
+//  - the Tait pressure is evaluated in binomial form from delta, avoiding the
+//    cancellation of (rho/rho0)^alpha - 1;
+//  - the wall phase stays FP64, walls are placed in FP64 and then converted;
+//    conservation reductions read this state in FP64 (sph_reduce.cu).
+#include <math.h>
+
+#include "sph_kernels.h"
+
+namespace sphgb {
+namespace {
+
+__device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
+  if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
+}
+
+inline int grid_for(int64_t n, int threads, int sm_count, int per_sm) {
+  int64_t g = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
+  return (uint32_t)cx | ((uint32_t)cy << kCellBitsX) | ((uint32_t)cz << (kCellBitsX + kCellBitsY));
+}
+__device__ __forceinline__ int cell_x(uint32_t c) { return (int)(c & ((1u << kCellBitsX) - 1)); }
+__device__ __forceinline__ int cell_y(uint32_t c) {
+  return (int)((c >> kCellBitsX) & ((1u << kCellBitsY) - 1));
+}
+__device__ __forceinline__ int cell_z(uint32_t c) { return (int)(c >> (kCellBitsX + kCellBitsY)); }
+
+// Kahan-compensated FP32 accumulation.
+struct Kahan {
+  float s, c;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// Double position -> (cell, FP32 offset) on one axis.  Returns false if the
+// cell falls outside the interior range (the cell is then clamped).
+__device__ __forceinline__ bool to_cell(const InstDev& P, int a, double x, int& c, float& o) {
+  const double u = (x - P.lo[a]) * P.inv_cell[a];
+  double t = floor(u);
+  bool ok = true;
+  const int lo = P.clo[a], hi = P.chi[a];
+  if (!(t >= (double)lo && t <= (double)hi)) {
+    ok = false;
+    t = (t > (double)hi) ? (double)hi : (double)lo;  // NaN -> lo
+  }
+  c = (int)t;
+  double r = (x - P.lo[a]) - t * P.cell[a];
+  if (!(r >= 0.0)) r = 0.0;
+  o = (float)r;
+  if (o >= P.cellf[a]) o = nextafterf(P.cellf[a], 0.f);
+  return ok;
+}
+
+// Keep o in [0, L) by moving whole cells; periodic axes wrap c modulo n.
+__device__ __forceinline__ bool normalize(float& o, int& c, float L, int lo, int hi,
+                                          bool periodic, int n) {
+  for (int k = 0; k < 4; ++k) {
+    if (o >= L) {
+      o -= L;
+      c += 1;
+    } else if (o < 0.f) {
+      o += L;
+      c -= 1;
+      if (o >= L) {  // |o| below half an ulp of L: the particle sits on the face
+        o = 0.f;
+        c += 1;
+      }
+    } else {
+      break;
+    }
+  }
+  bool ok = (o >= 0.f && o < L);
+  if (!ok) o = 0.f;
+  if (periodic) {
+    c = ((c % n) + n) % n;
+  } else if (c < lo || c > hi) {
+    ok = false;
+    c = c < lo ? lo : hi;
+  }
+  return ok;
+}
+
+// Pair vector r_i - r_j from cells and offsets (exactly antisymmetric).
+__device__ __forceinline__ void pair_vec(const InstDev& P, uint32_t ci, const float4& oi,
+                                         uint32_t cj, const float4& oj, float& dx, float& dy,
+                                         float& dz) {
+  const int ex = cell_x(ci) - cell_x(cj);
+  const int ey = cell_y(ci) - cell_y(cj);
+  int ez = cell_z(ci) - cell_z(cj);
+  if (P.periodic_z) {
+    if (ez > 1) ez -= P.nz;
+    else if (ez < -1) ez += P.nz;
+  }
+  dx = (float)ex * P.cellf[0] + (oi.x - oj.x);
+  dy = (float)ey * P.cellf[1] + (oi.y - oj.y);
+  dz = (float)ez * P.cellf[2] + (oi.z - oj.z);
+}
+
+__device__ __forceinline__ bool finite3f(float a, float b, float c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// ---------------------------------------------------------------- integrator
+
+__global__ void k_kick_drift_mixed(int64_t n, MixBuf b, MixFields f,
+                                   const InstDev* __restrict__ inst,
+                                   const InstState* __restrict__ ist, CellWs cw, uint32_t* err,
+                                   int mode) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = b.inst[i];
+    const InstDev& P = inst[k];
+    float4 o = b.off[i];
+    const int sp = (int)o.w;
+    int c[3];
+    bool ok = true;
+    if (sp < 2) {
+      const uint32_t cc = b.cell[i];
+      c[0] = cell_x(cc);
+      c[1] = cell_y(cc);
+      c[2] = cell_z(cc);
+      if (mode == 1) {
+        float4 v = b.vel[i];
+        float4 w = b.spin[i];
+        const float4 a = f.acc[i];
+        const float4 al = f.dspin[i];
+        v.x += P.hdt_f * a.x;
+        v.y += P.hdt_f * a.y;
+        v.z += P.hdt_f * a.z;
+        w.x += P.hdt_f * al.x;
+        w.y += P.hdt_f * al.y;
+        w.z += P.hdt_f * al.z;
+        o.x += P.dt_f * v.x;
+        o.y += P.dt_f * v.y;
+        o.z += P.dt_f * v.z;
+        ok &= normalize(o.x, c[0], P.cellf[0], P.clo[0], P.chi[0], false, P.nx);
+        ok &= normalize(o.y, c[1], P.cellf[1], P.clo[1], P.chi[1], false, P.ny);
+        ok &= normalize(o.z, c[2], P.cellf[2], P.clo[2], P.chi[2], P.periodic_z != 0, P.nz);
+        b.vel[i] = v;
+        b.spin[i] = w;
+        b.off[i] = o;
+        b.cell[i] = pack_cell(c[0], c[1], c[2]);
+        if (!finite3f(v.x, v.y, v.z) || !finite3f(w.x, w.y, w.z)) latch(err, ERR_NONFINITE);
+      }
+    } else {
+      double th = ist[k].theta;
+      if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
+      double s, cs;
+      sincos(th, &s, &cs);
+      const dvec2 r0 = b.ref[i];
+      const double x = __dsub_rn(__dmul_rn(cs, r0.x), __dmul_rn(s, r0.y));
+      const double y = __dadd_rn(__dmul_rn(s, r0.x), __dmul_rn(cs, r0.y));
+      // a wall keeps its z cell and offset; x, y follow the rigid rotation
+      const uint32_t cc = b.cell[i];
+      ok &= to_cell(P, 0, x, c[0], o.x);
+      ok &= to_cell(P, 1, y, c[1], o.y);
+      c[2] = cell_z(cc);
+      b.off[i] = o;
+      b.cell[i] = pack_cell(c[0], c[1], c[2]);
+      b.vel[i] = make_float4((float)(-P.Omega * y), (float)(P.Omega * x), 0.f, b.vel[i].w);
+      b.spin[i] = make_float4(0.f, 0.f, P.Omega_f, b.spin[i].w);
+    }
+    if (!ok) latch(err, ERR_ESCAPED);
+    const uint32_t key =
+        (uint32_t)(P.cell_base + c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2]));
+    cw.key[i] = key;
+    cw.slot[i] = atomicAdd(&cw.count[key], 1u);
+  }
+}
+
+__global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (b.off[i].w >= 2.f) continue;
+    const float hdt = inst[b.inst[i]].hdt_f;
+    const float4 a = f.acc[i];
+    const float4 al = f.dspin[i];
+    float4 v = b.vel[i];
+    float4 w = b.spin[i];
+    v.x += hdt * a.x;
+    v.y += hdt * a.y;
+    v.z += hdt * a.z;
+    w.x += hdt * al.x;
+    w.y += hdt * al.y;
+    w.z += hdt * al.z;
+    b.vel[i] = v;
+    b.spin[i] = w;
+  }
+}
+
+__global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = cw.perm[k];
+    dst.cell[k] = src.cell[j];
+    dst.off[k] = src.off[j];
+    dst.vel[k] = src.vel[j];
+    dst.spin[k] = src.spin[j];
+    dst.ref[k] = src.ref[j];
+    dst.id[k] = src.id[j];
+    dst.inst[k] = src.inst[j];
+    cw.skey[k] = cw.key[j];
+  }
+}
+
+// -------------------------------------------------------------------- density
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
+                NbrWs nw, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = inst[b.inst[i]];
+  const float4 oi = b.off[i];
+  const uint32_t ci = b.cell[i];
+  const int sp = (int)oi.w;
+  const int si = sp == 0 ? 0 : 1;
+  float delta;
+  uint32_t cnt = 0;
+  if (sp == 3) {
+    delta = 0.f;
+  } else {
+    const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
+    const uint32_t cap = (uint32_t)nw.cap;
+    const float cut2 = P.cut2_f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int z2 = cz + dz;
+      if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int64_t row = P.cell_base + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2);
+        const uint32_t s = cw.start[row + cx - 1];
+        const uint32_t e = cw.start[row + cx + 2];
+        for (uint32_t j = s; j < e; ++j) {
+          if (j == (uint32_t)i) continue;
+          float dx, dy2, dz2;
+          pair_vec(P, ci, oi, b.cell[j], b.off[j], dx, dy2, dz2);
+          const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+          if (r2 < cut2) {
+            if (cnt < cap) nw.list[(int64_t)cnt * n + i] = j;
+            ++cnt;
+          }
+        }
+      }
+    }
+    if (cnt > cap) {
+      latch(err, ERR_NEIGHBORS);
+      cnt = cap;
+    }
+    // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
+    // starting from the self term minus one carried as a float pair
+    Kahan acc{P.self_hi[si], -P.self_lo[si]};
+    for (uint32_t t = 0; t < cnt; ++t) {
+      const uint32_t j = nw.list[(int64_t)t * n + i];
+      const float4 oj = b.off[j];
+      float dx, dy2, dz2;
+      pair_vec(P, ci, oi, b.cell[j], oj, dx, dy2, dz2);
+      const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+      const float q = sqrtf(r2) * P.inv_h_f;
+      const float t1 = 1.f - 0.5f * q;
+      const float t2 = t1 * t1;
+      const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);
+      acc.add(P.mr_f[oj.w == 0.f ? 0 : 1] * W);
+    }
+    delta = acc.value();
+  }
+  nw.count[i] = cnt;
+  // Tait pressure in binomial form: P = p0 sum_k C(a,k) delta^k + (p0 - beta_P)
+  float h = P.binom[P.alphaP];
+  for (int k = P.alphaP - 1; k >= 1; --k) h = h * delta + P.binom[k];
+  const float Pres = P.p0_f * (delta * h) + P.p0mb_f;
+  const float rho = P.rho0_f * (1.f + delta);
+  f.delta[i] = delta;
+  f.P[i] = Pres;
+  b.vel[i].w = P.m_f[si] / rho;
+  b.spin[i].w = Pres / (rho * rho);
+  if (!isfinite(delta) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------------ pair pass
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
+               uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const float4 oi = b.off[i];
+  const int sp_i = (int)oi.w;
+  if (sp_i >= 2) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    f.acc[i] = z;
+    f.dspin[i] = z;
+    f.tw[i] = z;
+    return;
+  }
+  const InstDev& P = inst[b.inst[i]];
+  const uint32_t ci = b.cell[i];
+  const float4 vi = b.vel[i];   // w = V_i
+  const float4 wi = b.spin[i];  // w = P_i / rho_i^2
+  const int si = sp_i == 0 ? 0 : 1;
+  const float m_i = P.m_f[si];
+  const uint32_t fl = P.flags;
+  const float kP = (fl & SPH_TERM_P) ? 1.f : 0.f;
+  const float kT = (fl & SPH_TERM_T) ? P.C_T_f : 0.f;
+  const float kSH = (fl & SPH_TERM_SH) ? -P.A_f : 0.f;
+  const float kR = (fl & SPH_TERM_ROT) ? -P.B_f : 0.f;
+  const float kSN = (fl & SPH_TERM_SN) ? -P.C_l_f : 0.f;
+  const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
+  const bool lit = (fl & SPH_SN_LITERAL) != 0;
+  const bool inv_i = sp_i == 0;
+  // absolute position of i about the rotation axis (wall torque only)
+  const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
+  const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
+  const double zi = P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z;
+  const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
+  Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
+  float wx = 0.f, wy = 0.f, wz = 0.f;
+  const uint32_t cnt = nw.count[i];
+  for (uint32_t t = 0; t < cnt; ++t) {
+    const uint32_t j = nw.list[(int64_t)t * n + i];
+    const float4 oj = b.off[j];
+    const float4 vj = b.vel[j];
+    const float4 wj = b.spin[j];
+    float dx, dy, dz;
+    pair_vec(P, ci, oi, b.cell[j], oj, dx, dy, dz);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0.f)) continue;  // coincident particles: density only
+    const float inv_r = rsqrtf(r2);
+    const float r = r2 * inv_r;
+    const float q = r * P.inv_h_f;
+    const float t1 = 1.f - 0.5f * q;
+    const float t2 = t1 * t1;
+    const float F = P.cF_f * (t2 * t1);
+    const float W = P.aD_f * (t2 * t2) * (2.f * q + 1.f);
+    const bool inv_j = oj.w == 0.f;
+    const float mX = (inv_i != inv_j) ? 1.f : 0.f;
+    const float mV = (!inv_i && !inv_j) ? 1.f : 0.f;
+    const float m_j = P.m_f[inv_j ? 0 : 1];
+    // symmetric pair scalars (products taken in an order independent of i, j)
+    const float VV = vi.w * vj.w;
+    const float MM = m_i * m_j;
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+    const float sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
+    const float ux = vx + 0.5f * (dy * sz - dz * sy);
+    const float uy = vy + 0.5f * (dz * sx - dx * sz);
+    const float uz = vz + 0.5f * (dx * sy - dy * sx);
+    const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+    const float ev = ex * vx + ey * vy + ez * vz;
+    const float eu = ex * ux + ey * uy + ez * uz;
+    const float sP = kP * MM * ((wi.w + wj.w) * F);
+    const float sT = kT * mX * (VV * F);
+    const float sSH = kSH * mV * (VV * F) * ev;
+    const float sR = kR * mV * (VV * F);
+    const float sSN = kSN * mX * (VV * W);
+    const float frx = sR * (ux - eu * ex);
+    const float fry = sR * (uy - eu * ey);
+    const float frz = sR * (uz - eu * ez);
+    const float gx = lit ? vx : ux, gy = lit ? vy : uy, gz = lit ? vz : uz;
+    const float fnx = sSN * gx, fny = sSN * gy, fnz = sSN * gz;
+    const float pfx = (sP + sT) * dx + sSH * ex + frx + fnx;
+    const float pfy = (sP + sT) * dy + sSH * ey + fry + fny;
+    const float pfz = (sP + hz * sT) * dz + sSH * ez + frz + fnz;
+    fx.add(pfx);
+    fy.add(pfy);
+    fz.add(pfz);
+    const float kx = lit ? frx : frx + fnx;
+    const float ky = lit ? fry : fry + fny;
+    const float kz = lit ? frz : frz + fnz;
+    const float qx = -0.5f * (dy * kz - dz * ky);
+    const float qy = -0.5f * (dz * kx - dx * kz);
+    const float qz = -0.5f * (dx * ky - dy * kx);
+    tx.add(qx);
+    ty.add(qy);
+    tz.add(qz);
+    if (oj.w >= 2.f) {
+      wx += pyi * pfz - pzi * pfy + qx;
+      wy += pzi * pfx - pxi * pfz + qy;
+      wz += pxi * pfy - pyi * pfx + qz;
+    }
+  }
+  const float inv_m = P.inv_m_f[si], inv_I = P.inv_I_f[si];
+  const float ax = fx.value(), ay = fy.value(), az = fz.value();
+  const float bx = tx.value(), by = ty.value(), bz = tz.value();
+  f.acc[i] = make_float4(ax * inv_m, ay * inv_m, az * inv_m, 0.f);
+  f.dspin[i] = make_float4(bx * inv_I, by * inv_I, bz * inv_I, 0.f);
+  f.tw[i] = make_float4(wx, wy, wz, 0.f);
+  if (!finite3f(ax, ay, az) || !finite3f(bx, by, bz)) latch(err, ERR_NONFINITE);
+}
+
+// ----------------------------------------------------------- load / unload
+
+__global__ void k_load_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
+                             const double* __restrict__ pos, const double* __restrict__ vel,
+                             const double* __restrict__ spin, const uint8_t* __restrict__ sp,
+                             const uint32_t* __restrict__ inst_of, uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = inst_of[i];
+    const InstDev& P = inst[k];
+    int c[3];
+    float4 o;
+    bool ok = true;
+    ok &= to_cell(P, 0, pos[3 * i], c[0], o.x);
+    ok &= to_cell(P, 1, pos[3 * i + 1], c[1], o.y);
+    ok &= to_cell(P, 2, pos[3 * i + 2], c[2], o.z);
+    o.w = (float)sp[i];
+    if (!ok) latch(err, ERR_ESCAPED);
+    b.cell[i] = pack_cell(c[0], c[1], c[2]);
+    b.off[i] = o;
+    b.vel[i] = make_float4((float)vel[3 * i], (float)vel[3 * i + 1], (float)vel[3 * i + 2], 0.f);
+    b.spin[i] =
+        make_float4((float)spin[3 * i], (float)spin[3 * i + 1], (float)spin[3 * i + 2], 0.f);
+    b.ref[i] = dvec2{pos[3 * i], pos[3 * i + 1]};
+    b.id[i] = (uint32_t)i;
+    b.inst[i] = k;
+  }
+}
+
+__global__ void k_unsort_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst,
+                               double* pos, double* vel, double* spin, double* rho, double* P,
+                               double* acc, double* dspin) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b.id[k];
+    const InstDev& Q = inst[b.inst[k]];
+    if (pos) {
+      const uint32_t c = b.cell[k];
+      const float4 of = b.off[k];
+      pos[3 * o] = Q.lo[0] + (double)cell_x(c) * Q.cell[0] + (double)of.x;
+      pos[3 * o + 1] = Q.lo[1] + (double)cell_y(c) * Q.cell[1] + (double)of.y;
+      pos[3 * o + 2] = Q.lo[2] + (double)cell_z(c) * Q.cell[2] + (double)of.z;
+    }
+    if (vel) {
+      const float4 v = b.vel[k];
+      vel[3 * o] = v.x;
+      vel[3 * o + 1] = v.y;
+      vel[3 * o + 2] = v.z;
+    }
+    if (spin) {
+      const float4 w = b.spin[k];
+      spin[3 * o] = w.x;
+      spin[3 * o + 1] = w.y;
+      spin[3 * o + 2] = w.z;
+    }
+    if (rho) rho[o] = Q.rho0 * (1.0 + (double)f.delta[k]);
+    if (P) P[o] = f.P[k];
+    if (acc) {
+      const float4 a = f.acc[k];
+      acc[3 * o] = a.x;
+      acc[3 * o + 1] = a.y;
+      acc[3 * o + 2] = a.z;
+    }
+    if (dspin) {
+      const float4 a = f.dspin[k];
+      dspin[3 * o] = a.x;
+      dspin[3 * o + 1] = a.y;
+      dspin[3 * o + 2] = a.z;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                    const InstDev* inst, const InstState* ist, const CellWs& cw,
+                                    uint32_t* err, int mode, cudaStream_t s, const LaunchCfg& lc,
+                                    int* launches) {
+  k_kick_drift_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, ist, cw,
+                                                                        err, mode);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
+                                 const CellWs& cw, cudaStream_t s, const LaunchCfg& lc,
+                                 int* launches) {
+  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, cw);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                                 int* launches) {
+  if (lc.block_density == 256) {
+    k_density_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+  } else if (lc.block_density == 64) {
+    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+  } else {
+    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  if (lc.block_forces == 256) {
+    k_forces_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, nw, err);
+  } else if (lc.block_forces == 64) {
+    k_forces_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, nw, err);
+  } else {
+    k_forces_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
+  }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                              const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
+                              int* launches) {
+  k_kick_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, const double* pos,
+                              const double* vel, const double* spin, const uint8_t* sp,
+                              const uint32_t* inst_of, uint32_t* err, cudaStream_t s,
+                              const LaunchCfg& lc) {
+  k_load_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, inst, pos, vel, spin, sp,
+                                                                  inst_of, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                const InstDev* inst, double* pos, double* vel, double* spin,
+                                double* rho, double* P, double* acc, double* dspin,
+                                cudaStream_t s, const LaunchCfg& lc) {
+  k_unsort_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, pos, vel, spin,
+                                                                    rho, P, acc, dspin);
+  return cudaGetLastError();
+}
+
+}  // namespace sphgb

@@ -1,7 +1,7 @@
 // Deterministic FP64 reductions: the wall torque of each force evaluation
 // (angular-momentum budget of the driven vessel) and the conservation
 // diagnostics (total mass M = M_s + M_n of Sec. 2.1, momentum, orbital and spin
-// angular momentum, energies).
+// angular momentum, energies).  Both state forms are read in FP64.
 //
 // Each instance's particle range is cut into fixed chunks of kReduceChunk
 // particles counted from the instance's first particle; one block reduces one
@@ -17,6 +17,75 @@ namespace sphgb {
 namespace {
 
 constexpr int kRedThreads = 256;
+
+// Read-only FP64 views of the two state forms.
+struct Fp64View {
+  Fp64Buf b;
+  Fp64Fields f;
+  __device__ __forceinline__ int species(int64_t i) const { return (int)b.pos[i].w; }
+  __device__ __forceinline__ void pos(int64_t i, const InstDev&, double* r) const {
+    const dvec4 p = b.pos[i];
+    r[0] = p.x;
+    r[1] = p.y;
+    r[2] = p.z;
+  }
+  __device__ __forceinline__ void vel(int64_t i, double* v) const {
+    const dvec4 p = b.vel[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+  __device__ __forceinline__ void spin(int64_t i, double* v) const {
+    const dvec4 p = b.spin[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+  __device__ __forceinline__ double rho(int64_t i, const InstDev&) const { return f.rho[i]; }
+  __device__ __forceinline__ void tw(int64_t i, double* v) const {
+    const dvec4 p = f.tw[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+};
+
+struct MixView {
+  MixBuf b;
+  MixFields f;
+  __device__ __forceinline__ int species(int64_t i) const { return (int)b.off[i].w; }
+  __device__ __forceinline__ void pos(int64_t i, const InstDev& P, double* r) const {
+    const uint32_t c = b.cell[i];
+    const float4 o = b.off[i];
+    const int cx = (int)(c & ((1u << kCellBitsX) - 1));
+    const int cy = (int)((c >> kCellBitsX) & ((1u << kCellBitsY) - 1));
+    const int cz = (int)(c >> (kCellBitsX + kCellBitsY));
+    r[0] = P.lo[0] + (double)cx * P.cell[0] + (double)o.x;
+    r[1] = P.lo[1] + (double)cy * P.cell[1] + (double)o.y;
+    r[2] = P.lo[2] + (double)cz * P.cell[2] + (double)o.z;
+  }
+  __device__ __forceinline__ void vel(int64_t i, double* v) const {
+    const float4 p = b.vel[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+  __device__ __forceinline__ void spin(int64_t i, double* v) const {
+    const float4 p = b.spin[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+  __device__ __forceinline__ double rho(int64_t i, const InstDev& P) const {
+    return P.rho0 * (1.0 + (double)f.delta[i]);
+  }
+  __device__ __forceinline__ void tw(int64_t i, double* v) const {
+    const float4 p = f.tw[i];
+    v[0] = p.x;
+    v[1] = p.y;
+    v[2] = p.z;
+  }
+};
 
 struct ChunkRange {
   int64_t begin, end;
@@ -53,21 +122,24 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
   }
 }
 
+template <class View>
 __global__ void __launch_bounds__(kRedThreads)
-k_wall_torque_chunks(int32_t n_inst, const InstDev* __restrict__ inst, Fp64Buf b,
-                     Fp64Fields f, double* __restrict__ partials) {
+k_wall_torque_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V,
+                     double* __restrict__ partials) {
   __shared__ double sh[3 * kRedThreads];
   const ChunkRange r = chunk_range(inst, n_inst, blockIdx.x);
   double v[3] = {0.0, 0.0, 0.0};
   for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
-    if (b.pos[i].w >= 2.0) continue;
-    const dvec4 t = f.tw[i];
-    v[0] += t.x;
-    v[1] += t.y;
-    v[2] += t.z;
+    if (V.species(i) >= 2) continue;
+    double t[3];
+    V.tw(i, t);
+    v[0] += t[0];
+    v[1] += t[1];
+    v[2] += t[2];
   }
   block_sum<3>(v, sh);
-  if (threadIdx.x < 3) partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x * kRedThreads];
+  if (threadIdx.x < 3)
+    partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x * kRedThreads];
 }
 
 __global__ void k_wall_torque_final(int32_t n_inst, const InstDev* __restrict__ inst,
@@ -108,9 +180,10 @@ __device__ __forceinline__ double tait_energy(const InstDev& P, double rho) {
 // 13 E_rot, 14 E_int, 15 n_pairs; 16 rho_min, 17 rho_max, 18 v_max.
 constexpr int kSumFields = 16;
 
+template <class View>
 __global__ void __launch_bounds__(kRedThreads)
-k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, Fp64Buf b, Fp64Fields f,
-              NbrWs nw, double* __restrict__ partials) {
+k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw,
+              double* __restrict__ partials) {
   __shared__ double sh[kSumFields * kRedThreads];
   __shared__ double mx[3][kRedThreads];
   const ChunkRange r = chunk_range(inst, n_inst, blockIdx.x);
@@ -120,29 +193,33 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, Fp64Buf b, Fp64F
   for (int a = 0; a < kSumFields; ++a) v[a] = 0.0;
   double rmin = INFINITY, rmax = -INFINITY, vmax = 0.0;
   for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
-    const dvec4 p = b.pos[i];
-    if (p.w >= 2.0) continue;
-    const bool inv = p.w == 0.0;
+    const int sp = V.species(i);
+    if (sp >= 2) continue;
+    const bool inv = sp == 0;
     const double m = inv ? P.m_s : P.m_n;
     const double I = 1.0 / (inv ? P.inv_I_s : P.inv_I_n);
-    const dvec4 u = b.vel[i];
-    const dvec4 w = b.spin[i];
-    const double rho = f.rho[i];
-    v[0] += m;
-    v[1] += inv ? m : 0.0;
-    v[2] += inv ? 0.0 : m;
-    v[3] += m * u.x;
-    v[4] += m * u.y;
-    v[5] += m * u.z;
-    v[6] += m * (p.y * u.z - p.z * u.y);
-    v[7] += m * (p.z * u.x - p.x * u.z);
-    v[8] += m * (p.x * u.y - p.y * u.x);
-    v[9] += I * w.x;
-    v[10] += I * w.y;
-    v[11] += I * w.z;
-    const double u2 = u.x * u.x + u.y * u.y + u.z * u.z;
+    double p[3], u[3], w[3];
+    V.pos(i, P, p);
+    V.vel(i, u);
+    V.spin(i, w);
+    const double rho = V.rho(i, P);
+    // particle counts (exact integers): M_s = m_s N_s and M_n = m_n N_n are
+    // formed at the end, so the total mass is conserved bit for bit
+    v[0] += 1.0;
+    v[1] += inv ? 1.0 : 0.0;
+    v[2] += inv ? 0.0 : 1.0;
+    v[3] += m * u[0];
+    v[4] += m * u[1];
+    v[5] += m * u[2];
+    v[6] += m * (p[1] * u[2] - p[2] * u[1]);
+    v[7] += m * (p[2] * u[0] - p[0] * u[2]);
+    v[8] += m * (p[0] * u[1] - p[1] * u[0]);
+    v[9] += I * w[0];
+    v[10] += I * w[1];
+    v[11] += I * w[2];
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     v[12] += 0.5 * m * u2;
-    v[13] += 0.5 * I * (w.x * w.x + w.y * w.y + w.z * w.z);
+    v[13] += 0.5 * I * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     v[14] += m * tait_energy(P, rho);
     v[15] += (double)nw.count[i];
     rmin = fmin(rmin, rho);
@@ -185,31 +262,62 @@ __global__ void k_diag_final(int32_t n_inst, const InstDev* __restrict__ inst,
   }
   double* o = out + (int64_t)k * kDiagFields;
   for (int a = 0; a < kSumFields; ++a) o[a] = s[a];
+  o[1] = P.m_s * s[1];
+  o[2] = P.m_n * s[2];
+  o[0] = o[1] + o[2];
   o[kSumFields] = rmin;
   o[kSumFields + 1] = rmax;
   o[kSumFields + 2] = vmax;
 }
 
-}  // namespace
-
-cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks,
-                                    const InstDev* inst, InstState* ist,
-                                    const Fp64Buf& b, const Fp64Fields& f,
-                                    double* partials, int advance, cudaStream_t s,
-                                    int* launches) {
-  k_wall_torque_chunks<<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, b, f,
-                                                                      partials);
+template <class View>
+cudaError_t wall_torque(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                        InstState* ist, const View& V, double* partials, int advance,
+                        cudaStream_t s, int* launches) {
+  k_wall_torque_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, V,
+                                                                            partials);
   k_wall_torque_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, ist, partials, advance);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
 
+template <class View>
+cudaError_t diag(int32_t n_inst, int64_t total_chunks, const InstDev* inst, const View& V,
+                 const NbrWs& nw, double* partials, double* out, cudaStream_t s) {
+  k_diag_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, V, nw,
+                                                                     partials);
+  k_diag_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, partials, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                                    InstState* ist, const Fp64Buf& b, const Fp64Fields& f,
+                                    double* partials, int advance, cudaStream_t s,
+                                    int* launches) {
+  return wall_torque(n_inst, total_chunks, inst, ist, Fp64View{b, f}, partials, advance, s,
+                     launches);
+}
+
+cudaError_t launch_wall_torque_mixed(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                                     InstState* ist, const MixBuf& b, const MixFields& f,
+                                     double* partials, int advance, cudaStream_t s,
+                                     int* launches) {
+  return wall_torque(n_inst, total_chunks, inst, ist, MixView{b, f}, partials, advance, s,
+                     launches);
+}
+
 cudaError_t launch_diag_fp64(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
                              const Fp64Buf& b, const Fp64Fields& f, const NbrWs& nw,
                              double* partials, double* out, cudaStream_t s) {
-  k_diag_chunks<<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, b, f, nw, partials);
-  k_diag_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, partials, out);
-  return cudaGetLastError();
+  return diag(n_inst, total_chunks, inst, Fp64View{b, f}, nw, partials, out, s);
+}
+
+cudaError_t launch_diag_mixed(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
+                              const MixBuf& b, const MixFields& f, const NbrWs& nw,
+                              double* partials, double* out, cudaStream_t s) {
+  return diag(n_inst, total_chunks, inst, MixView{b, f}, nw, partials, out, s);
 }
 
 }  // namespace sphgb

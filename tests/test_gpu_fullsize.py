@@ -79,7 +79,7 @@ def test_fullsize_sampled_parity(name, k):
         assert rel(st["acc"][S], acc[S]) < 1e-12, stage
         assert rel(st["dspin"][S], dsp[S]) < 1e-11, stage
     d = sim.diagnostics()
-    assert d["mass"] == d0["mass"]
+    assert d["mass"] == d0["mass"]          # M = m_s N_s + m_n N_n: exact
     Lz0 = d0["L_orb"][2] + d0["L_spin"][2]
     Lz = d["L_orb"][2] + d["L_spin"][2]
     assert abs((Lz - Lz0) - d["J_wall"][2]) < 1e-9 * abs(Lz0)

@@ -1,0 +1,153 @@
+"""Mixed-precision form (integer cell + FP32 offset positions, FP32 pair math
+with Kahan-compensated sums, FP64 reductions and wall phase) against the FP64
+oracle and the FP64 GPU form.
+
+Tolerances (stated targets of the mixed form): every field within 2e-5
+relative L2 of the FP64 oracle after one step (rho, P, a, dspin, the
+displacement r1 - r0, v, spin); orbital + spin angular momentum within 1e-6
+relative of the FP64 form over 1000 steps; the mass exactly conserved.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_03980_gb300 import _binding as B
+from paper_2405_03980_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def sim_of(instances, precision=B.SPH_MIXED, **kw):
+    from paper_2405_03980_gb300.sim import Simulation
+    return Simulation(instances, precision=precision, **kw)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def field_errors(st, o, pos0, fluid):
+    return {
+        "rho": rel_l2(st["rho"], o.rho),
+        "P": rel_l2(st["P"], o.P),
+        "acc": rel_l2(st["acc"][fluid], o.acc[fluid]),
+        "dspin": rel_l2(st["dspin"][fluid], o.dspin[fluid]),
+        "dr": rel_l2((st["pos"] - pos0)[fluid], (o.pos - pos0)[fluid]),
+        "vel": rel_l2(st["vel"][fluid], o.vel[fluid]),
+        "spin": rel_l2(st["spin"][fluid], o.spin[fluid]),
+    }
+
+
+def test_mixed_initial_and_one_step_within_target():
+    c = synth.workload("cyl_8960")
+    fluid = c.species < 2
+    sim = sim_of(c)
+    o = oracle.Sim(c.params, c.pos, c.vel, c.spin, c.species)
+    st = sim.state_arrays()
+    e0 = field_errors(st, o, c.pos, fluid)
+    e0.pop("dr")
+    print("mixed t=0 relative L2 errors", e0)
+    sim.step(1)
+    o.step(1)
+    st = sim.state_arrays()
+    e1 = field_errors(st, o, c.pos, fluid)
+    print("mixed 1-step relative L2 errors", e1)
+    bad = {k: v for k, v in {**e0, **e1}.items() if not v <= L2_TOL}
+    assert not bad, f"above {L2_TOL}: {bad}"
+    sim.close()
+
+
+def test_mixed_neighbour_sets_differ_only_at_the_cutoff():
+    c = synth.workload("cyl_8960")
+    sim = sim_of(c)
+    st = sim.state_arrays()
+    sim.density()
+    off_g, nbr_g = sim.neighbors()
+    p = oracle.make_params(c.params)
+    off_o, nbr_o = oracle.neighbors(p, st["pos"])
+    cut2 = (2 * p.h) ** 2
+    ndiff = 0
+    for i in range(c.n):
+        if c.species[i] == 3:
+            continue
+        g = set(nbr_g[off_g[i]:off_g[i + 1]].tolist())
+        o = set(nbr_o[off_o[i]:off_o[i + 1]].tolist())
+        for j in g ^ o:
+            d = st["pos"][i] - st["pos"][j]
+            d[2] -= c.H * np.round(d[2] / c.H)
+            assert abs(d @ d - cut2) < 1e-5 * cut2, (i, j, d @ d)
+            ndiff += 1
+    assert ndiff < 1e-4 * off_o[-1]
+    sim.close()
+
+
+def test_mixed_pair_forces_are_antisymmetric():
+    """Bitwise antisymmetric pair terms: the total force is zero up to the
+    rounding of the compensated per-particle sums."""
+    pos, vel, spin, sp = synth.periodic_block(8, 8, 8, seed=4, f_v=0.4, vel_sigma=0.2)
+    prm = synth.workload_params(4.0, 8, 0.1)
+    prm.update(box_lo=(-2.0, -2.0, 0.0), box_hi=(10.0, 10.0, 8.0), C_T=0.5, C_l=0.3)
+    c = synth.Cylinder(R=4.0, H=8, dx=1.0, Omega=0.1, f_v=0.4, seed=4, pos=pos, vel=vel,
+                       spin=spin, species=sp, params=prm)
+    sim = sim_of(c)
+    st = sim.state_arrays()
+    m = sim.diagnostics()["mass"] / len(sp)
+    F = st["acc"] * m
+    tot = F.sum(0)
+    assert np.all(np.abs(tot) < 1e-6 * np.abs(F).sum(0)), tot
+    sim.close()
+
+
+def test_mixed_batch_equals_solo_bitwise():
+    cs = [synth.cylinder(R=r, H=h, Omega=om, f_v=fv, seed=s)
+          for r, h, om, fv, s in [(5.2, 10, 0.12, 0.3, 11), (3.4, 8, 0.2, 0.02, 12)]]
+    batch = sim_of(cs)
+    batch.step(4)
+    bst = batch.state_arrays()
+    off = 0
+    for k, c in enumerate(cs):
+        solo = sim_of(c)
+        solo.step(4)
+        s = solo.state_arrays()
+        for f in ("pos", "vel", "spin", "rho", "P", "acc", "dspin"):
+            assert np.array_equal(bst[f][off:off + c.n], s[f]), (k, f)
+        assert batch.diagnostics(k)["L_orb"] == solo.diagnostics(0)["L_orb"]
+        solo.close()
+        off += c.n
+    batch.close()
+
+
+def test_mixed_angular_momentum_over_1000_steps():
+    """L_z(t) - L_z(0) must equal the wall torque impulse J_z; the residual of
+    the mixed form and its gap to the FP64 form stay within 1e-6 of L_z."""
+    c = synth.workload("cyl_8960")
+    res = {}
+    for prec in (B.SPH_FP64, B.SPH_MIXED):
+        sim = sim_of(c, precision=prec)
+        d0 = sim.diagnostics()
+        sim.step(1000)
+        d = sim.diagnostics()
+        Lz0 = d0["L_orb"][2] + d0["L_spin"][2]
+        Lz = d["L_orb"][2] + d["L_spin"][2]
+        res[prec] = (Lz, Lz - Lz0 - d["J_wall"][2], Lz0, d["mass"] - d0["mass"])
+        sim.close()
+    Lz64, r64, Lz0, dm64 = res[B.SPH_FP64]
+    Lzm, rm, _, dmm = res[B.SPH_MIXED]
+    print("budget residual fp64 %.3e mixed %.3e; mixed-fp64 %.3e (relative to L_z0)"
+          % (r64 / Lz0, rm / Lz0, (Lzm - Lz64) / Lz0))
+    assert dm64 == 0.0 and dmm == 0.0
+    assert abs(r64) < 1e-10 * abs(Lz0)
+    assert abs(rm) < 1e-6 * abs(Lz0)
+    assert abs(Lzm - Lz64) < 1e-6 * abs(Lz0)
