@@ -58,6 +58,7 @@ def test_mixed_initial_and_one_step_within_target():
     st = sim.state_arrays()
     e0 = field_errors(st, o, c.pos, fluid)
     e0.pop("dr")
+    e0.pop("spin")  # the fluid starts with zero spin
     print("mixed t=0 relative L2 errors", e0)
     sim.step(1)
     o.step(1)
@@ -131,8 +132,13 @@ def test_mixed_batch_equals_solo_bitwise():
 
 def test_mixed_angular_momentum_over_1000_steps():
     """L_z(t) - L_z(0) must equal the wall torque impulse J_z; the residual of
-    the mixed form and its gap to the FP64 form stay within 1e-6 of L_z."""
+    the mixed form and its gap to the FP64 form stay within 1e-6 of L_z.
+    The two-layer wall lets agitated fluid particles diffuse into and through
+    the wall region over long runs, so the cell grid is widened to R + 12 dx
+    here to keep every particle inside it."""
     c = synth.workload("cyl_8960")
+    ext = c.R + 12.0
+    c.params = dict(c.params, box_lo=(-ext, -ext, 0.0), box_hi=(ext, ext, float(c.H)))
     res = {}
     for prec in (B.SPH_FP64, B.SPH_MIXED):
         sim = sim_of(c, precision=prec)
