@@ -205,6 +205,46 @@ SPH_API int32_t sph_launches_per_step(const sph_ctx* ctx);
  * the pipe peak against which the pair passes are reported.  Synchronises. */
 SPH_API sph_status sph_fma_peak(int32_t precision, int32_t iters, double* tflops);
 
+/* Number of doubles that sph_diag_sums_noalloc writes. */
+#define SPH_DIAG_SUMS 19
+
+/* FP64 conservation totals of one particle set without allocating anything.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * For callers that cannot call cudaMalloc -- code running inside a host
+ * application that owns every device allocation (an in-situ analysis plug-in
+ * of a larger simulation), or a process that reserved its whole device memory
+ * budget up front -- but already hold the particle arrays on the device.
+ * Instead of a caller-provided workspace, the partial sums live in one
+ * file-scope device array of 2049 x 24 doubles (393,408 bytes) that every GPU
+ * which loads the library holds until the process exits.
+ *
+ * params: the instance parameters (masses, spin inertia and the Tait law are
+ *   derived from them exactly as for sph_init).
+ * n: particles, 1 .. 67,108,864; a larger n is rejected with SPH_ERR_ARG
+ *   (the capacity of the fixed scratch array).
+ * pos, vel, spin (3n doubles, xyz-interleaved), species (n bytes), rho (n
+ *   doubles): device (or managed) pointers, in any particle order; anything
+ *   else returns SPH_ERR_ARG.
+ * out: SPH_DIAG_SUMS doubles, host or device: M, M_s, M_n, momentum[3],
+ *   L_orb[3], L_spin[3], E_kin, E_rot, E_int, 0 (pair counts need neighbour
+ *   lists, which this call does not build), rho_min, rho_max, |v|_max, summed
+ *   over the fluid particles as in sph_diagnostics.  A host out makes the call
+ *   synchronise the stream; a device out leaves it asynchronous.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * The first call on each device (with that device current) looks up the
+ * scratch array's device address with cudaGetSymbolAddress; make that first
+ * call before any stream capture.  Every call on a device shares the same
+ * scratch array and overwrites the partials it reads, so calls that may
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+SPH_API sph_status sph_diag_sums_noalloc(const sph_params* params, int64_t n, const double* pos,
+                                         const double* vel, const double* spin,
+                                         const uint8_t* species, const double* rho, double* out,
+                                         void* stream);
+
 /* Release the context (host memory, graphs, internal stream).  The caller
  * frees its own device buffers afterwards. */
 SPH_API sph_status sph_destroy(sph_ctx* ctx);

@@ -95,6 +95,7 @@ def lib(build_if_missing: bool = True):
                 "sph_stage_count": (C.c_int32, []),
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+                "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
                 "sph_destroy": (C.c_int, [vp]),
                 "sph_status_string": (C.c_char_p, [C.c_int]),
             }
@@ -112,7 +113,7 @@ def exported_symbols() -> list[str]:
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
-            "sph_fma_peak", "sph_destroy", "sph_status_string"]
+            "sph_fma_peak", "sph_diag_sums_noalloc", "sph_destroy", "sph_status_string"]
 
 
 def _ck(st: int, where: str):
@@ -258,6 +259,17 @@ def sph_fma_peak(precision: int, iters: int = 1 << 16) -> float:
     t = C.c_double()
     _ck(lib().sph_fma_peak(int(precision), int(iters), C.byref(t)), "sph_fma_peak")
     return t.value
+
+
+SPH_DIAG_SUMS = 19
+
+
+def sph_diag_sums_noalloc(params, n, pos, vel, spin, species, rho, out, stream=0):
+    """Conservation totals of device-resident arrays with no device allocation
+    (see include/sph.h); out: SPH_DIAG_SUMS doubles, host or device."""
+    _ck(lib().sph_diag_sums_noalloc(C.byref(params), int(n), _ptr(pos), _ptr(vel), _ptr(spin),
+                                    _ptr(species), _ptr(rho), _ptr(out), stream or None),
+        "sph_diag_sums_noalloc")
 
 
 def sph_destroy(ctx):

@@ -169,6 +169,8 @@ sph_status derive(const sph_params& p, InstDev& d) {
 
 }  // namespace
 
+sph_status sphgb::derive_instance(const sph_params& p, InstDev& d) { return derive(p, d); }
+
 struct sph_ctx {
   int32_t n_inst = 0;
   int64_t n = 0;

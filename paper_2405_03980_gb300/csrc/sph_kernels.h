@@ -4,6 +4,10 @@
 
 namespace sphgb {
 
+// Validate one instance's parameters and derive its device constants (cell
+// grid, kernel and EOS constants, masses); host only (sph_host.cu).
+sph_status derive_instance(const sph_params& p, InstDev& d);
+
 struct LaunchCfg {
   int sm_count;          // multiprocessors of the device
   int block_density;     // threads per block of the density pass
