@@ -50,7 +50,8 @@ typedef enum {
   SPH_ERR_ARG = -1,          /* invalid argument or parameter                 */
   SPH_ERR_CUDA = -2,         /* a CUDA runtime call failed                    */
   SPH_ERR_WORKSPACE = -3,    /* state/workspace buffer too small or misaligned */
-  SPH_ERR_GRID_OVERFLOW = -4,/* cell grid too large for 32-bit cell indices    */
+  SPH_ERR_GRID_OVERFLOW = -4,/* cell grid too large for 32-bit cell indices, or
+                                more than 67,108,864 particles in one context  */
   SPH_ERR_ESCAPED = -5,      /* a particle left the cell grid (clamped)        */
   SPH_ERR_NONFINITE = -6,    /* NaN or Inf in the state                        */
   SPH_ERR_TIMEOUT = -7,      /* a bounded device wait gave up                  */
@@ -103,7 +104,8 @@ typedef struct sph_params {
   int32_t periodic_z;   /* 1: periodic top/bottom (slip, Sec. 3); 0: open     */
   int32_t precision;    /* SPH_FP64 or SPH_MIXED (same for a whole batch)     */
   uint32_t flags;       /* SPH_TERM_* | SPH_HPROJ | SPH_SN_LITERAL            */
-  int32_t nbr_cap;      /* neighbour slots per particle, 0 = 160 (max 1024)   */
+  int32_t nbr_cap;      /* neighbour slots per particle: 0 (= 160) or a
+                           multiple of 8 in 64..1024                          */
 } sph_params;
 
 /* FP64 conservation diagnostics of one instance (sums over fluid particles). */

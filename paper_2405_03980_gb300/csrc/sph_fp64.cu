@@ -179,6 +179,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
                CellWs cw, NbrWs nw, uint32_t* err) {
+  __shared__ uint32_t stage[BLOCK * kStageStride];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -195,10 +196,11 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     const int cx = (int)(c % P.nx);
     const int cy = (int)((c / P.nx) % P.ny);
     const int cz = (int)(c / ((int64_t)P.nx * P.ny));
-    const uint32_t cap = (uint32_t)nw.cap;
     const float cut2f = P.cut2f_margin;
+    uint32_t* st = stage + threadIdx.x * kStageStride;
     // phase 1: FP32 prefilter over the 27 neighbour cells (9 contiguous runs,
     // x is the fastest cell index) into the provisional neighbour list
+    ListWriter pre(nw, n, i, st);
     for (int dz = -1; dz <= 1; ++dz) {
       int z2 = cz + dz;
       if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
@@ -207,7 +209,6 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
         const uint32_t s = cw.start[row + cx - 1];
         const uint32_t e = cw.start[row + cx + 2];
         for (uint32_t j = s; j < e; ++j) {
-          if (j == (uint32_t)i) continue;
           const float4 q = nw.posf[j];
           float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
           if (P.periodic_z) {
@@ -215,23 +216,19 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
             else if (ddz < -P.half_Hzf) ddz += P.Hzf;
           }
           const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2f < cut2f) {
-            if (cnt < cap) nw.list[(int64_t)cnt * n + i] = j;
-            ++cnt;
-          }
+          if (r2f < cut2f && j != (uint32_t)i) pre.append(j);
         }
       }
     }
-    if (cnt > cap) {
-      latch(err, ERR_NEIGHBORS);
-      cnt = cap;
-    }
+    cnt = pre.finish();
+    if (pre.total > (uint32_t)nw.cap) latch(err, ERR_NEIGHBORS);
     // phase 2: exact FP64 cutoff (no fused multiply-add in r^2, strict <),
-    // compaction of the list in place, and the density sum
+    // compaction of the list in place (a group is rewritten only after all
+    // of its entries were read), and the density sum
     rho = m_i * P.aD;  // self term W(0)
-    uint32_t w = 0;
+    ListWriter out(nw, n, i, st);
     for (uint32_t t = 0; t < cnt; ++t) {
-      const uint32_t j = nw.list[(int64_t)t * n + i];
+      const uint32_t j = nw.list[nbr_slot(n, i, t)];
       const dvec4 pj = b.pos[j];
       const double dx = __dsub_rn(pi.x, pj.x);
       const double dy = __dsub_rn(pi.y, pj.y);
@@ -243,8 +240,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
       const double r2 =
           __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
       if (r2 < P.cut2) {
-        nw.list[(int64_t)w * n + i] = j;
-        ++w;
+        out.append(j);
         const double q = sqrt(r2) * P.inv_h;
         const double t1 = 1.0 - 0.5 * q;
         const double t2 = t1 * t1;
@@ -252,7 +248,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
         rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
       }
     }
-    cnt = w;
+    cnt = out.finish();
   }
   nw.count[i] = cnt;
   const double Pres = P.p0 * ipow(rho * P.inv_rho0, P.alphaP) - P.beta_P;
@@ -286,12 +282,12 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double m_i = sp_i == 0 ? P.m_s : P.m_n;
   const double inv_I = sp_i == 0 ? P.inv_I_s : P.inv_I_n;
   const uint32_t fl = P.flags;
-  // per-particle coefficients with the term switches folded in
+  // per-particle coefficients with the term switches and V_i folded in
   const double cP = (fl & SPH_TERM_P) ? m_i : 0.0;
   const double cT = (fl & SPH_TERM_T) ? P.C_T * vi.w : 0.0;
-  const double cSH = (fl & SPH_TERM_SH) ? -P.A * vi.w : 0.0;
-  const double cR = (fl & SPH_TERM_ROT) ? -P.B * vi.w : 0.0;
-  const double cSN = (fl & SPH_TERM_SN) ? -P.C_l * vi.w : 0.0;
+  const double cA = (fl & SPH_TERM_SH) ? P.A * vi.w : 0.0;
+  const double cB = (fl & SPH_TERM_ROT) ? P.B * vi.w : 0.0;
+  const double cN = (fl & SPH_TERM_SN) ? P.C_l * vi.w : 0.0;
   const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
   const bool literal = (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
@@ -300,7 +296,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   double wx = 0.0, wy = 0.0, wz = 0.0;
   const uint32_t cnt = nw.count[i];
   for (uint32_t t = 0; t < cnt; ++t) {
-    const uint32_t j = nw.list[(int64_t)t * n + i];
+    const uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
     const dvec4 pj = b.pos[j];
     const dvec4 vj = b.vel[j];
     const dvec4 wj = b.spin[j];
@@ -314,6 +310,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
     if (!(r2 > 0.0)) continue;  // coincident particles: density only
     const double inv_r = rsqrt(r2);
     const double r = r2 * inv_r;
+    const double inv_r2 = inv_r * inv_r;
     const double q = r * P.inv_h;
     const double t1 = 1.0 - 0.5 * q;
     const double t2 = t1 * t1;
@@ -323,41 +320,38 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
     const double mX = (inv_i != inv_j) ? 1.0 : 0.0;
     const double mV = (!inv_i && !inv_j) ? 1.0 : 0.0;
     const double m_j = inv_j ? P.m_s : P.m_n;
-    const double Vj = vj.w;
-    // relative and spin-corrected velocity
+    // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
     const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
     const double ux = vx + 0.5 * (dy * sz - dz * sy);
     const double uy = vy + 0.5 * (dz * sx - dx * sz);
     const double uz = vz + 0.5 * (dx * sy - dy * sx);
-    const double ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-    const double ev = ex * vx + ey * vy + ez * vz;
-    const double eu = ex * ux + ey * uy + ez * uz;
-    // scalar coefficients of the five terms
-    const double sP = cP * m_j * (wi.w + wj.w) * F;
-    const double sT = cT * Vj * F * mX;
-    const double sSH = cSH * Vj * F * ev * mV;
-    const double sR = cR * Vj * F * mV;
-    const double sSN = cSN * Vj * W * mX;
-    // rotational viscosity (transverse part of u) and F_sn
-    const double frx = sR * (ux - eu * ex);
-    const double fry = sR * (uy - eu * ey);
-    const double frz = sR * (uz - eu * ez);
-    const double gx = literal ? vx : ux, gy = literal ? vy : uy, gz = literal ? vz : uz;
-    const double fnx = sSN * gx, fny = sSN * gy, fnz = sSN * gz;
-    const double pfx = sP * dx + sT * dx + sSH * ex + frx + fnx;
-    const double pfy = sP * dy + sT * dy + sSH * ey + fry + fny;
-    const double pfz = sP * dz + hz * sT * dz + sSH * ez + frz + fnz;
+    const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
+    const double du = dx * ux + dy * uy + dz * uz;  // r_ij . u_ij
+    // The five pair terms collected along r_ij and u_ij (and v_ij for the
+    // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
+    // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F du/r^2 r_ij.
+    const double VF = vj.w * F;
+    const double aP = cP * m_j * (wi.w + wj.w) * F;
+    const double aT = cT * mX * VF;
+    const double aV = VF * mV * inv_r2 * (cB * du - cA * dv);
+    const double bR = -cB * mV * VF;
+    const double bN = -cN * mX * vj.w * W;
+    const double al = aP + aT + aV;
+    const double alz = aP + hz * aT + aV;
+    const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
+    const double bv = literal ? bN : 0.0;      // coefficient of v_ij
+    const double pfx = al * dx + bu * ux + bv * vx;
+    const double pfy = al * dy + bu * uy + bv * vy;
+    const double pfz = alz * dz + bu * uz + bv * vz;
     fx += pfx;
     fy += pfy;
     fz += pfz;
-    // spin torque -1/2 r_ij x (f_rot + f_sn)
-    const double kx = frx + (literal ? 0.0 : fnx);
-    const double ky = fry + (literal ? 0.0 : fny);
-    const double kz = frz + (literal ? 0.0 : fnz);
-    const double qx = -0.5 * (dy * kz - dz * ky);
-    const double qy = -0.5 * (dz * kx - dx * kz);
-    const double qz = -0.5 * (dx * ky - dy * kx);
+    // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
+    const double hb = -0.5 * bu;
+    const double qx = hb * (dy * uz - dz * uy);
+    const double qy = hb * (dz * ux - dx * uz);
+    const double qz = hb * (dx * uy - dy * ux);
     tx += qx;
     ty += qy;
     tz += qz;

@@ -289,7 +289,7 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
   pl.inst.resize(n_inst);
   pl.precision = params[0].precision;
   pl.cap = params[0].nbr_cap ? params[0].nbr_cap : 160;
-  if (pl.cap < 64 || pl.cap > 1024) return SPH_ERR_ARG;
+  if (pl.cap < 64 || pl.cap > 1024 || pl.cap % kNbrGroup) return SPH_ERR_ARG;
   int64_t pb = 0, cb = 0, kb = 0;
   for (int32_t k = 0; k < n_inst; ++k) {
     if (params[k].precision != pl.precision) return SPH_ERR_ARG;
@@ -307,7 +307,7 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
     pb += counts[k];
     kb += d.n_chunks;
   }
-  if (pb >= (int64_t)0xFFFFFFF0ll || cb >= (int64_t)0xFFFFFFF0ll) return SPH_ERR_GRID_OVERFLOW;
+  if (pb > kMaxParticles || cb >= (int64_t)0xFFFFFFF0ll) return SPH_ERR_GRID_OVERFLOW;
   pl.n = pb;
   pl.n_cells = cb;
   pl.total_chunks = kb;
@@ -805,7 +805,8 @@ sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t
   for (int64_t o = 0; o < n; ++o) {
     const int64_t k = where[o];
     tmp.clear();
-    for (uint32_t t = 0; t < cnt[(size_t)k]; ++t) tmp.push_back(id[list[(size_t)t * n + k]]);
+    for (uint32_t t = 0; t < cnt[(size_t)k]; ++t)
+      tmp.push_back(id[list[(size_t)nbr_slot(n, k, t)] & kNbrIndexMask]);
     std::sort(tmp.begin(), tmp.end());
     for (size_t t = 0; t < tmp.size(); ++t) nbr[offsets[o] + (int64_t)t] = tmp[t];
   }

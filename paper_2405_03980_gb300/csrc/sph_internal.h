@@ -133,11 +133,61 @@ struct CellWs {
   int64_t n_scan_blocks;
 };
 
+// Neighbour lists.  Entry t of particle i lives at nbr_slot(n, i, t): groups
+// of 8 consecutive entries of one particle form one 32-byte sector, and the
+// groups of consecutive particles are adjacent ([cap/8][n][8]), so a warp
+// writes whole sectors and reads 1 KB contiguous per group.  An entry holds
+// the neighbour's sorted index in its low 26 bits and, in the top 6 bits, the
+// cell displacement code (dx+1) | (dy+1) << 2 | (dz+1) << 4 of the neighbour's
+// cell relative to the particle's own (used by the mixed form).
+constexpr int kNbrGroup = 8;
+constexpr uint32_t kNbrIndexBits = 26;
+constexpr uint32_t kNbrIndexMask = (1u << kNbrIndexBits) - 1u;
+constexpr int64_t kMaxParticles = (int64_t)1 << kNbrIndexBits;  // 67,108,864
+
+__host__ __device__ __forceinline__ int64_t nbr_slot(int64_t n, int64_t i, uint32_t t) {
+  return (((int64_t)(t >> 3) * n + i) << 3) + (int64_t)(t & 7u);
+}
+
 struct NbrWs {
-  uint32_t* list;       // [cap][n] column-major neighbour indices (sorted space)
+  uint32_t* list;       // neighbour entries, layout above
   uint32_t* count;      // neighbours per particle
-  float4* posf;         // FP32 copy of sorted positions (prefilter)
-  int32_t cap;
+  float4* posf;         // FP32 copy of sorted positions (FP64-form prefilter)
+  int32_t cap;          // slots per particle (multiple of 8)
 };
+
+#ifdef __CUDACC__
+// Per-thread neighbour-list builder: entries are staged in shared memory and
+// written to global memory 8 at a time as one full 32-byte sector.  Entries
+// beyond nw.cap are counted (total) but dropped.
+constexpr int kStageStride = 9;  // words of shared staging per thread (8 used)
+
+struct ListWriter {
+  uint32_t* list;
+  int64_t n, i;
+  uint32_t* st;
+  uint32_t cap;
+  uint32_t cnt = 0, total = 0;
+  __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
+      : list(nw.list), n(n_), i(i_), st(st_), cap((uint32_t)nw.cap) {}
+  __device__ __forceinline__ void flush(uint32_t group) {
+    uint4* dst = reinterpret_cast<uint4*>(list + nbr_slot(n, i, group << 3));
+    dst[0] = make_uint4(st[0], st[1], st[2], st[3]);
+    dst[1] = make_uint4(st[4], st[5], st[6], st[7]);
+  }
+  __device__ __forceinline__ void append(uint32_t e) {
+    ++total;
+    if (cnt >= cap) return;
+    st[cnt & 7u] = e;
+    if ((cnt & 7u) == 7u) flush(cnt >> 3);
+    ++cnt;
+  }
+  // Flush the last partial group; returns the number of stored entries.
+  __device__ __forceinline__ uint32_t finish() {
+    if (cnt & 7u) flush(cnt >> 3);
+    return cnt;
+  }
+};
+#endif
 
 }  // namespace sphgb

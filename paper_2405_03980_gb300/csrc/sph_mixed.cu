@@ -101,20 +101,20 @@ __device__ __forceinline__ bool normalize(float& o, int& c, float L, int lo, int
   return ok;
 }
 
-// Pair vector r_i - r_j from cells and offsets (exactly antisymmetric).
-__device__ __forceinline__ void pair_vec(const InstDev& P, uint32_t ci, const float4& oi,
-                                         uint32_t cj, const float4& oj, float& dx, float& dy,
-                                         float& dz) {
-  const int ex = cell_x(ci) - cell_x(cj);
-  const int ey = cell_y(ci) - cell_y(cj);
-  int ez = cell_z(ci) - cell_z(cj);
-  if (P.periodic_z) {
-    if (ez > 1) ez -= P.nz;
-    else if (ez < -1) ez += P.nz;
-  }
-  dx = (float)ex * P.cellf[0] + (oi.x - oj.x);
-  dy = (float)ey * P.cellf[1] + (oi.y - oj.y);
-  dz = (float)ez * P.cellf[2] + (oi.z - oj.z);
+// Pair vector r_i - r_j = (c_i - c_j) L + (o_i - o_j) from a neighbour-list
+// entry (whose top bits carry c_i - c_j + 1 per axis) and the two offsets;
+// exactly antisymmetric, and bit-identical to the candidate test that wrote
+// the entry.
+__device__ __forceinline__ void entry_vec(const InstDev& P, uint32_t ent, const float4& oi,
+                                          const float4& oj, float& dx, float& dy, float& dz) {
+  const uint32_t c = ent >> kNbrIndexBits;
+  const float ex = (float)((int)(c & 3u) - 1);
+  const float ey = (float)((int)((c >> 2) & 3u) - 1);
+  const float ez = (float)((int)(c >> 4) - 1);
+  const float exL = ex * P.cellf[0], eyL = ey * P.cellf[1], ezL = ez * P.cellf[2];
+  dx = exL + (oi.x - oj.x);
+  dy = eyL + (oi.y - oj.y);
+  dz = ezL + (oi.z - oj.z);
 }
 
 __device__ __forceinline__ bool finite3f(float a, float b, float c) {
@@ -230,6 +230,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
                 NbrWs nw, uint32_t* err) {
+  __shared__ uint32_t stage[BLOCK * kStageStride];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -243,39 +244,46 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     delta = 0.f;
   } else {
     const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
-    const uint32_t cap = (uint32_t)nw.cap;
     const float cut2 = P.cut2_f;
+    ListWriter lw(nw, n, i, stage + threadIdx.x * kStageStride);
+    // the 27 neighbour cells as 9 rows of 3 x-adjacent cells; within a row the
+    // three cells are consecutive runs of the sorted order, so the cell
+    // displacement of every candidate is known without reading its cell
     for (int dz = -1; dz <= 1; ++dz) {
       int z2 = cz + dz;
       if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
+      const float ezL = (float)(-dz) * P.cellf[2];
       for (int dy = -1; dy <= 1; ++dy) {
         const int64_t row = P.cell_base + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2);
-        const uint32_t s = cw.start[row + cx - 1];
-        const uint32_t e = cw.start[row + cx + 2];
-        for (uint32_t j = s; j < e; ++j) {
-          if (j == (uint32_t)i) continue;
-          float dx, dy2, dz2;
-          pair_vec(P, ci, oi, b.cell[j], b.off[j], dx, dy2, dz2);
-          const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          if (r2 < cut2) {
-            if (cnt < cap) nw.list[(int64_t)cnt * n + i] = j;
-            ++cnt;
+        const float eyL = (float)(-dy) * P.cellf[1];
+        uint32_t a = cw.start[row + cx - 1];
+        for (int dx = -1; dx <= 1; ++dx) {
+          const uint32_t e = cw.start[row + cx + dx + 1];
+          const float exL = (float)(-dx) * P.cellf[0];
+          const uint32_t code = (uint32_t)((1 - dx) | ((1 - dy) << 2) | ((1 - dz) << 4))
+                                << kNbrIndexBits;
+          for (uint32_t j = a; j < e; ++j) {
+            const float4 oj = b.off[j];
+            const float ddx = exL + (oi.x - oj.x);
+            const float ddy = eyL + (oi.y - oj.y);
+            const float ddz = ezL + (oi.z - oj.z);
+            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2 < cut2 && j != (uint32_t)i) lw.append(j | code);
           }
+          a = e;
         }
       }
     }
-    if (cnt > cap) {
-      latch(err, ERR_NEIGHBORS);
-      cnt = cap;
-    }
+    cnt = lw.finish();
+    if (lw.total > (uint32_t)nw.cap) latch(err, ERR_NEIGHBORS);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
     for (uint32_t t = 0; t < cnt; ++t) {
-      const uint32_t j = nw.list[(int64_t)t * n + i];
-      const float4 oj = b.off[j];
+      const uint32_t ent = nw.list[nbr_slot(n, i, t)];
+      const float4 oj = b.off[ent & kNbrIndexMask];
       float dx, dy2, dz2;
-      pair_vec(P, ci, oi, b.cell[j], oj, dx, dy2, dz2);
+      entry_vec(P, ent, oi, oj, dx, dy2, dz2);
       const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
       const float q = sqrtf(r2) * P.inv_h_f;
       const float t1 = 1.f - 0.5f * q;
@@ -324,9 +332,9 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const uint32_t fl = P.flags;
   const float kP = (fl & SPH_TERM_P) ? 1.f : 0.f;
   const float kT = (fl & SPH_TERM_T) ? P.C_T_f : 0.f;
-  const float kSH = (fl & SPH_TERM_SH) ? -P.A_f : 0.f;
-  const float kR = (fl & SPH_TERM_ROT) ? -P.B_f : 0.f;
-  const float kSN = (fl & SPH_TERM_SN) ? -P.C_l_f : 0.f;
+  const float kA = (fl & SPH_TERM_SH) ? P.A_f : 0.f;
+  const float kB = (fl & SPH_TERM_ROT) ? P.B_f : 0.f;
+  const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
   const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
   const bool lit = (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
@@ -339,16 +347,18 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const uint32_t cnt = nw.count[i];
   for (uint32_t t = 0; t < cnt; ++t) {
-    const uint32_t j = nw.list[(int64_t)t * n + i];
+    const uint32_t ent = nw.list[nbr_slot(n, i, t)];
+    const uint32_t j = ent & kNbrIndexMask;
     const float4 oj = b.off[j];
     const float4 vj = b.vel[j];
     const float4 wj = b.spin[j];
     float dx, dy, dz;
-    pair_vec(P, ci, oi, b.cell[j], oj, dx, dy, dz);
+    entry_vec(P, ent, oi, oj, dx, dy, dz);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 > 0.f)) continue;  // coincident particles: density only
     const float inv_r = rsqrtf(r2);
     const float r = r2 * inv_r;
+    const float inv_r2 = inv_r * inv_r;
     const float q = r * P.inv_h_f;
     const float t1 = 1.f - 0.5f * q;
     const float t2 = t1 * t1;
@@ -366,31 +376,31 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     const float ux = vx + 0.5f * (dy * sz - dz * sy);
     const float uy = vy + 0.5f * (dz * sx - dx * sz);
     const float uz = vz + 0.5f * (dx * sy - dy * sx);
-    const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-    const float ev = ex * vx + ey * vy + ez * vz;
-    const float eu = ex * ux + ey * uy + ez * uz;
-    const float sP = kP * MM * ((wi.w + wj.w) * F);
-    const float sT = kT * mX * (VV * F);
-    const float sSH = kSH * mV * (VV * F) * ev;
-    const float sR = kR * mV * (VV * F);
-    const float sSN = kSN * mX * (VV * W);
-    const float frx = sR * (ux - eu * ex);
-    const float fry = sR * (uy - eu * ey);
-    const float frz = sR * (uz - eu * ez);
-    const float gx = lit ? vx : ux, gy = lit ? vy : uy, gz = lit ? vz : uz;
-    const float fnx = sSN * gx, fny = sSN * gy, fnz = sSN * gz;
-    const float pfx = (sP + sT) * dx + sSH * ex + frx + fnx;
-    const float pfy = (sP + sT) * dy + sSH * ey + fry + fny;
-    const float pfz = (sP + hz * sT) * dz + sSH * ez + frz + fnz;
+    const float dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij (symmetric)
+    const float du = dx * ux + dy * uy + dz * uz;  // r_ij . u_ij (symmetric)
+    // the five terms collected along r_ij, u_ij and (literal F_sn) v_ij:
+    // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F du/r^2 r_ij
+    const float VF = VV * F;
+    const float aP = kP * MM * ((wi.w + wj.w) * F);
+    const float aT = kT * mX * VF;
+    const float aV = VF * mV * inv_r2 * (kB * du - kA * dv);
+    const float bR = -kB * mV * VF;
+    const float bN = -kN * mX * (VV * W);
+    const float al = aP + aT + aV;
+    const float alz = aP + hz * aT + aV;
+    const float bu = lit ? bR : bR + bN;
+    const float bv = lit ? bN : 0.f;
+    const float pfx = al * dx + bu * ux + bv * vx;
+    const float pfy = al * dy + bu * uy + bv * vy;
+    const float pfz = alz * dz + bu * uz + bv * vz;
     fx.add(pfx);
     fy.add(pfy);
     fz.add(pfz);
-    const float kx = lit ? frx : frx + fnx;
-    const float ky = lit ? fry : fry + fny;
-    const float kz = lit ? frz : frz + fnz;
-    const float qx = -0.5f * (dy * kz - dz * ky);
-    const float qy = -0.5f * (dz * kx - dx * kz);
-    const float qz = -0.5f * (dx * ky - dy * kx);
+    // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
+    const float hb = -0.5f * bu;
+    const float qx = hb * (dy * uz - dz * uy);
+    const float qy = hb * (dz * ux - dx * uz);
+    const float qz = hb * (dx * uy - dy * ux);
     tx.add(qx);
     ty.add(qy);
     tz.add(qz);
