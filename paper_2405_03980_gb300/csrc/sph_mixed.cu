@@ -279,9 +279,16 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
+    uint32_t ent_n = cnt > 0 ? nw.list[nbr_slot(n, i, 0)] : 0u;
+    float4 oj_n = cnt > 0 ? b.off[ent_n & kNbrIndexMask] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t t = 0; t < cnt; ++t) {
-      const uint32_t ent = nw.list[nbr_slot(n, i, t)];
-      const float4 oj = b.off[ent & kNbrIndexMask];
+      // the next entry and its offset record are loaded one pair ahead
+      const uint32_t ent = ent_n;
+      const float4 oj = oj_n;
+      if (t + 1 < cnt) {
+        ent_n = nw.list[nbr_slot(n, i, t + 1)];
+        oj_n = b.off[ent_n & kNbrIndexMask];
+      }
       float dx, dy2, dz2;
       entry_vec(P, ent, oi, oj, dx, dy2, dz2);
       const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
@@ -346,12 +353,29 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const uint32_t cnt = nw.count[i];
+  // software pipeline: the list entry two ahead and the neighbour record one
+  // ahead are in flight while the current pair is evaluated
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t ent_n = cnt > 0 ? nw.list[nbr_slot(n, i, 0)] : 0u;
+  uint32_t ent_nn = cnt > 1 ? nw.list[nbr_slot(n, i, 1)] : 0u;
+  float4 oj_n = zero4, vj_n = zero4, wj_n = zero4;
+  if (cnt > 0) {
+    const uint32_t j0 = ent_n & kNbrIndexMask;
+    oj_n = b.off[j0];
+    vj_n = b.vel[j0];
+    wj_n = b.spin[j0];
+  }
   for (uint32_t t = 0; t < cnt; ++t) {
-    const uint32_t ent = nw.list[nbr_slot(n, i, t)];
-    const uint32_t j = ent & kNbrIndexMask;
-    const float4 oj = b.off[j];
-    const float4 vj = b.vel[j];
-    const float4 wj = b.spin[j];
+    const uint32_t ent = ent_n;
+    const float4 oj = oj_n, vj = vj_n, wj = wj_n;
+    ent_n = ent_nn;
+    if (t + 1 < cnt) {
+      const uint32_t jn = ent_n & kNbrIndexMask;
+      oj_n = b.off[jn];
+      vj_n = b.vel[jn];
+      wj_n = b.spin[jn];
+    }
+    if (t + 2 < cnt) ent_nn = nw.list[nbr_slot(n, i, t + 2)];
     float dx, dy, dz;
     entry_vec(P, ent, oi, oj, dx, dy, dz);
     const float r2 = dx * dx + dy * dy + dz * dz;
