@@ -197,6 +197,16 @@ SPH_API sph_status sph_check(sph_ctx* ctx);
 SPH_API sph_status sph_profile_steps(sph_ctx* ctx, int32_t nsteps, double* stage_ms,
                                      int32_t n_stages);
 SPH_API int32_t sph_stage_count(void);
+
+/* Autotune the launch shape of the density and pair passes: each candidate
+ * block size (64, 128, 256 threads) is timed over reps launches on the current
+ * state with CUDA events, the fastest is kept for later steps, and the step
+ * graphs are re-captured on the next sph_step.  The trials recompute the same
+ * neighbour lists, densities and forces, so the state is unchanged.
+ * *block_density and *block_forces (may be NULL) receive the choice.
+ * Synchronises. */
+SPH_API sph_status sph_autotune(sph_ctx* ctx, int32_t reps, int32_t* block_density,
+                                int32_t* block_forces);
 SPH_API const char* sph_stage_name(int32_t stage);
 
 /* Number of kernel launches one sph_step(ctx, 1) enqueues. */

@@ -93,6 +93,8 @@ def lib(build_if_missing: bool = True):
                 "sph_launches_per_step": (C.c_int32, [vp]),
                 "sph_profile_steps": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.c_int32]),
                 "sph_stage_count": (C.c_int32, []),
+                "sph_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32)]),
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
@@ -113,6 +115,7 @@ def exported_symbols() -> list[str]:
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
+            "sph_autotune",
             "sph_fma_peak", "sph_diag_sums_noalloc", "sph_destroy", "sph_status_string"]
 
 
@@ -270,6 +273,12 @@ def sph_diag_sums_noalloc(params, n, pos, vel, spin, species, rho, out, stream=0
     _ck(lib().sph_diag_sums_noalloc(C.byref(params), int(n), _ptr(pos), _ptr(vel), _ptr(spin),
                                     _ptr(species), _ptr(rho), _ptr(out), stream or None),
         "sph_diag_sums_noalloc")
+
+
+def sph_autotune(ctx, reps: int = 3) -> tuple[int, int]:
+    bd, bf = C.c_int32(), C.c_int32()
+    _ck(lib().sph_autotune(ctx, int(reps), C.byref(bd), C.byref(bf)), "sph_autotune")
+    return bd.value, bf.value
 
 
 def sph_destroy(ctx):

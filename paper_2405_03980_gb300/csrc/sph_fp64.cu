@@ -201,27 +201,21 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     // phase 1: FP32 prefilter over the 27 neighbour cells (9 contiguous runs,
     // x is the fastest cell index) into the provisional neighbour list
     ListWriter pre(nw, n, i, st);
-    for (int dz = -1; dz <= 1; ++dz) {
-      int z2 = cz + dz;
-      if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int64_t row = P.cell_base + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2);
-        const uint32_t s = cw.start[row + cx - 1];
-        const uint32_t e = cw.start[row + cx + 2];
-        for (uint32_t j = s; j < e; ++j) {
-          const float4 q = nw.posf[j];
-          float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
-          if (P.periodic_z) {
-            if (ddz > P.half_Hzf) ddz -= P.Hzf;
-            else if (ddz < -P.half_Hzf) ddz += P.Hzf;
-          }
-          const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2f < cut2f && j != (uint32_t)i) pre.append(j);
-        }
+    CellWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, cx, cy, cz, P.periodic_z != 0, 0.f,
+                  0.f, 0.f);
+    uint32_t j;
+    while (wk.next(&j)) {
+      const float4 q = nw.posf[j];
+      float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
+      if (P.periodic_z) {
+        if (ddz > P.half_Hzf) ddz -= P.Hzf;
+        else if (ddz < -P.half_Hzf) ddz += P.Hzf;
       }
+      const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+      if (r2f < cut2f && j != (uint32_t)i) pre.append(j);
     }
     cnt = pre.finish();
-    if (pre.total > (uint32_t)nw.cap) latch(err, ERR_NEIGHBORS);
+    if (pre.overflow()) latch(err, ERR_NEIGHBORS);
     // phase 2: exact FP64 cutoff (no fused multiply-add in r^2, strict <),
     // compaction of the list in place (a group is rewritten only after all
     // of its entries were read), and the density sum
@@ -450,9 +444,12 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches) {
-  (void)lc;
-  constexpr int B = 128;
-  k_density_fp64<B><<<(unsigned)((n + B - 1) / B), B, 0, s>>>(n, b, f, inst, cw, nw, err);
+  if (lc.block_density == 256)
+    k_density_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+  else if (lc.block_density == 64)
+    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+  else
+    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -460,9 +457,12 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  (void)lc;
-  constexpr int B = 128;
-  k_forces_fp64<B><<<(unsigned)((n + B - 1) / B), B, 0, s>>>(n, b, f, inst, nw, err);
+  if (lc.block_forces == 256)
+    k_forces_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, nw, err);
+  else if (lc.block_forces == 64)
+    k_forces_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, nw, err);
+  else
+    k_forces_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

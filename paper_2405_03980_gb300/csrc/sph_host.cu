@@ -846,6 +846,61 @@ sph_status sph_profile_steps(sph_ctx* c, int32_t nsteps, double* stage_ms, int32
   return sph_check(c);
 }
 
+sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_t* block_forces) {
+  if (!c || reps < 1) return SPH_ERR_ARG;
+  cudaStream_t s = c->stream;
+  // density and forces recompute the same lists, fields and wall torque from
+  // the same state, so the trials leave the state exactly as they found it
+  sph_status st = SPH_OK;
+  if (!c->lists_valid) st = enqueue_density(c, s, nullptr);
+  if (st != SPH_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return SPH_ERR_CUDA;
+  }
+  const int cand[3] = {64, 128, 256};
+  float best_d = INFINITY, best_f = INFINITY;
+  int bd = c->lc.block_density, bf = c->lc.block_forces;
+  for (int k = 0; k < 3 && st == SPH_OK; ++k) {
+    for (int which = 0; which < 2 && st == SPH_OK; ++which) {
+      LaunchCfg saved = c->lc;
+      if (which == 0) c->lc.block_density = cand[k];
+      else c->lc.block_forces = cand[k];
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && st == SPH_OK; ++r)
+        st = which == 0 ? enqueue_density(c, s, nullptr) : enqueue_forces(c, s, 0, nullptr);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (st == SPH_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = SPH_ERR_CUDA;
+      if (which == 0 && ms < best_d) best_d = ms, bd = cand[k];
+      if (which == 1 && ms < best_f) best_f = ms, bf = cand[k];
+      c->lc = saved;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SPH_OK) return st;
+  c->lc.block_density = bd;
+  c->lc.block_forces = bf;
+  // re-evaluate once with the chosen shapes and drop the graphs captured with
+  // the old ones; they are captured again by the next sph_step
+  st = enqueue_density(c, s, nullptr);
+  if (st == SPH_OK) st = enqueue_forces(c, s, 0, nullptr);
+  if (st != SPH_OK) return st;
+  c->forces_valid = true;
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) {
+      cudaGraphExecDestroy(c->graph[g]);
+      c->graph[g] = nullptr;
+    }
+  if (block_density) *block_density = bd;
+  if (block_forces) *block_forces = bf;
+  return sph_check(c);
+}
+
 int32_t sph_stage_count(void) { return kStages; }
 
 const char* sph_stage_name(int32_t stage) {

@@ -166,26 +166,78 @@ struct ListWriter {
   uint32_t* list;
   int64_t n, i;
   uint32_t* st;
-  uint32_t cap;
-  uint32_t cnt = 0, total = 0;
+  uint32_t groups;  // cap / 8
+  uint32_t cnt = 0;  // entries appended (may exceed the capacity)
   __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
-      : list(nw.list), n(n_), i(i_), st(st_), cap((uint32_t)nw.cap) {}
+      : list(nw.list), n(n_), i(i_), st(st_), groups((uint32_t)nw.cap >> 3) {}
   __device__ __forceinline__ void flush(uint32_t group) {
+    if (group >= groups) return;  // beyond the capacity: dropped
     uint4* dst = reinterpret_cast<uint4*>(list + nbr_slot(n, i, group << 3));
     dst[0] = make_uint4(st[0], st[1], st[2], st[3]);
     dst[1] = make_uint4(st[4], st[5], st[6], st[7]);
   }
   __device__ __forceinline__ void append(uint32_t e) {
-    ++total;
-    if (cnt >= cap) return;
     st[cnt & 7u] = e;
-    if ((cnt & 7u) == 7u) flush(cnt >> 3);
     ++cnt;
+    if ((cnt & 7u) == 0u) flush((cnt >> 3) - 1u);
   }
+  __device__ __forceinline__ bool overflow() const { return cnt > (groups << 3); }
   // Flush the last partial group; returns the number of stored entries.
   __device__ __forceinline__ uint32_t finish() {
     if (cnt & 7u) flush(cnt >> 3);
-    return cnt;
+    return cnt < (groups << 3) ? cnt : (groups << 3);
+  }
+};
+
+// Walks the candidates of one particle's 27 neighbour cells as one flat
+// sequence: 9 rows (dy, dz) of 3 x-adjacent cells, each row a contiguous run
+// of the sorted order split at the cell starts.  For the current candidate
+// it provides the cell displacement c_i - c_j (as -1/0/+1 times the cell
+// side per axis) and its 6-bit code.  One flat loop per thread keeps the
+// lanes of a warp in step even when they sit in different cells.
+struct CellWalker {
+  const uint32_t* start;
+  int64_t base;
+  int nx, ny, nz, cx, cy, cz;
+  bool periodic;
+  float Lx, Ly, Lz;
+  int kx = 2, ky = 2, kz = -1;
+  uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  uint32_t j = 0, e = 0;
+  float exL = 0.f, eyL = 0.f, ezL = 0.f;
+  uint32_t code_yz = 0, code = 0;
+  __device__ __forceinline__ CellWalker(const uint32_t* start_, int64_t base_, int nx_, int ny_,
+                                        int nz_, int cx_, int cy_, int cz_, bool periodic_,
+                                        float Lx_, float Ly_, float Lz_)
+      : start(start_), base(base_), nx(nx_), ny(ny_), nz(nz_), cx(cx_), cy(cy_), cz(cz_),
+        periodic(periodic_), Lx(Lx_), Ly(Ly_), Lz(Lz_) {}
+  // Next candidate index in *jj; false when all 27 cells are done.
+  __device__ __forceinline__ bool next(uint32_t* jj) {
+    while (j == e) {
+      if (++kx == 3) {
+        kx = 0;
+        if (++ky == 3) {
+          ky = 0;
+          if (++kz == 3) return false;
+        }
+        int z2 = cz + kz - 1;
+        if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
+        const int64_t row = base + (int64_t)nx * ((cy + ky - 1) + (int64_t)ny * z2);
+        r0 = start[row + cx - 1];
+        r1 = start[row + cx];
+        r2 = start[row + cx + 1];
+        r3 = start[row + cx + 2];
+        eyL = (float)(1 - ky) * Ly;
+        ezL = (float)(1 - kz) * Lz;
+        code_yz = ((uint32_t)(2 - ky) << 2) | ((uint32_t)(2 - kz) << 4);
+      }
+      j = kx == 0 ? r0 : (kx == 1 ? r1 : r2);
+      e = kx == 0 ? r1 : (kx == 1 ? r2 : r3);
+      exL = (float)(1 - kx) * Lx;
+      code = ((uint32_t)(2 - kx) | code_yz) << kNbrIndexBits;
+    }
+    *jj = j++;
+    return true;
   }
 };
 #endif

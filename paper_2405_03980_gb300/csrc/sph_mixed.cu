@@ -246,36 +246,22 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
     const float cut2 = P.cut2_f;
     ListWriter lw(nw, n, i, stage + threadIdx.x * kStageStride);
-    // the 27 neighbour cells as 9 rows of 3 x-adjacent cells; within a row the
-    // three cells are consecutive runs of the sorted order, so the cell
-    // displacement of every candidate is known without reading its cell
-    for (int dz = -1; dz <= 1; ++dz) {
-      int z2 = cz + dz;
-      if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
-      const float ezL = (float)(-dz) * P.cellf[2];
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int64_t row = P.cell_base + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2);
-        const float eyL = (float)(-dy) * P.cellf[1];
-        uint32_t a = cw.start[row + cx - 1];
-        for (int dx = -1; dx <= 1; ++dx) {
-          const uint32_t e = cw.start[row + cx + dx + 1];
-          const float exL = (float)(-dx) * P.cellf[0];
-          const uint32_t code = (uint32_t)((1 - dx) | ((1 - dy) << 2) | ((1 - dz) << 4))
-                                << kNbrIndexBits;
-          for (uint32_t j = a; j < e; ++j) {
-            const float4 oj = b.off[j];
-            const float ddx = exL + (oi.x - oj.x);
-            const float ddy = eyL + (oi.y - oj.y);
-            const float ddz = ezL + (oi.z - oj.z);
-            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < cut2 && j != (uint32_t)i) lw.append(j | code);
-          }
-          a = e;
-        }
-      }
+    // the 27 neighbour cells as one flat candidate sequence; the cell
+    // displacement of every candidate is known from its run, without reading
+    // the candidate's cell
+    CellWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, cx, cy, cz, P.periodic_z != 0,
+                  P.cellf[0], P.cellf[1], P.cellf[2]);
+    uint32_t j;
+    while (wk.next(&j)) {
+      const float4 oj = b.off[j];
+      const float ddx = wk.exL + (oi.x - oj.x);
+      const float ddy = wk.eyL + (oi.y - oj.y);
+      const float ddz = wk.ezL + (oi.z - oj.z);
+      const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+      if (r2 < cut2 && j != (uint32_t)i) lw.append(j | wk.code);
     }
     cnt = lw.finish();
-    if (lw.total > (uint32_t)nw.cap) latch(err, ERR_NEIGHBORS);
+    if (lw.overflow()) latch(err, ERR_NEIGHBORS);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
@@ -350,7 +336,10 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
   const double zi = P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z;
   const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
+  // compensated sums across groups of 8 neighbours (one list group), plain
+  // FP32 sums inside a group
   Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
+  float gfx = 0.f, gfy = 0.f, gfz = 0.f, gtx = 0.f, gty = 0.f, gtz = 0.f;
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const uint32_t cnt = nw.count[i];
   // software pipeline: the list entry two ahead and the neighbour record one
@@ -379,7 +368,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     float dx, dy, dz;
     entry_vec(P, ent, oi, oj, dx, dy, dz);
     const float r2 = dx * dx + dy * dy + dz * dz;
-    if (!(r2 > 0.f)) continue;  // coincident particles: density only
+    if (r2 > 0.f) {  // coincident particles: density only
     const float inv_r = rsqrtf(r2);
     const float r = r2 * inv_r;
     const float inv_r2 = inv_r * inv_r;
@@ -417,21 +406,31 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     const float pfx = al * dx + bu * ux + bv * vx;
     const float pfy = al * dy + bu * uy + bv * vy;
     const float pfz = alz * dz + bu * uz + bv * vz;
-    fx.add(pfx);
-    fy.add(pfy);
-    fz.add(pfz);
+    gfx += pfx;
+    gfy += pfy;
+    gfz += pfz;
     // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
     const float hb = -0.5f * bu;
     const float qx = hb * (dy * uz - dz * uy);
     const float qy = hb * (dz * ux - dx * uz);
     const float qz = hb * (dx * uy - dy * ux);
-    tx.add(qx);
-    ty.add(qy);
-    tz.add(qz);
+    gtx += qx;
+    gty += qy;
+    gtz += qz;
     if (oj.w >= 2.f) {
       wx += pyi * pfz - pzi * pfy + qx;
       wy += pzi * pfx - pxi * pfz + qy;
       wz += pxi * pfy - pyi * pfx + qz;
+    }
+    }
+    if ((t & 7u) == 7u || t + 1 == cnt) {
+      fx.add(gfx);
+      fy.add(gfy);
+      fz.add(gfz);
+      tx.add(gtx);
+      ty.add(gty);
+      tz.add(gtz);
+      gfx = gfy = gfz = gtx = gty = gtz = 0.f;
     }
   }
   const float inv_m = P.inv_m_f[si], inv_I = P.inv_I_f[si];

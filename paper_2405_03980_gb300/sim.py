@@ -90,6 +90,9 @@ class Simulation:
     def profile(self, nsteps: int) -> dict:
         return B.sph_profile_steps(self.ctx, nsteps)
 
+    def autotune(self, reps: int = 3) -> tuple[int, int]:
+        return B.sph_autotune(self.ctx, reps)
+
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)
 

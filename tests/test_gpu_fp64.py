@@ -220,3 +220,27 @@ def test_device_errors_are_latched_not_trapped():
     ok.step(1)
     ok.check()
     ok.close()
+
+
+@pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
+def test_autotune_leaves_state_and_results_unchanged(precision):
+    """The autotuner times launch shapes on the current state; per-particle
+    results do not depend on the block size, so the state after tuning and the
+    trajectory that follows are bit-identical to an untuned run."""
+    c = synth.workload("cyl_8960", seed=4)
+    a = sim_of(c, precision=precision)
+    b = sim_of(c, precision=precision)
+    a.step(2)
+    b.step(2)
+    bd, bf = b.autotune(2)
+    assert bd in (64, 128, 256) and bf in (64, 128, 256)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    for f in sa:
+        assert np.array_equal(sa[f], sb[f]), f
+    a.step(3)
+    b.step(3)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    for f in sa:
+        assert np.array_equal(sa[f], sb[f]), f
+    a.close()
+    b.close()
