@@ -214,10 +214,10 @@ def cpu_baseline(c, n_sample=0):
 
 
 def run_reference(args, dist):
-    from paper_2405_03980_gb300 import synth
     if dist.rank != 0:
         return
-    c = synth.workload(args.workload)
+    # the oracle is O(N) per row: the sample is drawn from the largest instance
+    c = max(load_workload(args.workload), key=lambda x: x.n)
     target = min(10.0, max(1.0, 90.0 / max(1, args.steps + args.warmup)))
     _, S, R, run, _ = oracle_sample(c, target_s=target, n_sample=args.cpu_sample)
     for _ in range(args.warmup):
@@ -243,12 +243,12 @@ def run_reference(args, dist):
 
 # ------------------------------------------------------------------ GPU leg
 
-def time_form(c, precision, args, dist, dev):
+def time_form(insts, precision, args, dist, dev):
     import torch
     from paper_2405_03980_gb300 import _binding as B
     from paper_2405_03980_gb300.sim import Simulation
 
-    sim = Simulation(c, precision=precision, device=f"cuda:{dev}")
+    sim = Simulation(insts, precision=precision, device=f"cuda:{dev}")
     stream = sim.stream
     blocks = None if args.no_autotune else sim.autotune(2)
     sim.step(args.warmup)
@@ -270,6 +270,7 @@ def time_form(c, precision, args, dist, dev):
     ms = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms)
     diag = sim.diagnostics()
+    diag["n_pairs"] = sum(sim.diagnostics(k)["n_pairs"] for k in range(len(insts)))
     stages = sim.profile(args.profile_steps)
     launches = sim.launches_per_step()
     out = {"ms_per_step": ms, "diag": diag, "stages": stages, "clocks": ck,
@@ -277,19 +278,30 @@ def time_form(c, precision, args, dist, dev):
     return out
 
 
-def e2e_buffers(c):
+def e2e_buffers(insts):
     """Pinned host copies of the inputs and of the state read back."""
     import torch
 
-    def pinned(a):
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    def pinned(parts):
+        t = torch.from_numpy(np.ascontiguousarray(np.concatenate(parts))).pin_memory()
         return t
 
-    pos, vel, spin = pinned(c.pos), pinned(c.vel), pinned(c.spin)
-    sp = pinned(c.species)
-    out_pos, out_vel, out_spin = (torch.empty((c.n, 3), dtype=torch.float64).pin_memory()
+    pos = pinned([c.pos for c in insts])
+    vel = pinned([c.vel for c in insts])
+    spin = pinned([c.spin for c in insts])
+    sp = pinned([c.species for c in insts])
+    n = sum(c.n for c in insts)
+    out_pos, out_vel, out_spin = (torch.empty((n, 3), dtype=torch.float64).pin_memory()
                                   for _ in range(3))
     return pos, vel, spin, sp, out_pos, out_vel, out_spin
+
+
+def load_workload(name):
+    """A named cylinder, or "ensembleK": K uneven cylinders advanced together."""
+    from paper_2405_03980_gb300 import synth
+    if name.startswith("ensemble"):
+        return synth.ensemble(int(name[len("ensemble"):] or 64))
+    return [synth.workload(name, seed=0)]
 
 
 def run_ours(args, dist):
@@ -300,15 +312,16 @@ def run_ours(args, dist):
     dev = dist.local
     torch.cuda.set_device(dev)
     B.lib(build_if_missing=True)
-    c = synth.workload(args.workload, seed=0)
+    insts = load_workload(args.workload)
+    n_part = sum(c.n for c in insts)
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     prec = {"fp64": B.SPH_FP64, "mixed": B.SPH_MIXED}
     results = {}
     for f in forms:
-        results[f] = time_form(c, prec[f], args, dist, dev)
+        results[f] = time_form(insts, prec[f], args, dist, dev)
     best = min(results, key=lambda f: results[f]["ms_per_step"])
     r = results[best]
-    n_total = c.n * dist.world
+    n_total = n_part * dist.world
     value = n_total / (r["ms_per_step"] * 1e-3)
     pairs = r["diag"]["n_pairs"]
 
@@ -338,7 +351,7 @@ def run_ours(args, dist):
     e2e = None
     if not args.no_e2e:
         sim = r["sim"]
-        pos, vel, spin, sp, opos, ovel, ospin = e2e_buffers(c)
+        pos, vel, spin, sp, opos, ovel, ospin = e2e_buffers(insts)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         sim.reinit(pos, vel, spin, sp)
@@ -348,8 +361,8 @@ def run_ours(args, dist):
         B.sph_get_state(sim.ctx, opos, ovel, ospin)
         t = time.perf_counter() - t0
         t = dist.max(t)
-        h2d = c.n * (3 * 3 * 8 + 1)
-        d2h = args.steps * 8 * 33 + c.n * 3 * 3 * 8
+        h2d = n_part * (3 * 3 * 8 + 1)
+        d2h = args.steps * 8 * 33 + n_part * 3 * 3 * 8
         e2e = {"value": n_total * args.steps / t, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "sph_init from pinned host state (initial density+forces), "
@@ -359,7 +372,7 @@ def run_ours(args, dist):
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(c, n_sample=args.cpu_sample)
+        cpu = cpu_baseline(max(insts, key=lambda c: c.n), n_sample=args.cpu_sample)
 
     if dist.rank == 0:
         forms_out = {f: {"ms_per_step": results[f]["ms_per_step"],
@@ -375,9 +388,12 @@ def run_ours(args, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if best == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "particles": c.n, "fluid": c.n_fluid,
-                       "R": c.R, "H": c.H, "form": best, "parallelism": "replicas",
-                       "l2": "inputs larger than L2 (~6 GB state), no flush"},
+            "config": {"workload": args.workload, "particles": n_part,
+                       "fluid": sum(c.n_fluid for c in insts), "instances": len(insts),
+                       "R": insts[0].R if len(insts) == 1 else None,
+                       "H": insts[0].H if len(insts) == 1 else None,
+                       "form": best, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (state of GBs), no flush"},
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,
             "roofline": roof,

@@ -202,7 +202,9 @@ SPH_API int32_t sph_stage_count(void);
  * block size (64, 128, 256 threads) is timed over reps launches on the current
  * state with CUDA events, the fastest is kept for later steps, and the step
  * graphs are re-captured on the next sph_step.  The trials recompute the same
- * neighbour lists, densities and forces, so the state is unchanged.
+ * neighbour lists and densities; the pair-pass outputs (which a step computed
+ * from half-step velocities) are saved in the workspace and restored, so the
+ * state is left bit for bit as it was.
  * *block_density and *block_forces (may be NULL) receive the choice.
  * Synchronises. */
 SPH_API sph_status sph_autotune(sph_ctx* ctx, int32_t reps, int32_t* block_density,

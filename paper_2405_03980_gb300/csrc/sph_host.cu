@@ -191,6 +191,7 @@ struct sph_ctx {
   double* part_tw = nullptr;
   double* part_diag = nullptr;
   double* diag_out = nullptr;
+  char* backup = nullptr;        // autotuner copy of acc, dspin, wall torque, InstState
   void* staging = nullptr;
   size_t staging_bytes = 0;
   cudaStream_t stream = nullptr;
@@ -215,8 +216,18 @@ struct Carved {
   InstState* ist;
   uint32_t* err;
   double *part_tw, *part_diag, *diag_out;
+  char* backup;
   size_t state_bytes, ws_bytes;
 };
+
+// Per-particle fields the pair pass writes (acc, dspin, wall torque) and the
+// per-instance scalars: what sph_autotune saves and restores.
+int64_t field_bytes(int32_t precision, int64_t n) {
+  return (int64_t)(precision == SPH_FP64 ? sizeof(dvec4) : sizeof(float4)) * n;
+}
+int64_t backup_bytes(int32_t precision, int64_t n, int32_t n_inst) {
+  return 3 * field_bytes(precision, n) + (int64_t)sizeof(InstState) * n_inst + 3 * 256;
+}
 
 void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
            int64_t total_chunks, int32_t cap, int32_t precision, Carved& c) {
@@ -274,6 +285,7 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.part_tw = w.take<double>(3 * total_chunks);
   c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
   c.diag_out = w.take<double>((int64_t)kDiagFields * n_inst);
+  c.backup = w.take<char>(backup_bytes(precision, n, n_inst));
   c.ws_bytes = w.off + kAlign;
 }
 
@@ -568,6 +580,7 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->part_tw = cv.part_tw;
   c->part_diag = cv.part_diag;
   c->diag_out = cv.diag_out;
+  c->backup = cv.backup;
   c->staging = cv.nw.list;
   c->staging_bytes = sizeof(uint32_t) * (size_t)pl.cap * (size_t)pl.n;
   c->stream = (cudaStream_t)stream;
@@ -849,11 +862,35 @@ sph_status sph_profile_steps(sph_ctx* c, int32_t nsteps, double* stage_ms, int32
 sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_t* block_forces) {
   if (!c || reps < 1) return SPH_ERR_ARG;
   cudaStream_t s = c->stream;
-  // density and forces recompute the same lists, fields and wall torque from
-  // the same state, so the trials leave the state exactly as they found it
+  // The density pass is a function of the positions alone, so repeating it
+  // reproduces the same lists and fields.  The pair pass of a step used the
+  // half-step velocities, which are gone after the step: its outputs (acc,
+  // dspin, wall torque and the per-instance torque record) are saved first
+  // and restored after the trials.
   sph_status st = SPH_OK;
   if (!c->lists_valid) st = enqueue_density(c, s, nullptr);
   if (st != SPH_OK) return st;
+  const size_t fb = (size_t)field_bytes(c->precision, c->n);
+  void* fields[3];
+  if (mixed(c)) {
+    fields[0] = c->mf.acc;
+    fields[1] = c->mf.dspin;
+    fields[2] = c->mf.tw;
+  } else {
+    fields[0] = c->f.acc;
+    fields[1] = c->f.dspin;
+    fields[2] = c->f.tw;
+  }
+  char* bk[4];
+  {
+    size_t off = 0;
+    for (int k = 0; k < 4; ++k) {
+      bk[k] = c->backup + off;
+      off += ((k < 3 ? fb : sizeof(InstState) * (size_t)c->n_inst) + 255) / 256 * 256;
+    }
+  }
+  for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(bk[k], fields[k], fb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(bk[3], c->ist, sizeof(InstState) * c->n_inst, cudaMemcpyDeviceToDevice, s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -885,12 +922,12 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
   if (st != SPH_OK) return st;
   c->lc.block_density = bd;
   c->lc.block_forces = bf;
-  // re-evaluate once with the chosen shapes and drop the graphs captured with
-  // the old ones; they are captured again by the next sph_step
+  // restore the pair-pass outputs, and drop the graphs captured with the old
+  // shapes; they are captured again by the next sph_step
   st = enqueue_density(c, s, nullptr);
-  if (st == SPH_OK) st = enqueue_forces(c, s, 0, nullptr);
   if (st != SPH_OK) return st;
-  c->forces_valid = true;
+  for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(fields[k], bk[k], fb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->ist, bk[3], sizeof(InstState) * c->n_inst, cudaMemcpyDeviceToDevice, s));
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {
       cudaGraphExecDestroy(c->graph[g]);
