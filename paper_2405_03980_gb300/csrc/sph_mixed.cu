@@ -251,14 +251,32 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // the candidate's cell
     CellWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, cx, cy, cz, P.periodic_z != 0,
                   P.cellf[0], P.cellf[1], P.cellf[2]);
-    uint32_t j;
-    while (wk.next(&j)) {
-      const float4 oj = b.off[j];
-      const float ddx = wk.exL + (oi.x - oj.x);
-      const float ddy = wk.eyL + (oi.y - oj.y);
-      const float ddz = wk.ezL + (oi.z - oj.z);
+    // one candidate ahead is in flight while the current one is tested; the
+    // test uses the same antisymmetric pair vector as every later use of the
+    // entry, so j lists i exactly when i lists j
+    uint32_t jn = 0;
+    bool more = wk.next(&jn);
+    float4 on = more ? b.off[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float exn = wk.exL, eyn = wk.eyL, ezn = wk.ezL;
+    uint32_t cn = wk.code;
+    while (more) {
+      const uint32_t j = jn;
+      const float4 oj = on;
+      const float exL = exn, eyL = eyn, ezL = ezn;
+      const uint32_t code = cn;
+      more = wk.next(&jn);
+      if (more) {
+        on = b.off[jn];
+        exn = wk.exL;
+        eyn = wk.eyL;
+        ezn = wk.ezL;
+        cn = wk.code;
+      }
+      const float ddx = exL + (oi.x - oj.x);
+      const float ddy = eyL + (oi.y - oj.y);
+      const float ddz = ezL + (oi.z - oj.z);
       const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      if (r2 < cut2 && j != (uint32_t)i) lw.append(j | wk.code);
+      if (r2 < cut2 && j != (uint32_t)i) lw.append(j | code);
     }
     cnt = lw.finish();
     if (lw.overflow()) latch(err, ERR_NEIGHBORS);
