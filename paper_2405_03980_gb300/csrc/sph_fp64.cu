@@ -55,7 +55,12 @@ __device__ __forceinline__ uint32_t cell_key(const InstDev& P, double x, double 
     }
   }
   if (bad) latch(err, ERR_ESCAPED);
-  return (uint32_t)(P.cell_base + c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2]));
+  // x-slab of the particle inside its cell
+  int slab = (int)floor(((r[0] - P.lo[0]) * P.inv_cell[0] - (double)c[0]) * P.slabs);
+  slab = slab < 0 ? 0 : (slab >= P.slabs ? P.slabs - 1 : slab);
+  return (uint32_t)(P.cell_base +
+                    ((int64_t)c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2])) * P.slabs +
+                    slab);
 }
 
 inline int grid_for(int64_t n, int threads, int sm_count, int per_sm) {
@@ -192,18 +197,22 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     rho = P.rho0;
   } else {
     const float4 pf = nw.posf[i];
-    const int64_t c = (int64_t)cw.skey[i] - P.cell_base;
+    const int64_t c = ((int64_t)cw.skey[i] - P.cell_base) / P.slabs;
     const int cx = (int)(c % P.nx);
     const int cy = (int)((c / P.nx) % P.ny);
     const int cz = (int)(c / ((int64_t)P.nx * P.ny));
     const float cut2f = P.cut2f_margin;
     uint32_t* st = stage + threadIdx.x * kStageStride;
-    // phase 1: FP32 prefilter over the 27 neighbour cells (9 contiguous runs,
-    // x is the fastest cell index) into the provisional neighbour list
+    // phase 1: FP32 prefilter over the x-windows of the 27 neighbour cells
+    // into the provisional neighbour list
     ListWriter pre(nw, n, i, st);
-    CellWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, cx, cy, cz, P.periodic_z != 0, 0.f,
-                  0.f, 0.f);
+    SlabWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
+                  cz, (float)P.cell[0], (float)P.cell[1], (float)P.cell[2],
+                  (float)((pi.x - P.lo[0]) - cx * P.cell[0]),
+                  (float)((pi.y - P.lo[1]) - cy * P.cell[1]),
+                  (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f);
     uint32_t j;
+    uint32_t it = 0;
     while (wk.next(&j)) {
       const float4 q = nw.posf[j];
       float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
@@ -212,7 +221,11 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
         else if (ddz < -P.half_Hzf) ddz += P.Hzf;
       }
       const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-      if (r2f < cut2f && j != (uint32_t)i) pre.append(j);
+      pre.push(j, r2f < cut2f && j != (uint32_t)i);
+      if (++it == kDrainEvery) {
+        pre.drain();
+        it = 0;
+      }
     }
     cnt = pre.finish();
     if (pre.overflow()) latch(err, ERR_NEIGHBORS);
@@ -233,14 +246,16 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
       }
       const double r2 =
           __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      if (r2 < P.cut2) {
-        out.append(j);
+      const bool keep = r2 < P.cut2;
+      out.push(j, keep);
+      if (keep) {
         const double q = sqrt(r2) * P.inv_h;
         const double t1 = 1.0 - 0.5 * q;
         const double t2 = t1 * t1;
         const double m_j = pj.w == 0.0 ? P.m_s : P.m_n;
         rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
       }
+      if (((t + 1) & (kDrainEvery - 1)) == 0) out.drain();
     }
     cnt = out.finish();
   }

@@ -86,6 +86,7 @@ sph_status derive(const sph_params& p, InstDev& d) {
   d.alphaP = (int32_t)p.alpha_P;
   d.flags = p.flags;
   d.periodic_z = p.periodic_z ? 1 : 0;
+  d.slabs = kSlabs;
   const double side = 2.0 * h;
   double xmax = 0.0;
   int32_t n[3];
@@ -315,7 +316,7 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
     d.p_end = pb + counts[k];
     d.chunk_base = kb;
     d.n_chunks = (counts[k] + kReduceChunk - 1) / kReduceChunk;
-    cb += (int64_t)d.nx * d.ny * d.nz;
+    cb += (int64_t)d.nx * d.ny * d.nz * d.slabs;
     pb += counts[k];
     kb += d.n_chunks;
   }

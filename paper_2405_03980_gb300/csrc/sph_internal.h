@@ -20,6 +20,7 @@ constexpr int kScanChunk = 4096;       // elements per block of the cell-count s
 constexpr int kReduceChunk = 32768;    // particles per partial of the FP64 reductions
 constexpr int kDiagFields = 24;        // doubles per diagnostics partial
 constexpr int kMaxInst = 65535;
+constexpr int kSlabs = 4;              // x-slabs per cell in the sort key
 
 // Error bits latched on the device.
 enum : uint32_t {
@@ -49,7 +50,8 @@ struct InstDev {
   int32_t alphaP;                 // integer Tait exponent
   uint32_t flags;
   int32_t periodic_z;
-  int64_t cell_base;              // first global cell index of the instance
+  int32_t slabs;                  // x-slabs per cell: sort key = cell * slabs + slab
+  int64_t cell_base;              // first global sort key of the instance
   int64_t p_begin, p_end;         // particle range (fixed across sorts)
   int64_t chunk_base;             // first reduction chunk of the instance
   int64_t n_chunks;
@@ -157,84 +159,121 @@ struct NbrWs {
 };
 
 #ifdef __CUDACC__
-// Per-thread neighbour-list builder: entries are staged in shared memory and
-// written to global memory 8 at a time as one full 32-byte sector.  Entries
-// beyond nw.cap are counted (total) but dropped.
-constexpr int kStageStride = 9;  // words of shared staging per thread (8 used)
+// Per-thread neighbour-list builder.  push() stores every candidate entry in
+// the thread's shared-memory staging and advances the fill only if it is a
+// neighbour (no branch per candidate); drain(), called by all lanes of a warp
+// at the same points (every kDrainEvery pushes), writes the complete groups
+// of 8 as full 32-byte sectors and keeps the remainder.  Entries beyond
+// nw.cap are counted but dropped.
+constexpr int kDrainEvery = 32;
+constexpr int kStageWords = 40;  // >= 7 + kDrainEvery
+constexpr int kStageStride = 41;  // odd stride spreads the threads over banks
 
 struct ListWriter {
   uint32_t* list;
   int64_t n, i;
   uint32_t* st;
-  uint32_t groups;  // cap / 8
-  uint32_t cnt = 0;  // entries appended (may exceed the capacity)
+  uint32_t groups;       // cap / 8
+  uint32_t pend = 0;     // staged entries not yet written
+  uint32_t written = 0;  // groups written (or dropped beyond the capacity)
   __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
       : list(nw.list), n(n_), i(i_), st(st_), groups((uint32_t)nw.cap >> 3) {}
-  __device__ __forceinline__ void flush(uint32_t group) {
-    if (group >= groups) return;  // beyond the capacity: dropped
-    uint4* dst = reinterpret_cast<uint4*>(list + nbr_slot(n, i, group << 3));
-    dst[0] = make_uint4(st[0], st[1], st[2], st[3]);
-    dst[1] = make_uint4(st[4], st[5], st[6], st[7]);
+  __device__ __forceinline__ void push(uint32_t e, bool keep) {
+    st[pend] = e;
+    pend += keep ? 1u : 0u;
   }
-  __device__ __forceinline__ void append(uint32_t e) {
-    st[cnt & 7u] = e;
-    ++cnt;
-    if ((cnt & 7u) == 0u) flush((cnt >> 3) - 1u);
+  __device__ __forceinline__ void write_group(uint32_t from) {
+    if (written < groups) {
+      uint4* dst = reinterpret_cast<uint4*>(list + nbr_slot(n, i, written << 3));
+      dst[0] = make_uint4(st[from], st[from + 1], st[from + 2], st[from + 3]);
+      dst[1] = make_uint4(st[from + 4], st[from + 5], st[from + 6], st[from + 7]);
+    }
+    ++written;
   }
-  __device__ __forceinline__ bool overflow() const { return cnt > (groups << 3); }
-  // Flush the last partial group; returns the number of stored entries.
+  __device__ __forceinline__ void drain() {
+    const uint32_t g = pend >> 3;
+    for (uint32_t k = 0; k < g; ++k) write_group(k << 3);
+    const uint32_t rem = pend & 7u;
+    for (uint32_t r = 0; r < rem; ++r) st[r] = st[(g << 3) + r];
+    pend = rem;
+  }
+  __device__ __forceinline__ uint32_t total() const { return (written << 3) + pend; }
+  __device__ __forceinline__ bool overflow() const { return total() > (groups << 3); }
+  // Write everything (the last group partially); returns the stored count.
   __device__ __forceinline__ uint32_t finish() {
-    if (cnt & 7u) flush(cnt >> 3);
-    return cnt < (groups << 3) ? cnt : (groups << 3);
+    drain();
+    const uint32_t t = total();
+    if (pend) write_group(0);
+    return t < (groups << 3) ? t : (groups << 3);
   }
 };
 
-// Walks the candidates of one particle's 27 neighbour cells as one flat
-// sequence: 9 rows (dy, dz) of 3 x-adjacent cells, each row a contiguous run
-// of the sorted order split at the cell starts.  For the current candidate
-// it provides the cell displacement c_i - c_j (as -1/0/+1 times the cell
-// side per axis) and its 6-bit code.  One flat loop per thread keeps the
-// lanes of a warp in step even when they sit in different cells.
-struct CellWalker {
+// Walks the candidates of one particle: the 9 rows (dy, dz) of the 27-cell
+// stencil, each row the 3 x-adjacent cells cx-1..cx+1, which the sort keeps
+// as one run of S x-slabs per cell.  A row out of reach (its nearest y-z
+// distance >= the cutoff) is skipped, and within a row only the slabs that
+// overlap the x-window |x_j - x_i| <= sqrt(cut^2 - d_yz^2) (+ margin) are
+// visited, split at the cell boundaries so that the cell displacement
+// c_i - c_j of every candidate is known (as -1/0/+1 times the cell side, and
+// as its 6-bit code).  One flat loop per thread keeps the lanes of a warp in
+// step.
+struct SlabWalker {
   const uint32_t* start;
   int64_t base;
-  int nx, ny, nz, cx, cy, cz;
+  int nx, ny, nz, cx, cy, cz, S;
   bool periodic;
-  float Lx, Ly, Lz;
-  int kx = 2, ky = 2, kz = -1;
-  uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  float Lx, Ly, Lz, ox, oy, oz, cut2, inv_slab;
+  int kr = -1, kc = 0, slo = 0, shi = -1;
+  int64_t rowkey = 0;
   uint32_t j = 0, e = 0;
   float exL = 0.f, eyL = 0.f, ezL = 0.f;
   uint32_t code_yz = 0, code = 0;
-  __device__ __forceinline__ CellWalker(const uint32_t* start_, int64_t base_, int nx_, int ny_,
-                                        int nz_, int cx_, int cy_, int cz_, bool periodic_,
-                                        float Lx_, float Ly_, float Lz_)
-      : start(start_), base(base_), nx(nx_), ny(ny_), nz(nz_), cx(cx_), cy(cy_), cz(cz_),
-        periodic(periodic_), Lx(Lx_), Ly(Ly_), Lz(Lz_) {}
-  // Next candidate index in *jj; false when all 27 cells are done.
+  // own cell (cx, cy, cz) and FP32 offsets (ox, oy, oz) inside it; cut2 is
+  // the squared cutoff the candidates are tested against.
+  __device__ __forceinline__ SlabWalker(const uint32_t* start_, int64_t base_, int nx_, int ny_,
+                                        int nz_, int S_, bool periodic_, int cx_, int cy_, int cz_,
+                                        float Lx_, float Ly_, float Lz_, float ox_, float oy_,
+                                        float oz_, float cut2_)
+      : start(start_), base(base_), nx(nx_), ny(ny_), nz(nz_), cx(cx_), cy(cy_), cz(cz_), S(S_),
+        periodic(periodic_), Lx(Lx_), Ly(Ly_), Lz(Lz_), ox(ox_), oy(oy_), oz(oz_), cut2(cut2_),
+        inv_slab((float)S_ / Lx_) {}
+  // Next candidate index in *jj; false when the stencil is exhausted.
   __device__ __forceinline__ bool next(uint32_t* jj) {
     while (j == e) {
-      if (++kx == 3) {
-        kx = 0;
-        if (++ky == 3) {
-          ky = 0;
-          if (++kz == 3) return false;
-        }
-        int z2 = cz + kz - 1;
+      if (kc * S > shi) {
+        // next row within reach
+        float d2;
+        int dy, dz;
+        do {
+          if (++kr == 9) return false;
+          dz = kr / 3 - 1;
+          dy = kr - 3 * (kr / 3) - 1;
+          const float ry = dy < 0 ? oy : (dy > 0 ? Ly - oy : 0.f);
+          const float rz = dz < 0 ? oz : (dz > 0 ? Lz - oz : 0.f);
+          d2 = ry * ry + rz * rz;
+        } while (d2 >= cut2 + 1e-3f);
+        const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
+        const float xr = Lx + ox;  // x relative to the start of cell cx-1
+        const int lo = (int)floorf((xr - w) * inv_slab);
+        const int hi = (int)floorf((xr + w) * inv_slab);
+        slo = lo < 0 ? 0 : lo;
+        shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
+        int z2 = cz + dz;
         if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
-        const int64_t row = base + (int64_t)nx * ((cy + ky - 1) + (int64_t)ny * z2);
-        r0 = start[row + cx - 1];
-        r1 = start[row + cx];
-        r2 = start[row + cx + 1];
-        r3 = start[row + cx + 2];
-        eyL = (float)(1 - ky) * Ly;
-        ezL = (float)(1 - kz) * Lz;
-        code_yz = ((uint32_t)(2 - ky) << 2) | ((uint32_t)(2 - kz) << 4);
+        rowkey = base + ((int64_t)(cx - 1) + (int64_t)nx * ((cy + dy) + (int64_t)ny * z2)) * S;
+        eyL = (float)(-dy) * Ly;
+        ezL = (float)(-dz) * Lz;
+        code_yz = ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4);
+        kc = slo / S;
+        continue;
       }
-      j = kx == 0 ? r0 : (kx == 1 ? r1 : r2);
-      e = kx == 0 ? r1 : (kx == 1 ? r2 : r3);
-      exL = (float)(1 - kx) * Lx;
-      code = ((uint32_t)(2 - kx) | code_yz) << kNbrIndexBits;
+      const int a = kc * S > slo ? kc * S : slo;
+      const int b = kc * S + S - 1 < shi ? kc * S + S - 1 : shi;
+      j = start[rowkey + a];
+      e = start[rowkey + b + 1];
+      exL = (float)(1 - kc) * Lx;
+      code = ((uint32_t)(2 - kc) | code_yz) << kNbrIndexBits;
+      ++kc;
     }
     *jj = j++;
     return true;

@@ -182,8 +182,12 @@ __global__ void k_kick_drift_mixed(int64_t n, MixBuf b, MixFields f,
       b.spin[i] = make_float4(0.f, 0.f, P.Omega_f, b.spin[i].w);
     }
     if (!ok) latch(err, ERR_ESCAPED);
-    const uint32_t key =
-        (uint32_t)(P.cell_base + c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2]));
+    int slab = (int)(o.x * ((float)P.slabs / P.cellf[0]));
+    slab = slab < 0 ? 0 : (slab >= P.slabs ? P.slabs - 1 : slab);
+    const uint32_t key = (uint32_t)(P.cell_base +
+                                    ((int64_t)c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2])) *
+                                        P.slabs +
+                                    slab);
     cw.key[i] = key;
     cw.slot[i] = atomicAdd(&cw.count[key], 1u);
   }
@@ -246,37 +250,26 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
     const float cut2 = P.cut2_f;
     ListWriter lw(nw, n, i, stage + threadIdx.x * kStageStride);
-    // the 27 neighbour cells as one flat candidate sequence; the cell
-    // displacement of every candidate is known from its run, without reading
-    // the candidate's cell
-    CellWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, cx, cy, cz, P.periodic_z != 0,
-                  P.cellf[0], P.cellf[1], P.cellf[2]);
-    // one candidate ahead is in flight while the current one is tested; the
-    // test uses the same antisymmetric pair vector as every later use of the
-    // entry, so j lists i exactly when i lists j
-    uint32_t jn = 0;
-    bool more = wk.next(&jn);
-    float4 on = more ? b.off[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float exn = wk.exL, eyn = wk.eyL, ezn = wk.ezL;
-    uint32_t cn = wk.code;
-    while (more) {
-      const uint32_t j = jn;
-      const float4 oj = on;
-      const float exL = exn, eyL = eyn, ezL = ezn;
-      const uint32_t code = cn;
-      more = wk.next(&jn);
-      if (more) {
-        on = b.off[jn];
-        exn = wk.exL;
-        eyn = wk.eyL;
-        ezn = wk.ezL;
-        cn = wk.code;
-      }
-      const float ddx = exL + (oi.x - oj.x);
-      const float ddy = eyL + (oi.y - oj.y);
-      const float ddz = ezL + (oi.z - oj.z);
+    // the x-windows of the 27 neighbour cells as one flat candidate sequence;
+    // the cell displacement of every candidate is known from its run, without
+    // reading the candidate's cell.  The test uses the same antisymmetric pair
+    // vector as every later use of the entry, so j lists i exactly when i
+    // lists j.
+    SlabWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
+                  cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2);
+    uint32_t j;
+    uint32_t it = 0;
+    while (wk.next(&j)) {
+      const float4 oj = b.off[j];
+      const float ddx = wk.exL + (oi.x - oj.x);
+      const float ddy = wk.eyL + (oi.y - oj.y);
+      const float ddz = wk.ezL + (oi.z - oj.z);
       const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      if (r2 < cut2 && j != (uint32_t)i) lw.append(j | code);
+      lw.push(j | wk.code, r2 < cut2 && j != (uint32_t)i);
+      if (++it == kDrainEvery) {
+        lw.drain();
+        it = 0;
+      }
     }
     cnt = lw.finish();
     if (lw.overflow()) latch(err, ERR_NEIGHBORS);
