@@ -209,6 +209,12 @@ SPH_API int32_t sph_stage_count(void);
  * Synchronises. */
 SPH_API sph_status sph_autotune(sph_ctx* ctx, int32_t reps, int32_t* block_density,
                                 int32_t* block_forces);
+
+/* The launch shape in use: threads per block of the density and pair passes,
+ * and the density pass's candidate walk (1 = x-windows of the stencil rows,
+ * 0 = whole rows).  Any pointer may be NULL. */
+SPH_API sph_status sph_get_launch_config(const sph_ctx* ctx, int32_t* block_density,
+                                         int32_t* block_forces, int32_t* density_window);
 SPH_API const char* sph_stage_name(int32_t stage);
 
 /* Number of kernel launches one sph_step(ctx, 1) enqueues. */

@@ -95,6 +95,8 @@ def lib(build_if_missing: bool = True):
                 "sph_stage_count": (C.c_int32, []),
                 "sph_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32),
                                            C.POINTER(C.c_int32)]),
+                "sph_get_launch_config": (C.c_int, [vp, C.POINTER(C.c_int32),
+                                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
@@ -115,7 +117,7 @@ def exported_symbols() -> list[str]:
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
-            "sph_autotune",
+            "sph_autotune", "sph_get_launch_config",
             "sph_fma_peak", "sph_diag_sums_noalloc", "sph_destroy", "sph_status_string"]
 
 
@@ -279,6 +281,13 @@ def sph_autotune(ctx, reps: int = 3) -> tuple[int, int]:
     bd, bf = C.c_int32(), C.c_int32()
     _ck(lib().sph_autotune(ctx, int(reps), C.byref(bd), C.byref(bf)), "sph_autotune")
     return bd.value, bf.value
+
+
+def sph_get_launch_config(ctx) -> dict:
+    a, b, w = C.c_int32(), C.c_int32(), C.c_int32()
+    _ck(lib().sph_get_launch_config(ctx, C.byref(a), C.byref(b), C.byref(w)),
+        "sph_get_launch_config")
+    return {"block_density": a.value, "block_forces": b.value, "density_window": w.value}
 
 
 def sph_destroy(ctx):

@@ -183,7 +183,7 @@ __device__ __forceinline__ double ipow(double x, int e) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
-               CellWs cw, NbrWs nw, uint32_t* err) {
+               CellWs cw, NbrWs nw, uint32_t* err, int window) {
   __shared__ uint32_t stage[BLOCK * kStageStride];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
@@ -210,7 +210,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
                   cz, (float)P.cell[0], (float)P.cell[1], (float)P.cell[2],
                   (float)((pi.x - P.lo[0]) - cx * P.cell[0]),
                   (float)((pi.y - P.lo[1]) - cy * P.cell[1]),
-                  (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f);
+                  (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f, window != 0);
     uint32_t j;
     uint32_t it = 0;
     while (wk.next(&j)) {
@@ -460,11 +460,14 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches) {
   if (lc.block_density == 256)
-    k_density_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   else if (lc.block_density == 64)
-    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   else
-    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

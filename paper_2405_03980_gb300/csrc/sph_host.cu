@@ -595,6 +595,7 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
     return fail(SPH_ERR_CUDA);
   c->lc.block_density = 128;
   c->lc.block_forces = 128;
+  c->lc.density_window = 1;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(SPH_ERR_CUDA);
 
@@ -899,30 +900,35 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
   }
   const int cand[3] = {64, 128, 256};
   float best_d = INFINITY, best_f = INFINITY;
-  int bd = c->lc.block_density, bf = c->lc.block_forces;
-  for (int k = 0; k < 3 && st == SPH_OK; ++k) {
-    for (int which = 0; which < 2 && st == SPH_OK; ++which) {
-      LaunchCfg saved = c->lc;
-      if (which == 0) c->lc.block_density = cand[k];
-      else c->lc.block_forces = cand[k];
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < reps && st == SPH_OK; ++r)
-        st = which == 0 ? enqueue_density(c, s, nullptr) : enqueue_forces(c, s, 0, nullptr);
-      cudaEventRecord(e1, s);
-      float ms = 0.f;
-      if (st == SPH_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
-                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        st = SPH_ERR_CUDA;
-      if (which == 0 && ms < best_d) best_d = ms, bd = cand[k];
-      if (which == 1 && ms < best_f) best_f = ms, bf = cand[k];
-      c->lc = saved;
+  int bd = c->lc.block_density, bf = c->lc.block_forces, bw = c->lc.density_window;
+  // density: block size x candidate walk (x-windows or whole rows); forces: block size
+  for (int trial = 0; trial < 9 && st == SPH_OK; ++trial) {
+    const bool dens = trial < 6;
+    LaunchCfg saved = c->lc;
+    if (dens) {
+      c->lc.block_density = cand[trial % 3];
+      c->lc.density_window = trial / 3;
+    } else {
+      c->lc.block_forces = cand[trial - 6];
     }
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == SPH_OK; ++r)
+      st = dens ? enqueue_density(c, s, nullptr) : enqueue_forces(c, s, 0, nullptr);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (st == SPH_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = SPH_ERR_CUDA;
+    if (dens && ms < best_d) best_d = ms, bd = c->lc.block_density, bw = c->lc.density_window;
+    if (!dens && ms < best_f) best_f = ms, bf = c->lc.block_forces;
+    c->lc = saved;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SPH_OK) return st;
   c->lc.block_density = bd;
   c->lc.block_forces = bf;
+  c->lc.density_window = bw;
   // restore the pair-pass outputs, and drop the graphs captured with the old
   // shapes; they are captured again by the next sph_step
   st = enqueue_density(c, s, nullptr);
@@ -937,6 +943,15 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
   if (block_density) *block_density = bd;
   if (block_forces) *block_forces = bf;
   return sph_check(c);
+}
+
+sph_status sph_get_launch_config(const sph_ctx* c, int32_t* block_density, int32_t* block_forces,
+                                 int32_t* density_window) {
+  if (!c) return SPH_ERR_ARG;
+  if (block_density) *block_density = c->lc.block_density;
+  if (block_forces) *block_forces = c->lc.block_forces;
+  if (density_window) *density_window = c->lc.density_window;
+  return SPH_OK;
 }
 
 int32_t sph_stage_count(void) { return kStages; }

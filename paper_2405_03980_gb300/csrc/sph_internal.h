@@ -179,8 +179,7 @@ struct ListWriter {
   __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
       : list(nw.list), n(n_), i(i_), st(st_), groups((uint32_t)nw.cap >> 3) {}
   __device__ __forceinline__ void push(uint32_t e, bool keep) {
-    st[pend] = e;
-    pend += keep ? 1u : 0u;
+    if (keep) st[pend++] = e;  // a predicated store, no branch
   }
   __device__ __forceinline__ void write_group(uint32_t from) {
     if (written < groups) {
@@ -216,12 +215,13 @@ struct ListWriter {
 // visited, split at the cell boundaries so that the cell displacement
 // c_i - c_j of every candidate is known (as -1/0/+1 times the cell side, and
 // as its 6-bit code).  One flat loop per thread keeps the lanes of a warp in
-// step.
+// step.  With window == false every row is visited whole (3 cells), which
+// costs more candidates but less bookkeeping; the autotuner picks.
 struct SlabWalker {
   const uint32_t* start;
   int64_t base;
   int nx, ny, nz, cx, cy, cz, S;
-  bool periodic;
+  bool periodic, window;
   float Lx, Ly, Lz, ox, oy, oz, cut2, inv_slab;
   int kr = -1, kc = 0, slo = 0, shi = -1;
   int64_t rowkey = 0;
@@ -233,10 +233,10 @@ struct SlabWalker {
   __device__ __forceinline__ SlabWalker(const uint32_t* start_, int64_t base_, int nx_, int ny_,
                                         int nz_, int S_, bool periodic_, int cx_, int cy_, int cz_,
                                         float Lx_, float Ly_, float Lz_, float ox_, float oy_,
-                                        float oz_, float cut2_)
+                                        float oz_, float cut2_, bool window_)
       : start(start_), base(base_), nx(nx_), ny(ny_), nz(nz_), cx(cx_), cy(cy_), cz(cz_), S(S_),
-        periodic(periodic_), Lx(Lx_), Ly(Ly_), Lz(Lz_), ox(ox_), oy(oy_), oz(oz_), cut2(cut2_),
-        inv_slab((float)S_ / Lx_) {}
+        periodic(periodic_), window(window_), Lx(Lx_), Ly(Ly_), Lz(Lz_), ox(ox_), oy(oy_),
+        oz(oz_), cut2(cut2_), inv_slab((float)S_ / Lx_) {}
   // Next candidate index in *jj; false when the stencil is exhausted.
   __device__ __forceinline__ bool next(uint32_t* jj) {
     while (j == e) {
@@ -251,13 +251,18 @@ struct SlabWalker {
           const float ry = dy < 0 ? oy : (dy > 0 ? Ly - oy : 0.f);
           const float rz = dz < 0 ? oz : (dz > 0 ? Lz - oz : 0.f);
           d2 = ry * ry + rz * rz;
-        } while (d2 >= cut2 + 1e-3f);
-        const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
-        const float xr = Lx + ox;  // x relative to the start of cell cx-1
-        const int lo = (int)floorf((xr - w) * inv_slab);
-        const int hi = (int)floorf((xr + w) * inv_slab);
-        slo = lo < 0 ? 0 : lo;
-        shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
+        } while (window && d2 >= cut2 + 1e-3f);
+        if (window) {
+          const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
+          const float xr = Lx + ox;  // x relative to the start of cell cx-1
+          const int lo = (int)floorf((xr - w) * inv_slab);
+          const int hi = (int)floorf((xr + w) * inv_slab);
+          slo = lo < 0 ? 0 : lo;
+          shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
+        } else {
+          slo = 0;
+          shi = 3 * S - 1;
+        }
         int z2 = cz + dz;
         if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
         rowkey = base + ((int64_t)(cx - 1) + (int64_t)nx * ((cy + dy) + (int64_t)ny * z2)) * S;

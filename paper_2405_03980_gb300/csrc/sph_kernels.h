@@ -12,6 +12,7 @@ struct LaunchCfg {
   int sm_count;          // multiprocessors of the device
   int block_density;     // threads per block of the density pass
   int block_forces;      // threads per block of the pair pass
+  int density_window;    // 1: candidate walk restricted to x-windows; 0: whole rows
 };
 
 // ---- cell build (sph_cells.cu) --------------------------------------------

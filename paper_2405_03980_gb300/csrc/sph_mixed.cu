@@ -105,16 +105,25 @@ __device__ __forceinline__ bool normalize(float& o, int& c, float L, int lo, int
 // entry (whose top bits carry c_i - c_j + 1 per axis) and the two offsets;
 // exactly antisymmetric, and bit-identical to the candidate test that wrote
 // the entry.
-__device__ __forceinline__ void entry_vec(const InstDev& P, uint32_t ent, const float4& oi,
-                                          const float4& oj, float& dx, float& dy, float& dz) {
-  const uint32_t c = ent >> kNbrIndexBits;
-  const float ex = (float)((int)(c & 3u) - 1);
-  const float ey = (float)((int)((c >> 2) & 3u) - 1);
-  const float ez = (float)((int)(c >> 4) - 1);
-  const float exL = ex * P.cellf[0], eyL = ey * P.cellf[1], ezL = ez * P.cellf[2];
-  dx = exL + (oi.x - oj.x);
-  dy = eyL + (oi.y - oj.y);
-  dz = ezL + (oi.z - oj.z);
+// The displacement code is decoded through a 64-entry shared table of the
+// unit displacements (-1, 0, +1 per axis); (+-1 or 0) x L is exact, so the
+// fused multiply-add gives the same bits as the candidate test's
+// (c_i - c_j) L + (o_i - o_j).
+__device__ __forceinline__ void fill_disp_table(float4* tab) {
+  for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+    const int ex = (int)(c & 3) - 1, ey = (int)((c >> 2) & 3) - 1, ez = (int)(c >> 4) - 1;
+    tab[c] = make_float4(ex > 1 ? 0.f : (float)ex, ey > 1 ? 0.f : (float)ey,
+                         ez > 1 ? 0.f : (float)ez, 0.f);
+  }
+}
+
+__device__ __forceinline__ void entry_vec(const InstDev& P, const float4* tab, uint32_t ent,
+                                          const float4& oi, const float4& oj, float& dx, float& dy,
+                                          float& dz) {
+  const float4 e = tab[ent >> kNbrIndexBits];
+  dx = fmaf(e.x, P.cellf[0], oi.x - oj.x);
+  dy = fmaf(e.y, P.cellf[1], oi.y - oj.y);
+  dz = fmaf(e.z, P.cellf[2], oi.z - oj.z);
 }
 
 __device__ __forceinline__ bool finite3f(float a, float b, float c) {
@@ -233,8 +242,11 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
-                NbrWs nw, uint32_t* err) {
+                NbrWs nw, uint32_t* err, int window) {
   __shared__ uint32_t stage[BLOCK * kStageStride];
+  __shared__ float4 dtab[64];
+  fill_disp_table(dtab);
+  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -256,7 +268,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // vector as every later use of the entry, so j lists i exactly when i
     // lists j.
     SlabWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
-                  cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2);
+                  cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2, window != 0);
     uint32_t j;
     uint32_t it = 0;
     while (wk.next(&j)) {
@@ -287,7 +299,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
         oj_n = b.off[ent_n & kNbrIndexMask];
       }
       float dx, dy2, dz2;
-      entry_vec(P, ent, oi, oj, dx, dy2, dz2);
+      entry_vec(P, dtab, ent, oi, oj, dx, dy2, dz2);
       const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
       const float q = sqrtf(r2) * P.inv_h_f;
       const float t1 = 1.f - 0.5f * q;
@@ -316,6 +328,9 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                uint32_t* err) {
+  __shared__ float4 dtab[64];
+  fill_disp_table(dtab);
+  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const float4 oi = b.off[i];
@@ -377,7 +392,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     }
     if (t + 2 < cnt) ent_nn = nw.list[nbr_slot(n, i, t + 2)];
     float dx, dy, dz;
-    entry_vec(P, ent, oi, oj, dx, dy, dz);
+    entry_vec(P, dtab, ent, oi, oj, dx, dy, dz);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 > 0.f) {  // coincident particles: density only
     const float inv_r = rsqrtf(r2);
@@ -550,11 +565,14 @@ cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                  int* launches) {
   if (lc.block_density == 256) {
-    k_density_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   } else if (lc.block_density == 64) {
-    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   } else {
-    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err,
+                                                                   lc.density_window);
   }
   if (launches) ++*launches;
   return cudaGetLastError();

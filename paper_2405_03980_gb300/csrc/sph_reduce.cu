@@ -142,15 +142,21 @@ k_wall_torque_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V,
     partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x * kRedThreads];
 }
 
+// One warp per instance: lane l adds chunks l, l + 32, ... in order, then a
+// fixed butterfly combines the lanes (deterministic, independent of batching).
 __global__ void k_wall_torque_final(int32_t n_inst, const InstDev* __restrict__ inst,
                                     InstState* __restrict__ ist,
                                     const double* __restrict__ partials, int advance) {
-  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t k = blockIdx.x;
   if (k >= n_inst) return;
+  const int lane = threadIdx.x;
   const InstDev& P = inst[k];
   double T[3] = {0.0, 0.0, 0.0};
-  for (int64_t c = 0; c < P.n_chunks; ++c)
+  for (int64_t c = lane; c < P.n_chunks; c += 32)
     for (int a = 0; a < 3; ++a) T[a] += partials[(P.chunk_base + c) * 3 + a];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int a = 0; a < 3; ++a) T[a] += __shfl_xor_sync(0xffffffffu, T[a], o);
+  if (lane != 0) return;
   InstState s = ist[k];
   if (advance) {
     for (int a = 0; a < 3; ++a) s.J_wall[a] += P.hdt * (s.T_wall[a] + T[a]);
@@ -276,7 +282,7 @@ cudaError_t wall_torque(int32_t n_inst, int64_t total_chunks, const InstDev* ins
                         cudaStream_t s, int* launches) {
   k_wall_torque_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, V,
                                                                             partials);
-  k_wall_torque_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, ist, partials, advance);
+  k_wall_torque_final<<<n_inst, 32, 0, s>>>(n_inst, inst, ist, partials, advance);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }

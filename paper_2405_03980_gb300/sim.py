@@ -93,6 +93,9 @@ class Simulation:
     def autotune(self, reps: int = 3) -> tuple[int, int]:
         return B.sph_autotune(self.ctx, reps)
 
+    def launch_config(self) -> dict:
+        return B.sph_get_launch_config(self.ctx)
+
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)
 
