@@ -206,27 +206,26 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     // phase 1: FP32 prefilter over the x-windows of the 27 neighbour cells
     // into the provisional neighbour list
     ListWriter pre(nw, n, i, st);
-    SlabWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
-                  cz, (float)P.cell[0], (float)P.cell[1], (float)P.cell[2],
-                  (float)((pi.x - P.lo[0]) - cx * P.cell[0]),
-                  (float)((pi.y - P.lo[1]) - cy * P.cell[1]),
-                  (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f, window != 0);
-    uint32_t j;
     uint32_t it = 0;
-    while (wk.next(&j)) {
-      const float4 q = nw.posf[j];
-      float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
-      if (P.periodic_z) {
-        if (ddz > P.half_Hzf) ddz -= P.Hzf;
-        else if (ddz < -P.half_Hzf) ddz += P.Hzf;
-      }
-      const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-      pre.push(j, r2f < cut2f && j != (uint32_t)i);
-      if (++it == kDrainEvery) {
-        pre.drain();
-        it = 0;
-      }
-    }
+    visit_candidates(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
+                     cz, (float)P.cell[0], (float)P.cell[1], (float)P.cell[2],
+                     (float)((pi.x - P.lo[0]) - cx * P.cell[0]),
+                     (float)((pi.y - P.lo[1]) - cy * P.cell[1]),
+                     (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f, window != 0,
+                     [&](uint32_t j, float, float, float, uint32_t) {
+                       const float4 q = nw.posf[j];
+                       float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
+                       if (P.periodic_z) {
+                         if (ddz > P.half_Hzf) ddz -= P.Hzf;
+                         else if (ddz < -P.half_Hzf) ddz += P.Hzf;
+                       }
+                       const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+                       pre.push(j, r2f < cut2f && j != (uint32_t)i);
+                       if (++it == kDrainEvery) {
+                         pre.drain();
+                         it = 0;
+                       }
+                     });
     cnt = pre.finish();
     if (pre.overflow()) latch(err, ERR_NEIGHBORS);
     // phase 2: exact FP64 cutoff (no fused multiply-add in r^2, strict <),

@@ -207,83 +207,57 @@ struct ListWriter {
   }
 };
 
-// Walks the candidates of one particle: the 9 rows (dy, dz) of the 27-cell
+// Visits the candidates of one particle: the 9 rows (dy, dz) of the 27-cell
 // stencil, each row the 3 x-adjacent cells cx-1..cx+1, which the sort keeps
-// as one run of S x-slabs per cell.  A row out of reach (its nearest y-z
-// distance >= the cutoff) is skipped, and within a row only the slabs that
-// overlap the x-window |x_j - x_i| <= sqrt(cut^2 - d_yz^2) (+ margin) are
-// visited, split at the cell boundaries so that the cell displacement
-// c_i - c_j of every candidate is known (as -1/0/+1 times the cell side, and
-// as its 6-bit code).  One flat loop per thread keeps the lanes of a warp in
-// step.  With window == false every row is visited whole (3 cells), which
-// costs more candidates but less bookkeeping; the autotuner picks.
-struct SlabWalker {
-  const uint32_t* start;
-  int64_t base;
-  int nx, ny, nz, cx, cy, cz, S;
-  bool periodic, window;
-  float Lx, Ly, Lz, ox, oy, oz, cut2, inv_slab;
-  int kr = -1, kc = 0, slo = 0, shi = -1;
-  int64_t rowkey = 0;
-  uint32_t j = 0, e = 0;
-  float exL = 0.f, eyL = 0.f, ezL = 0.f;
-  uint32_t code_yz = 0, code = 0;
-  // own cell (cx, cy, cz) and FP32 offsets (ox, oy, oz) inside it; cut2 is
-  // the squared cutoff the candidates are tested against.
-  __device__ __forceinline__ SlabWalker(const uint32_t* start_, int64_t base_, int nx_, int ny_,
-                                        int nz_, int S_, bool periodic_, int cx_, int cy_, int cz_,
-                                        float Lx_, float Ly_, float Lz_, float ox_, float oy_,
-                                        float oz_, float cut2_, bool window_)
-      : start(start_), base(base_), nx(nx_), ny(ny_), nz(nz_), cx(cx_), cy(cy_), cz(cz_), S(S_),
-        periodic(periodic_), window(window_), Lx(Lx_), Ly(Ly_), Lz(Lz_), ox(ox_), oy(oy_),
-        oz(oz_), cut2(cut2_), inv_slab((float)S_ / Lx_) {}
-  // Next candidate index in *jj; false when the stencil is exhausted.
-  __device__ __forceinline__ bool next(uint32_t* jj) {
-    while (j == e) {
-      if (kc * S > shi) {
-        // next row within reach
-        float d2;
-        int dy, dz;
-        do {
-          if (++kr == 9) return false;
-          dz = kr / 3 - 1;
-          dy = kr - 3 * (kr / 3) - 1;
-          const float ry = dy < 0 ? oy : (dy > 0 ? Ly - oy : 0.f);
-          const float rz = dz < 0 ? oz : (dz > 0 ? Lz - oz : 0.f);
-          d2 = ry * ry + rz * rz;
-        } while (window && d2 >= cut2 + 1e-3f);
-        if (window) {
-          const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
-          const float xr = Lx + ox;  // x relative to the start of cell cx-1
-          const int lo = (int)floorf((xr - w) * inv_slab);
-          const int hi = (int)floorf((xr + w) * inv_slab);
-          slo = lo < 0 ? 0 : lo;
-          shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
-        } else {
-          slo = 0;
-          shi = 3 * S - 1;
-        }
-        int z2 = cz + dz;
-        if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
-        rowkey = base + ((int64_t)(cx - 1) + (int64_t)nx * ((cy + dy) + (int64_t)ny * z2)) * S;
-        eyL = (float)(-dy) * Ly;
-        ezL = (float)(-dz) * Lz;
-        code_yz = ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4);
-        kc = slo / S;
-        continue;
+// as one run of S x-slabs per cell.  With window, a row out of reach (its
+// nearest y-z distance >= the cutoff) is skipped and within a row only the
+// slabs overlapping the x-window |x_j - x_i| <= sqrt(cut^2 - d_yz^2) (+ a
+// margin) are visited.  Runs are split at the cell boundaries, so the cell
+// displacement c_i - c_j of every candidate is known: visit(j, exL, eyL, ezL,
+// code) gets it as -1/0/+1 times the cell side per axis and as its 6-bit
+// code.  (ox, oy, oz) are the particle's FP32 offsets inside its cell
+// (cx, cy, cz); cut2 is the squared cutoff of the candidate test.
+template <class Visit>
+__device__ __forceinline__ void visit_candidates(const uint32_t* __restrict__ start, int64_t base,
+                                                 int nx, int ny, int nz, int S, bool periodic,
+                                                 int cx, int cy, int cz, float Lx, float Ly,
+                                                 float Lz, float ox, float oy, float oz,
+                                                 float cut2, bool window, Visit&& visit) {
+  const float inv_slab = (float)S / Lx;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int z2 = cz + dz;
+    if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
+    const float rz = dz < 0 ? oz : (dz > 0 ? Lz - oz : 0.f);
+    const float ezL = (float)(-dz) * Lz;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int slo = 0, shi = 3 * S - 1;
+      if (window) {
+        const float ry = dy < 0 ? oy : (dy > 0 ? Ly - oy : 0.f);
+        const float d2 = ry * ry + rz * rz;
+        if (d2 >= cut2 + 1e-3f) continue;  // row out of reach
+        const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
+        const float xr = Lx + ox;  // x relative to the start of cell cx-1
+        const int lo = (int)floorf((xr - w) * inv_slab);
+        const int hi = (int)floorf((xr + w) * inv_slab);
+        slo = lo < 0 ? 0 : lo;
+        shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
       }
-      const int a = kc * S > slo ? kc * S : slo;
-      const int b = kc * S + S - 1 < shi ? kc * S + S - 1 : shi;
-      j = start[rowkey + a];
-      e = start[rowkey + b + 1];
-      exL = (float)(1 - kc) * Lx;
-      code = ((uint32_t)(2 - kc) | code_yz) << kNbrIndexBits;
-      ++kc;
+      const int64_t rowkey =
+          base + ((int64_t)(cx - 1) + (int64_t)nx * ((cy + dy) + (int64_t)ny * z2)) * S;
+      const float eyL = (float)(-dy) * Ly;
+      const uint32_t code_yz = ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4);
+      for (int kc = slo / S; kc < 3 && kc * S <= shi; ++kc) {
+        const int a = kc * S > slo ? kc * S : slo;
+        const int b = kc * S + S - 1 < shi ? kc * S + S - 1 : shi;
+        const uint32_t j0 = start[rowkey + a];
+        const uint32_t j1 = start[rowkey + b + 1];
+        const float exL = (float)(1 - kc) * Lx;
+        const uint32_t code = ((uint32_t)(2 - kc) | code_yz) << kNbrIndexBits;
+        for (uint32_t j = j0; j < j1; ++j) visit(j, exL, eyL, ezL, code);
+      }
     }
-    *jj = j++;
-    return true;
   }
-};
+}
 #endif
 
 }  // namespace sphgb

@@ -267,22 +267,21 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // reading the candidate's cell.  The test uses the same antisymmetric pair
     // vector as every later use of the entry, so j lists i exactly when i
     // lists j.
-    SlabWalker wk(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
-                  cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2, window != 0);
-    uint32_t j;
     uint32_t it = 0;
-    while (wk.next(&j)) {
-      const float4 oj = b.off[j];
-      const float ddx = wk.exL + (oi.x - oj.x);
-      const float ddy = wk.eyL + (oi.y - oj.y);
-      const float ddz = wk.ezL + (oi.z - oj.z);
-      const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      lw.push(j | wk.code, r2 < cut2 && j != (uint32_t)i);
-      if (++it == kDrainEvery) {
-        lw.drain();
-        it = 0;
-      }
-    }
+    visit_candidates(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
+                     cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2, window != 0,
+                     [&](uint32_t j, float exL, float eyL, float ezL, uint32_t code) {
+                       const float4 oj = b.off[j];
+                       const float ddx = exL + (oi.x - oj.x);
+                       const float ddy = eyL + (oi.y - oj.y);
+                       const float ddz = ezL + (oi.z - oj.z);
+                       const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                       lw.push(j | code, r2 < cut2 && j != (uint32_t)i);
+                       if (++it == kDrainEvery) {
+                         lw.drain();
+                         it = 0;
+                       }
+                     });
     cnt = lw.finish();
     if (lw.overflow()) latch(err, ERR_NEIGHBORS);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
