@@ -335,14 +335,14 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
     const double uy = vy + 0.5 * (dz * sx - dx * sz);
     const double uz = vz + 0.5 * (dx * sy - dy * sx);
     const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
-    const double du = dx * ux + dy * uy + dz * uz;  // r_ij . u_ij
     // The five pair terms collected along r_ij and u_ij (and v_ij for the
     // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
-    // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F du/r^2 r_ij.
+    // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F dv/r^2 r_ij.
     const double VF = vj.w * F;
     const double aP = cP * m_j * (wi.w + wj.w) * F;
     const double aT = cT * mX * VF;
-    const double aV = VF * mV * inv_r2 * (cB * du - cA * dv);
+    // r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij
+    const double aV = VF * mV * inv_r2 * ((cB - cA) * dv);
     const double bR = -cB * mV * VF;
     const double bN = -cN * mX * vj.w * W;
     const double al = aP + aT + aV;

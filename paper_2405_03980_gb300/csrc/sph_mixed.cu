@@ -415,13 +415,13 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     const float uy = vy + 0.5f * (dz * sx - dx * sz);
     const float uz = vz + 0.5f * (dx * sy - dy * sx);
     const float dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij (symmetric)
-    const float du = dx * ux + dy * uy + dz * uz;  // r_ij . u_ij (symmetric)
     // the five terms collected along r_ij, u_ij and (literal F_sn) v_ij:
-    // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F du/r^2 r_ij
+    // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F dv/r^2 r_ij
     const float VF = VV * F;
     const float aP = kP * MM * ((wi.w + wj.w) * F);
     const float aT = kT * mX * VF;
-    const float aV = VF * mV * inv_r2 * (kB * du - kA * dv);
+    // r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij
+    const float aV = VF * mV * inv_r2 * ((kB - kA) * dv);
     const float bR = -kB * mV * VF;
     const float bN = -kN * mX * (VV * W);
     const float al = aP + aT + aV;
