@@ -38,12 +38,46 @@ UNIT = "particle-steps/s"
 # FP64 operations per neighbour pair of the pair pass, counted from the kernel
 # source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
 # work of one force launch is this times the number of fluid neighbour pairs.
-FORCE_FLOPS_PER_PAIR = {"fp64": 103, "mixed": 111}   # mixed adds cell offsets and Kahan
+FORCE_FLOPS_PER_PAIR = {"fp64": 94, "mixed": 103}   # mixed adds cell offsets and Kahan
 # Density pass: operations per neighbour pair of the density sum (pair vector,
 # r^2, sqrt, Wendland W, accumulation; the mixed form adds the cell offsets
 # and the Kahan update).  The candidate tests that find the neighbours are
 # not counted as algorithmic work.
 DENSITY_FLOPS_PER_PAIR = {"fp64": 20, "mixed": 31}
+# Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
+# mixed form adds the cell displacement).  Its work is the candidate tests of
+# the 27-cell stencil of every particle that keeps a list (fluid and inner
+# wall), counted on the host from the initial positions (candidate_tests).
+SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
+
+
+def candidate_tests(insts):
+    """Sum over the particles that keep a neighbour list of the particle count
+    of their 27 surrounding grid cells (cell side >= 2h, the grid of the
+    library: floor(L / 2h) cells per axis, periodic in z)."""
+    total = 0
+    for c in insts:
+        p = c.params
+        lo = np.array(p["box_lo"], dtype=np.float64)
+        hi = np.array(p["box_hi"], dtype=np.float64)
+        ncell = np.maximum(np.floor((hi - lo) / (2.0 * p["h"])), 1).astype(np.int64)
+        side = (hi - lo) / ncell
+        idx = np.clip(np.floor((c.pos - lo) / side).astype(np.int64), 0, ncell - 1)
+        cnt = np.zeros(tuple(ncell + 2), dtype=np.int64)  # one ghost layer per side
+        np.add.at(cnt, (idx[:, 0] + 1, idx[:, 1] + 1, idx[:, 2] + 1), 1)
+        if p.get("periodic_z", 1):
+            cnt[:, :, 0] = cnt[:, :, -2]
+            cnt[:, :, -1] = cnt[:, :, 1]
+        nb = np.zeros_like(cnt)
+        for ox in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for oz in (-1, 0, 1):
+                    nb[1:-1, 1:-1, 1:-1] += cnt[1 + ox:cnt.shape[0] - 1 + ox,
+                                                1 + oy:cnt.shape[1] - 1 + oy,
+                                                1 + oz:cnt.shape[2] - 1 + oz]
+        keep = c.species != 3
+        total += int(nb[idx[keep, 0] + 1, idx[keep, 1] + 1, idx[keep, 2] + 1].sum())
+    return total
 
 
 def parse():
@@ -339,20 +373,28 @@ def run_ours(args, dist):
     peaks = {"fp64": B.sph_fma_peak(B.SPH_FP64, 1 << 15),
              "mixed": B.sph_fma_peak(B.SPH_MIXED, 1 << 20)}
     roofs = {}
+    tests = candidate_tests(insts)
     for f in results:
         pr = results[f]["diag"]["n_pairs"]
         unit = "FP64" if f == "fp64" else "FP32"
-        src = f"measured {unit} FMA-chain rate of this GPU (sph_fma_peak), of measured"
-        for stage, kern, fpp in (("forces", f"k_forces_{f}", FORCE_FLOPS_PER_PAIR[f]),
-                                 ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f])):
+        for stage, kern, fpp, units, what, u in (
+                ("forces", f"k_forces_{f}", FORCE_FLOPS_PER_PAIR[f], pr,
+                 "fluid neighbour pairs", unit),
+                ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], pr,
+                 "fluid neighbour pairs", unit),
+                ("cell_search", f"k_cell_search<{str(f == 'mixed').lower()}>",
+                 SEARCH_FLOPS_PER_TEST[f], tests, "candidate tests (initial positions)",
+                 "FP32")):
+            pk = peaks["mixed"] if u == "FP32" else peaks["fp64"]
+            src = f"measured {u} FMA-chain rate of this GPU (sph_fma_peak), of measured"
             t = results[f]["stages"][stage] * 1e-3
-            ach = fpp * pr / t / 1e12
+            ach = fpp * units / t / 1e12
             roofs.setdefault(f, {})[stage] = {
-                "kernel": kern, "bound": "alu", "achieved": ach, "peak": peaks[f],
-                "unit": "TFLOP/s", "frac": ach / peaks[f], "traffic": None, "peak_source": src,
-                "work": f"{fpp} {unit} flop x {pr} fluid neighbour pairs per launch",
+                "kernel": kern, "bound": "alu", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s", "frac": ach / pk, "traffic": None, "peak_source": src,
+                "work": f"{fpp} {u} flop x {units} {what} per launch",
                 "launch_ms": results[f]["stages"][stage]}
-    dom_stage = "density" if st["density"] >= st["forces"] else "forces"
+    dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
     roof = roofs[best][dom_stage]
 
     # end-to-end through the C ABI with host buffers

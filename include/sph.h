@@ -56,7 +56,9 @@ typedef enum {
   SPH_ERR_NONFINITE = -6,    /* NaN or Inf in the state                        */
   SPH_ERR_TIMEOUT = -7,      /* a bounded device wait gave up                  */
   SPH_ERR_STATE = -8,        /* call out of order (e.g. step before init)      */
-  SPH_ERR_NEIGHBORS = -9     /* a neighbour list exceeded nbr_cap (truncated)  */
+  SPH_ERR_NEIGHBORS = -9     /* a neighbour list exceeded nbr_cap (truncated),
+                                or a cell's 27-cell stencil held more than 1024
+                                particles (those beyond are not searched)     */
 } sph_status;
 
 /* Particle species (Sec. 2.1 two components; Sec. 3 wall and dummy particles). */
@@ -198,23 +200,24 @@ SPH_API sph_status sph_profile_steps(sph_ctx* ctx, int32_t nsteps, double* stage
                                      int32_t n_stages);
 SPH_API int32_t sph_stage_count(void);
 
-/* Autotune the launch shape of the density and pair passes: each candidate
- * block size (64, 128, 256 threads) is timed over reps launches on the current
- * state with CUDA events, the fastest is kept for later steps, and the step
- * graphs are re-captured on the next sph_step.  The trials recompute the same
- * neighbour lists and densities; the pair-pass outputs (which a step computed
- * from half-step velocities) are saved in the workspace and restored, so the
- * state is left bit for bit as it was.
- * *block_density and *block_forces (may be NULL) receive the choice.
- * Synchronises. */
+/* Autotune the launch shape of the neighbour search, the density pass and the
+ * pair pass: each candidate (2, 4 or 8 warps per block of the search; 32, 64
+ * or 128 threads per block of the density pass; 64, 128 or 256 of the pair
+ * pass) is timed over reps launches on the current state with CUDA events,
+ * the fastest is kept for later steps, and the step graphs are re-captured on
+ * the next sph_step.  The trials recompute the same neighbour lists and
+ * densities; the pair-pass outputs (which a step computed from half-step
+ * velocities) are saved in the workspace and restored, so the state is left
+ * bit for bit as it was.  *block_density and *block_forces (may be NULL)
+ * receive the choice.  Synchronises. */
 SPH_API sph_status sph_autotune(sph_ctx* ctx, int32_t reps, int32_t* block_density,
                                 int32_t* block_forces);
 
 /* The launch shape in use: threads per block of the density and pair passes,
- * and the density pass's candidate walk (1 = x-windows of the stencil rows,
- * 0 = whole rows).  Any pointer may be NULL. */
+ * and warps per block of the neighbour search (one warp per grid cell).  Any
+ * pointer may be NULL. */
 SPH_API sph_status sph_get_launch_config(const sph_ctx* ctx, int32_t* block_density,
-                                         int32_t* block_forces, int32_t* density_window);
+                                         int32_t* block_forces, int32_t* search_warps);
 SPH_API const char* sph_stage_name(int32_t stage);
 
 /* Number of kernel launches one sph_step(ctx, 1) enqueues. */

@@ -287,7 +287,7 @@ def sph_get_launch_config(ctx) -> dict:
     a, b, w = C.c_int32(), C.c_int32(), C.c_int32()
     _ck(lib().sph_get_launch_config(ctx, C.byref(a), C.byref(b), C.byref(w)),
         "sph_get_launch_config")
-    return {"block_density": a.value, "block_forces": b.value, "density_window": w.value}
+    return {"block_density": a.value, "block_forces": b.value, "search_warps": w.value}
 
 
 def sph_destroy(ctx):

@@ -180,10 +180,18 @@ __device__ __forceinline__ double ipow(double x, int e) {
   return r;
 }
 
+// Density and Tait pressure (Eq. 4), one thread per particle, from the hit
+// bits of the FP32 prefilter of the neighbour search (sph_search.cu): every
+// candidate whose bit is set is re-tested exactly in FP64 (no fused
+// multiply-add in r^2, strict <); the neighbours are summed and written, in
+// candidate order, as i's neighbour list for the pair pass.  The walk takes
+// 4 candidates at a time: their table entries, then their position records,
+// are loaded together before they are tested.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
-               CellWs cw, NbrWs nw, uint32_t* err, int window) {
+k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
+               NbrWs nw, uint32_t* err) {
+  __shared__ uint32_t smask[BLOCK * kMaxCandWords];
   __shared__ uint32_t stage[BLOCK * kStageStride];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
@@ -196,67 +204,42 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   if (sp == 3) {
     rho = P.rho0;
   } else {
-    const float4 pf = nw.posf[i];
-    const int64_t c = ((int64_t)cw.skey[i] - P.cell_base) / P.slabs;
-    const int cx = (int)(c % P.nx);
-    const int cy = (int)((c / P.nx) % P.ny);
-    const int cz = (int)(c / ((int64_t)P.nx * P.ny));
-    const float cut2f = P.cut2f_margin;
-    uint32_t* st = stage + threadIdx.x * kStageStride;
-    // phase 1: FP32 prefilter over the x-windows of the 27 neighbour cells
-    // into the provisional neighbour list
-    ListWriter pre(nw, n, i, st);
-    uint32_t it = 0;
-    visit_candidates(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
-                     cz, (float)P.cell[0], (float)P.cell[1], (float)P.cell[2],
-                     (float)((pi.x - P.lo[0]) - cx * P.cell[0]),
-                     (float)((pi.y - P.lo[1]) - cy * P.cell[1]),
-                     (float)((pi.z - P.lo[2]) - cz * P.cell[2]), cut2f, window != 0,
-                     [&](uint32_t j, float, float, float, uint32_t) {
-                       const float4 q = nw.posf[j];
-                       float ddx = pf.x - q.x, ddy = pf.y - q.y, ddz = pf.z - q.z;
-                       if (P.periodic_z) {
-                         if (ddz > P.half_Hzf) ddz -= P.Hzf;
-                         else if (ddz < -P.half_Hzf) ddz += P.Hzf;
-                       }
-                       const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-                       pre.push(j, r2f < cut2f && j != (uint32_t)i);
-                       if (++it == kDrainEvery) {
-                         pre.drain();
-                         it = 0;
-                       }
-                     });
-    cnt = pre.finish();
-    if (pre.overflow()) latch(err, ERR_NEIGHBORS);
-    // phase 2: exact FP64 cutoff (no fused multiply-add in r^2, strict <),
-    // compaction of the list in place (a group is rewritten only after all
-    // of its entries were read), and the density sum
+    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
+    ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
     rho = m_i * P.aD;  // self term W(0)
-    ListWriter out(nw, n, i, st);
-    for (uint32_t t = 0; t < cnt; ++t) {
-      const uint32_t j = nw.list[nbr_slot(n, i, t)];
-      const dvec4 pj = b.pos[j];
-      const double dx = __dsub_rn(pi.x, pj.x);
-      const double dy = __dsub_rn(pi.y, pj.y);
-      double dz = __dsub_rn(pi.z, pj.z);
-      if (P.periodic_z) {
-        if (dz > P.half_Hz) dz = __dsub_rn(dz, P.Hz);
-        else if (dz < -P.half_Hz) dz = __dadd_rn(dz, P.Hz);
+    uint32_t e[4];
+    for (uint32_t m; (m = mk.next(e)) != 0u;) {
+      dvec4 pj[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u)
+        if (u < m) pj[u] = b.pos[e[u] & kNbrIndexMask];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        if (u < m) {
+          const double dx = __dsub_rn(pi.x, pj[u].x);
+          const double dy = __dsub_rn(pi.y, pj[u].y);
+          double dz = __dsub_rn(pi.z, pj[u].z);
+          if (P.periodic_z) {
+            if (dz > P.half_Hz) dz = __dsub_rn(dz, P.Hz);
+            else if (dz < -P.half_Hz) dz = __dadd_rn(dz, P.Hz);
+          }
+          const double r2 =
+              __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+          const bool keep = r2 < P.cut2;
+          out.push(e[u] & kNbrIndexMask, keep);
+          if (keep) {
+            const double q = sqrt(r2) * P.inv_h;
+            const double t1 = 1.0 - 0.5 * q;
+            const double t2 = t1 * t1;
+            const double m_j = pj[u].w == 0.0 ? P.m_s : P.m_n;
+            rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
+          }
+        }
       }
-      const double r2 =
-          __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      const bool keep = r2 < P.cut2;
-      out.push(j, keep);
-      if (keep) {
-        const double q = sqrt(r2) * P.inv_h;
-        const double t1 = 1.0 - 0.5 * q;
-        const double t2 = t1 * t1;
-        const double m_j = pj.w == 0.0 ? P.m_s : P.m_n;
-        rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
-      }
-      if (((t + 1) & (kDrainEvery - 1)) == 0) out.drain();
+      if (out.pend >= (uint32_t)kDrainAt) out.drain();
     }
     cnt = out.finish();
+    if (out.overflow()) latch(err, ERR_NEIGHBORS);
   }
   nw.count[i] = cnt;
   const double Pres = P.p0 * ipow(rho * P.inv_rho0, P.alphaP) - P.beta_P;
@@ -269,7 +252,9 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 
 // ------------------------------------------------------------------ pair pass
 
-template <int BLOCK>
+// kLiteral: some instance uses the literal F_sn (coefficient of v_ij); the
+// default form has none and drops that term at compile time.
+template <int BLOCK, bool kLiteral>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
               NbrWs nw, uint32_t* err) {
@@ -297,76 +282,98 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double cB = (fl & SPH_TERM_ROT) ? P.B * vi.w : 0.0;
   const double cN = (fl & SPH_TERM_SN) ? P.C_l * vi.w : 0.0;
   const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
-  const bool literal = (fl & SPH_SN_LITERAL) != 0;
+  const bool literal = kLiteral && (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
+  // The species factors of the pair terms depend on j only through whether
+  // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
+  // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
+  // rotational); walls count as viscous.
+  const double mX0 = inv_i ? 0.0 : 1.0, mX1 = inv_i ? 1.0 : 0.0;
+  const double mV1 = inv_i ? 0.0 : 1.0;
+  const double cP0 = cP * P.m_s, cP1 = cP * P.m_n;
+  const double cT0 = cT * mX0, cT1 = cT * mX1;
+  const double cBA1 = mV1 != 0.0 ? cB - cA : 0.0;
+  const double cB1 = -cB * mV1;
+  const double cN0 = -cN * mX0, cN1 = -cN * mX1;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   double tx = 0.0, ty = 0.0, tz = 0.0;
   double wx = 0.0, wy = 0.0, wz = 0.0;
   const uint32_t cnt = nw.count[i];
-  for (uint32_t t = 0; t < cnt; ++t) {
-    const uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
-    const dvec4 pj = b.pos[j];
-    const dvec4 vj = b.vel[j];
-    const dvec4 wj = b.spin[j];
-    const double dx = pi.x - pj.x, dy = pi.y - pj.y;
-    double dz = pi.z - pj.z;
-    if (P.periodic_z) {
-      if (dz > P.half_Hz) dz -= P.Hz;
-      else if (dz < -P.half_Hz) dz += P.Hz;
-    }
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (!(r2 > 0.0)) continue;  // coincident particles: density only
-    const double inv_r = rsqrt(r2);
-    const double r = r2 * inv_r;
-    const double inv_r2 = inv_r * inv_r;
-    const double q = r * P.inv_h;
-    const double t1 = 1.0 - 0.5 * q;
-    const double t2 = t1 * t1;
-    const double F = P.cF * t2 * t1;
-    const double W = P.aD * t2 * t2 * (2.0 * q + 1.0);
-    const bool inv_j = pj.w == 0.0;
-    const double mX = (inv_i != inv_j) ? 1.0 : 0.0;
-    const double mV = (!inv_i && !inv_j) ? 1.0 : 0.0;
-    const double m_j = inv_j ? P.m_s : P.m_n;
-    // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
-    const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-    const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
-    const double ux = vx + 0.5 * (dy * sz - dz * sy);
-    const double uy = vy + 0.5 * (dz * sx - dx * sz);
-    const double uz = vz + 0.5 * (dx * sy - dy * sx);
-    const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
-    // The five pair terms collected along r_ij and u_ij (and v_ij for the
-    // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
-    // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F dv/r^2 r_ij.
-    const double VF = vj.w * F;
-    const double aP = cP * m_j * (wi.w + wj.w) * F;
-    const double aT = cT * mX * VF;
-    // r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij
-    const double aV = VF * mV * inv_r2 * ((cB - cA) * dv);
-    const double bR = -cB * mV * VF;
-    const double bN = -cN * mX * vj.w * W;
-    const double al = aP + aT + aV;
-    const double alz = aP + hz * aT + aV;
-    const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
-    const double bv = literal ? bN : 0.0;      // coefficient of v_ij
-    const double pfx = al * dx + bu * ux + bv * vx;
-    const double pfy = al * dy + bu * uy + bv * vy;
-    const double pfz = alz * dz + bu * uz + bv * vz;
-    fx += pfx;
-    fy += pfy;
-    fz += pfz;
-    // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
-    const double hb = -0.5 * bu;
-    const double qx = hb * (dy * uz - dz * uy);
-    const double qy = hb * (dz * ux - dx * uz);
-    const double qz = hb * (dx * uy - dy * ux);
-    tx += qx;
-    ty += qy;
-    tz += qz;
-    if (pj.w >= 2.0) {  // torque exerted by the wall on particle i
-      wx += pi.y * pfz - pi.z * pfy + qx;
-      wy += pi.z * pfx - pi.x * pfz + qy;
-      wz += pi.x * pfy - pi.y * pfx + qz;
+  const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
+    // one group of 8 entries (a 32-byte sector) per read
+    const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
+    const uint4 ga = groups[g], gb = groups[g + 1];
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      if (u >= m) break;
+      const uint32_t j = e[u] & kNbrIndexMask;
+      const dvec4 pj = b.pos[j];
+      const dvec4 vj = b.vel[j];
+      const dvec4 wj = b.spin[j];
+      const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+      double dz = pi.z - pj.z;
+      if (P.periodic_z) {
+        if (dz > P.half_Hz) dz -= P.Hz;
+        else if (dz < -P.half_Hz) dz += P.Hz;
+      }
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 > 0.0)) continue;  // coincident particles: density only
+      const double inv_r = rsqrt(r2);
+      const double r = r2 * inv_r;
+      const double inv_r2 = inv_r * inv_r;
+      const double q = r * P.inv_h;
+      const double t1 = 1.0 - 0.5 * q;
+      const double t2 = t1 * t1;
+      const double F = P.cF * t2 * t1;
+      const double W = P.aD * t2 * t2 * (2.0 * q + 1.0);
+      const bool vis_j = pj.w != 0.0;
+      // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
+      const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+      const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
+      const double ux = vx + 0.5 * (dy * sz - dz * sy);
+      const double uy = vy + 0.5 * (dz * sx - dx * sz);
+      const double uz = vz + 0.5 * (dx * sy - dy * sx);
+      const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
+      // The five pair terms collected along r_ij and u_ij (and v_ij for the
+      // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
+      // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F dv/r^2 r_ij
+      // (r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij).
+      const double VF = vj.w * F;
+      const double aP = (vis_j ? cP1 : cP0) * (wi.w + wj.w) * F;
+      const double aT = (vis_j ? cT1 : cT0) * VF;
+      const double aV = vis_j ? VF * inv_r2 * (cBA1 * dv) : 0.0;
+      const double bR = vis_j ? cB1 * VF : 0.0;
+      const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
+      const double al = aP + aT + aV;
+      const double alz = aP + hz * aT + aV;
+      const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
+      double pfx = al * dx + bu * ux;
+      double pfy = al * dy + bu * uy;
+      double pfz = alz * dz + bu * uz;
+      if (kLiteral && literal) {  // coefficient bN of v_ij
+        pfx += bN * vx;
+        pfy += bN * vy;
+        pfz += bN * vz;
+      }
+      fx += pfx;
+      fy += pfy;
+      fz += pfz;
+      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
+      const double hb = -0.5 * bu;
+      const double qx = hb * (dy * uz - dz * uy);
+      const double qy = hb * (dz * ux - dx * uz);
+      const double qz = hb * (dx * uy - dy * ux);
+      tx += qx;
+      ty += qy;
+      tz += qz;
+      if (pj.w >= 2.0) {  // torque exerted by the wall on particle i
+        wx += pi.y * pfz - pi.z * pfy + qx;
+        wy += pi.z * pfx - pi.x * pfz + qy;
+        wz += pi.x * pfy - pi.y * pfx + qz;
+      }
     }
   }
   const double inv_m = 1.0 / m_i;
@@ -458,15 +465,12 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches) {
-  if (lc.block_density == 256)
-    k_density_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
+  if (lc.block_density == 32)
+    k_density_fp64<32><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(n, b, f, inst, cw, nw, err);
   else if (lc.block_density == 64)
-    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
+    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
   else
-    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
+    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -474,12 +478,23 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  if (lc.block_forces == 256)
-    k_forces_fp64<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, nw, err);
-  else if (lc.block_forces == 64)
-    k_forces_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, nw, err);
-  else
-    k_forces_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
+  const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
+                 g64 = (unsigned)((n + 63) / 64);
+  if (lc.any_literal) {
+    if (lc.block_forces == 256)
+      k_forces_fp64<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+    else if (lc.block_forces == 64)
+      k_forces_fp64<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+    else
+      k_forces_fp64<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+  } else {
+    if (lc.block_forces == 256)
+      k_forces_fp64<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+    else if (lc.block_forces == 64)
+      k_forces_fp64<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+    else
+      k_forces_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -201,6 +202,7 @@ struct sph_ctx {
   bool forces_valid = false;
   bool lists_valid = false;      // neighbour lists of the current sorted order
   int launches_per_step = 0;
+  int64_t max_cells = 0;         // largest cell grid of an instance
   LaunchCfg lc;
 };
 
@@ -218,6 +220,8 @@ struct Carved {
   uint32_t* err;
   double *part_tw, *part_diag, *diag_out;
   char* backup;
+  char* staging;
+  size_t staging_bytes;
   size_t state_bytes, ws_bytes;
 };
 
@@ -282,11 +286,18 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.nw.list = w.take<uint32_t>((int64_t)cap * n);
   c.nw.count = w.take<uint32_t>(n);
   c.nw.posf = precision == SPH_FP64 ? w.take<float4>(n) : nullptr;
+  c.nw.mask = w.take<uint32_t>((int64_t)kMaxCandWords * n);
+  c.nw.ncand = w.take<uint32_t>(n_cells / kSlabs);
+  c.nw.cand = w.take<uint32_t>(n_cells / kSlabs * kMaxCand);
   c.nw.cap = cap;
   c.part_tw = w.take<double>(3 * total_chunks);
   c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
   c.diag_out = w.take<double>((int64_t)kDiagFields * n_inst);
   c.backup = w.take<char>(backup_bytes(precision, n, n_inst));
+  // host arrays in and out: at most 17 doubles per particle (sph_get_state),
+  // each array aligned
+  c.staging_bytes = sizeof(double) * 17 * (size_t)n + 8 * kAlign;
+  c.staging = w.take<char>((int64_t)c.staging_bytes);
   c.ws_bytes = w.off + kAlign;
 }
 
@@ -364,10 +375,10 @@ inline void mark(Marks* m, cudaStream_t s) {
   if (m) cudaEventRecord(m->ev[m->k++], s);
 }
 
-constexpr int kStages = 8;
+constexpr int kStages = 9;
 const char* const kStageNames[kStages] = {"kick_drift_keys", "cell_scan", "scatter_cell_sort",
-                                          "reorder",         "density",   "forces",
-                                          "kick",            "wall_torque"};
+                                          "reorder",         "cell_search", "density",
+                                          "forces",          "kick",        "wall_torque"};
 
 bool mixed(const sph_ctx* c) { return c->precision == SPH_MIXED; }
 
@@ -395,14 +406,31 @@ sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
   return SPH_OK;
 }
 
-sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
-  mark(m, s);
+sph_status enqueue_search(sph_ctx* c, cudaStream_t s, int* launches) {
+  const float4* rec = mixed(c) ? c->mbuf[c->cur].off : c->nw.posf;
+  CK(launch_cell_search(mixed(c), c->n, rec, c->inst, c->n_inst, c->max_cells, c->cw, c->nw,
+                        c->err, s, c->lc, launches));
+  return SPH_OK;
+}
+
+sph_status enqueue_density_only(sph_ctx* c, cudaStream_t s, int* launches) {
   if (mixed(c))
     CK(launch_density_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->cw, c->nw, c->err, s,
                             c->lc, launches));
   else
-    CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
-                           launches));
+    CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s,
+                           c->lc, launches));
+  return SPH_OK;
+}
+
+// Neighbour search, then density and pressure.
+sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
+  mark(m, s);
+  sph_status st = enqueue_search(c, s, launches);
+  if (st != SPH_OK) return st;
+  mark(m, s);
+  st = enqueue_density_only(c, s, launches);
+  if (st != SPH_OK) return st;
   c->lists_valid = true;
   return SPH_OK;
 }
@@ -582,8 +610,8 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->part_diag = cv.part_diag;
   c->diag_out = cv.diag_out;
   c->backup = cv.backup;
-  c->staging = cv.nw.list;
-  c->staging_bytes = sizeof(uint32_t) * (size_t)pl.cap * (size_t)pl.n;
+  c->staging = cv.staging;
+  c->staging_bytes = cv.staging_bytes;
   c->stream = (cudaStream_t)stream;
   int dev = 0;
   auto fail = [&](sph_status s) {
@@ -595,14 +623,25 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
     return fail(SPH_ERR_CUDA);
   c->lc.block_density = 128;
   c->lc.block_forces = 128;
-  c->lc.density_window = 1;
+  c->lc.search_warps = 4;
+  c->lc.any_literal = false;
+  for (const InstDev& d : pl.inst) {
+    c->max_cells = std::max(c->max_cells, (int64_t)d.nx * d.ny * d.nz);
+    if (d.flags & SPH_SN_LITERAL) c->lc.any_literal = true;
+  }
+  {
+    static std::once_flag once;
+    static cudaError_t prep = cudaSuccess;
+    std::call_once(once, [] { prep = prepare_search_kernels(); });
+    if (prep != cudaSuccess) return fail(SPH_ERR_CUDA);
+  }
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(SPH_ERR_CUDA);
 
   cudaStream_t s = c->stream;
   const int64_t n = pl.n;
   // inputs: device pointers are used in place, host pointers go through the
-  // staging area (the neighbour-list region, unused until the first density)
+  // staging area
   char* stg = (char*)c->staging;
   size_t off = 0;
   auto stage = [&](const void* src, size_t bytes, const void** dst) -> sph_status {
@@ -787,11 +826,7 @@ sph_status sph_get_state(sph_ctx* c, double* pos, double* vel, double* spin, dou
     if (outs[k] && dev[k] != outs[k])
       CK(cudaMemcpyAsync(outs[k], dev[k], sizeof(double) * (size_t)width[k] * (size_t)n,
                          cudaMemcpyDeviceToHost, c->stream));
-  sph_status st = sph_check(c);
-  // host outputs were staged in the neighbour-list region; a, alpha, rho and P
-  // are intact but the lists must be rebuilt by the next density pass
-  if (off > 0) c->lists_valid = false;
-  return st;
+  return sph_check(c);
 }
 
 sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t cap) {
@@ -802,8 +837,7 @@ sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int64_t* nbr, int64_t
   CK(cudaMemcpyAsync(cnt.data(), c->nw.count, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
                      c->stream));
   CK(cudaMemcpyAsync(id.data(), mixed(c) ? c->mbuf[c->cur].id : c->buf[c->cur].id,
-                     sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
-                     c->stream));
+                     sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(list.data(), c->nw.list, sizeof(uint32_t) * list.size(),
                      cudaMemcpyDeviceToHost, c->stream));
   sph_status st = sph_check(c);
@@ -898,37 +932,46 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
     if (e0) cudaEventDestroy(e0);
     return SPH_ERR_CUDA;
   }
-  const int cand[3] = {64, 128, 256};
-  float best_d = INFINITY, best_f = INFINITY;
-  int bd = c->lc.block_density, bf = c->lc.block_forces, bw = c->lc.density_window;
-  // density: block size x candidate walk (x-windows or whole rows); forces: block size
+  const int cand[3] = {64, 128, 256};   // pair pass
+  const int dcand[3] = {32, 64, 128};   // density pass
+  const int wcand[3] = {2, 4, 8};
+  float best[3] = {INFINITY, INFINITY, INFINITY};
+  LaunchCfg pick = c->lc;
+  // trials 0-2: warps per block of the neighbour search (timed alone);
+  // 3-5: density block size (timed with the search before it, which rebuilds
+  // the lists it compacts); 6-8: pair-pass block size
   for (int trial = 0; trial < 9 && st == SPH_OK; ++trial) {
-    const bool dens = trial < 6;
+    const int kind = trial / 3;
     LaunchCfg saved = c->lc;
-    if (dens) {
-      c->lc.block_density = cand[trial % 3];
-      c->lc.density_window = trial / 3;
-    } else {
-      c->lc.block_forces = cand[trial - 6];
-    }
+    if (kind == 0) c->lc.search_warps = wcand[trial % 3];
+    if (kind == 1) c->lc.block_density = dcand[trial % 3];
+    if (kind == 2) c->lc.block_forces = cand[trial % 3];
     cudaEventRecord(e0, s);
-    for (int r = 0; r < reps && st == SPH_OK; ++r)
-      st = dens ? enqueue_density(c, s, nullptr) : enqueue_forces(c, s, 0, nullptr);
+    for (int r = 0; r < reps && st == SPH_OK; ++r) {
+      if (kind == 0) st = enqueue_search(c, s, nullptr);
+      else if (kind == 1) st = enqueue_density(c, s, nullptr);
+      else st = enqueue_forces(c, s, 0, nullptr);
+    }
     cudaEventRecord(e1, s);
     float ms = 0.f;
     if (st == SPH_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
       st = SPH_ERR_CUDA;
-    if (dens && ms < best_d) best_d = ms, bd = c->lc.block_density, bw = c->lc.density_window;
-    if (!dens && ms < best_f) best_f = ms, bf = c->lc.block_forces;
+    if (ms < best[kind]) {
+      best[kind] = ms;
+      if (kind == 0) pick.search_warps = c->lc.search_warps;
+      if (kind == 1) pick.block_density = c->lc.block_density;
+      if (kind == 2) pick.block_forces = c->lc.block_forces;
+    }
     c->lc = saved;
+    // the density trials must see the chosen search shape
+    if (kind == 0 && trial == 2) c->lc.search_warps = pick.search_warps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SPH_OK) return st;
-  c->lc.block_density = bd;
-  c->lc.block_forces = bf;
-  c->lc.density_window = bw;
+  c->lc = pick;
+  const int bd = pick.block_density, bf = pick.block_forces;
   // restore the pair-pass outputs, and drop the graphs captured with the old
   // shapes; they are captured again by the next sph_step
   st = enqueue_density(c, s, nullptr);
@@ -946,11 +989,11 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
 }
 
 sph_status sph_get_launch_config(const sph_ctx* c, int32_t* block_density, int32_t* block_forces,
-                                 int32_t* density_window) {
+                                 int32_t* search_warps) {
   if (!c) return SPH_ERR_ARG;
   if (block_density) *block_density = c->lc.block_density;
   if (block_forces) *block_forces = c->lc.block_forces;
-  if (density_window) *density_window = c->lc.density_window;
+  if (search_warps) *search_warps = c->lc.search_warps;
   return SPH_OK;
 }
 

@@ -135,17 +135,28 @@ struct CellWs {
   int64_t n_scan_blocks;
 };
 
-// Neighbour lists.  Entry t of particle i lives at nbr_slot(n, i, t): groups
-// of 8 consecutive entries of one particle form one 32-byte sector, and the
-// groups of consecutive particles are adjacent ([cap/8][n][8]), so a warp
-// writes whole sectors and reads 1 KB contiguous per group.  An entry holds
-// the neighbour's sorted index in its low 26 bits and, in the top 6 bits, the
-// cell displacement code (dx+1) | (dy+1) << 2 | (dz+1) << 4 of the neighbour's
-// cell relative to the particle's own (used by the mixed form).
-constexpr int kNbrGroup = 8;
+// Neighbour sets.  The neighbour search writes, for every grid cell, its
+// candidate table: the particles of the 27-cell stencil in candidate order
+// (rows dz, dy, cells kc, sorted index), at most kMaxCand entries, each the
+// candidate's sorted index in the low 26 bits and, in the top 6 bits, the
+// cell displacement code (dx+1) | (dy+1) << 2 | (dz+1) << 4 of the particle's
+// cell relative to the candidate's (used by the mixed form).  Per particle it
+// writes one bit per candidate of its cell: word k of particle i, at
+// mask[k * n + i], covers candidates 32k .. 32k + 31.  The density pass walks
+// the set bits in order (the FP64 form re-tests each exactly) and writes the
+// neighbours as i's neighbour list for the pair pass.
 constexpr uint32_t kNbrIndexBits = 26;
 constexpr uint32_t kNbrIndexMask = (1u << kNbrIndexBits) - 1u;
 constexpr int64_t kMaxParticles = (int64_t)1 << kNbrIndexBits;  // 67,108,864
+constexpr int kMaxCand = 1024;
+constexpr int kMaxCandWords = kMaxCand / 32;
+
+// Neighbour lists.  Entry t of particle i lives at nbr_slot(n, i, t): groups
+// of 8 consecutive entries of one particle form one 32-byte sector, and the
+// groups of consecutive particles are adjacent ([cap/8][n][8]), so a warp
+// writes whole sectors and reads 1 KB contiguous per group.  An entry is a
+// candidate-table entry (index | displacement code).
+constexpr int kNbrGroup = 8;
 
 __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t n, int64_t i, uint32_t t) {
   return (((int64_t)(t >> 3) * n + i) << 3) + (int64_t)(t & 7u);
@@ -153,20 +164,59 @@ __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t n, int64_t i, uint3
 
 struct NbrWs {
   uint32_t* list;       // neighbour entries, layout above
-  uint32_t* count;      // neighbours per particle
+  uint32_t* count;      // neighbours per particle (list length)
   float4* posf;         // FP32 copy of sorted positions (FP64-form prefilter)
-  int32_t cap;          // slots per particle (multiple of 8)
+  uint32_t* mask;       // [kMaxCandWords][n] candidate hit bits
+  uint32_t* cand;       // [grid cells][kMaxCand] candidate table of each cell
+  uint32_t* ncand;      // [grid cells] candidates of each cell
+  int32_t cap;          // list slots per particle (multiple of 8)
 };
 
 #ifdef __CUDACC__
-// Per-thread neighbour-list builder.  push() stores every candidate entry in
-// the thread's shared-memory staging and advances the fill only if it is a
-// neighbour (no branch per candidate); drain(), called by all lanes of a warp
-// at the same points (every kDrainEvery pushes), writes the complete groups
-// of 8 as full 32-byte sectors and keeps the remainder.  Entries beyond
-// nw.cap are counted but dropped.
-constexpr int kDrainEvery = 32;
-constexpr int kStageWords = 40;  // >= 7 + kDrainEvery
+// Walks the set bits of one particle's candidate mask in candidate order and
+// yields the candidate-table entries, B at a time: the B table loads of a
+// batch are independent and in flight together.  The K mask words are first
+// copied, also all in flight together, to the thread's column of shared
+// memory (word k at sw[k * stride]).
+struct MaskWalk {
+  const uint32_t* __restrict__ tab;
+  uint32_t* sw;
+  uint32_t stride, K;
+  uint32_t k = 0, w = 0;
+  __device__ __forceinline__ MaskWalk(const NbrWs& nw, int64_t n, int64_t i, int64_t g,
+                                      uint32_t* sw_, uint32_t stride_)
+      : tab(nw.cand + g * kMaxCand), sw(sw_), stride(stride_) {
+    K = (nw.ncand[g] + 31u) >> 5;
+    const uint32_t* __restrict__ mw = nw.mask + i;
+#pragma unroll 4
+    for (uint32_t t = 0; t < K; ++t) sw[t * stride] = mw[(int64_t)t * n];
+    w = sw[0];
+  }
+  // Fills e[0 .. m) with the next m <= B entries; m = 0 at the end.
+  template <int B>
+  __device__ __forceinline__ uint32_t next(uint32_t (&e)[B]) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      while (w == 0u && k + 1 < K) w = sw[++k * stride];
+      if (w != 0u) {
+        const uint32_t bit = (uint32_t)__ffs(w) - 1u;
+        w &= w - 1u;
+        e[u] = tab[(k << 5) + bit];
+        m = (uint32_t)u + 1u;
+      }
+    }
+    return m;
+  }
+};
+
+// Per-thread neighbour-list builder.  push() stores an entry in the thread's
+// shared-memory staging and advances the fill only if it is kept (a
+// predicated store, no branch); drain(), called whenever 32 or more entries
+// are staged, writes the complete groups of 8 as full 32-byte sectors and
+// keeps the remainder.  Entries beyond nw.cap are counted but dropped.
+constexpr int kDrainAt = 32;
+constexpr int kStageWords = 40;   // >= kDrainAt - 1 + the largest batch pushed
 constexpr int kStageStride = 41;  // odd stride spreads the threads over banks
 
 struct ListWriter {
@@ -179,7 +229,7 @@ struct ListWriter {
   __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
       : list(nw.list), n(n_), i(i_), st(st_), groups((uint32_t)nw.cap >> 3) {}
   __device__ __forceinline__ void push(uint32_t e, bool keep) {
-    if (keep) st[pend++] = e;  // a predicated store, no branch
+    if (keep) st[pend++] = e;
   }
   __device__ __forceinline__ void write_group(uint32_t from) {
     if (written < groups) {
@@ -206,58 +256,6 @@ struct ListWriter {
     return t < (groups << 3) ? t : (groups << 3);
   }
 };
-
-// Visits the candidates of one particle: the 9 rows (dy, dz) of the 27-cell
-// stencil, each row the 3 x-adjacent cells cx-1..cx+1, which the sort keeps
-// as one run of S x-slabs per cell.  With window, a row out of reach (its
-// nearest y-z distance >= the cutoff) is skipped and within a row only the
-// slabs overlapping the x-window |x_j - x_i| <= sqrt(cut^2 - d_yz^2) (+ a
-// margin) are visited.  Runs are split at the cell boundaries, so the cell
-// displacement c_i - c_j of every candidate is known: visit(j, exL, eyL, ezL,
-// code) gets it as -1/0/+1 times the cell side per axis and as its 6-bit
-// code.  (ox, oy, oz) are the particle's FP32 offsets inside its cell
-// (cx, cy, cz); cut2 is the squared cutoff of the candidate test.
-template <class Visit>
-__device__ __forceinline__ void visit_candidates(const uint32_t* __restrict__ start, int64_t base,
-                                                 int nx, int ny, int nz, int S, bool periodic,
-                                                 int cx, int cy, int cz, float Lx, float Ly,
-                                                 float Lz, float ox, float oy, float oz,
-                                                 float cut2, bool window, Visit&& visit) {
-  const float inv_slab = (float)S / Lx;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int z2 = cz + dz;
-    if (periodic) z2 = z2 < 0 ? z2 + nz : (z2 >= nz ? z2 - nz : z2);
-    const float rz = dz < 0 ? oz : (dz > 0 ? Lz - oz : 0.f);
-    const float ezL = (float)(-dz) * Lz;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int slo = 0, shi = 3 * S - 1;
-      if (window) {
-        const float ry = dy < 0 ? oy : (dy > 0 ? Ly - oy : 0.f);
-        const float d2 = ry * ry + rz * rz;
-        if (d2 >= cut2 + 1e-3f) continue;  // row out of reach
-        const float w = sqrtf(fmaxf(cut2 - d2, 0.f)) + 2e-3f;
-        const float xr = Lx + ox;  // x relative to the start of cell cx-1
-        const int lo = (int)floorf((xr - w) * inv_slab);
-        const int hi = (int)floorf((xr + w) * inv_slab);
-        slo = lo < 0 ? 0 : lo;
-        shi = hi > 3 * S - 1 ? 3 * S - 1 : hi;
-      }
-      const int64_t rowkey =
-          base + ((int64_t)(cx - 1) + (int64_t)nx * ((cy + dy) + (int64_t)ny * z2)) * S;
-      const float eyL = (float)(-dy) * Ly;
-      const uint32_t code_yz = ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4);
-      for (int kc = slo / S; kc < 3 && kc * S <= shi; ++kc) {
-        const int a = kc * S > slo ? kc * S : slo;
-        const int b = kc * S + S - 1 < shi ? kc * S + S - 1 : shi;
-        const uint32_t j0 = start[rowkey + a];
-        const uint32_t j1 = start[rowkey + b + 1];
-        const float exL = (float)(1 - kc) * Lx;
-        const uint32_t code = ((uint32_t)(2 - kc) | code_yz) << kNbrIndexBits;
-        for (uint32_t j = j0; j < j1; ++j) visit(j, exL, eyL, ezL, code);
-      }
-    }
-  }
-}
 #endif
 
 }  // namespace sphgb

@@ -10,9 +10,10 @@ sph_status derive_instance(const sph_params& p, InstDev& d);
 
 struct LaunchCfg {
   int sm_count;          // multiprocessors of the device
-  int block_density;     // threads per block of the density pass
+  int block_density;     // threads per block of the density pass (32, 64, 128)
   int block_forces;      // threads per block of the pair pass
-  int density_window;    // 1: candidate walk restricted to x-windows; 0: whole rows
+  int search_warps;      // warps (cells) per block of the neighbour search
+  bool any_literal;      // some instance uses the literal F_sn (SPH_SN_LITERAL)
 };
 
 // ---- cell build (sph_cells.cu) --------------------------------------------
@@ -21,6 +22,21 @@ cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, int* launches);
 // perm[start[key[i]] + slot[i]] = i, then sort each cell by particle id.
 cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches);
+
+// ---- neighbour search (sph_search.cu) ---------------------------------------
+// One warp per cell of every instance (grid.y = instance); writes the
+// candidate tables and candidate masks of nw, from which the density pass
+// builds the neighbour lists.  rec: the per-particle FP32 records (mixed: cell offset
+// and species, FP64 form: the rounded position and species).  mixed_form:
+// exact FP32 test with cell-displacement codes; otherwise the FP32 prefilter.
+cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec, const InstDev* inst,
+                               int32_t n_inst, int64_t max_cells, const CellWs& cw,
+                               const NbrWs& nw, uint32_t* err, cudaStream_t s,
+                               const LaunchCfg& lc, int* launches);
+// Raise the dynamic shared-memory limit of the search kernels (once, before
+// any launch or stream capture).
+cudaError_t prepare_search_kernels();
+int search_max_warps();
 
 // ---- FP64 path (sph_fp64.cu) ------------------------------------------------
 // mode 0: initial placement (walls at the current phase, no kick/drift);

@@ -239,10 +239,17 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
 
 // -------------------------------------------------------------------- density
 
+// Density deviation and Tait pressure, one thread per particle, summed over
+// the set bits of the particle's candidate mask (sph_search.cu; the search's
+// test is exact in this form, so every set bit is a neighbour), which are
+// also written, in order, as the particle's neighbour list for the pair pass.
+// The walk takes 8 neighbours at a time: their table entries, then their
+// offset records, are loaded together before the 8 pairs are summed.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
-                NbrWs nw, uint32_t* err, int window) {
+                NbrWs nw, uint32_t* err) {
+  __shared__ uint32_t smask[BLOCK * kMaxCandWords];
   __shared__ uint32_t stage[BLOCK * kStageStride];
   __shared__ float4 dtab[64];
   fill_disp_table(dtab);
@@ -251,7 +258,6 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
   const float4 oi = b.off[i];
-  const uint32_t ci = b.cell[i];
   const int sp = (int)oi.w;
   const int si = sp == 0 ? 0 : 1;
   float delta;
@@ -259,53 +265,35 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   if (sp == 3) {
     delta = 0.f;
   } else {
-    const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
-    const float cut2 = P.cut2_f;
+    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
     ListWriter lw(nw, n, i, stage + threadIdx.x * kStageStride);
-    // the x-windows of the 27 neighbour cells as one flat candidate sequence;
-    // the cell displacement of every candidate is known from its run, without
-    // reading the candidate's cell.  The test uses the same antisymmetric pair
-    // vector as every later use of the entry, so j lists i exactly when i
-    // lists j.
-    uint32_t it = 0;
-    visit_candidates(cw.start, P.cell_base, P.nx, P.ny, P.nz, P.slabs, P.periodic_z != 0, cx, cy,
-                     cz, P.cellf[0], P.cellf[1], P.cellf[2], oi.x, oi.y, oi.z, cut2, window != 0,
-                     [&](uint32_t j, float exL, float eyL, float ezL, uint32_t code) {
-                       const float4 oj = b.off[j];
-                       const float ddx = exL + (oi.x - oj.x);
-                       const float ddy = eyL + (oi.y - oj.y);
-                       const float ddz = ezL + (oi.z - oj.z);
-                       const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                       lw.push(j | code, r2 < cut2 && j != (uint32_t)i);
-                       if (++it == kDrainEvery) {
-                         lw.drain();
-                         it = 0;
-                       }
-                     });
-    cnt = lw.finish();
-    if (lw.overflow()) latch(err, ERR_NEIGHBORS);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
-    uint32_t ent_n = cnt > 0 ? nw.list[nbr_slot(n, i, 0)] : 0u;
-    float4 oj_n = cnt > 0 ? b.off[ent_n & kNbrIndexMask] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t t = 0; t < cnt; ++t) {
-      // the next entry and its offset record are loaded one pair ahead
-      const uint32_t ent = ent_n;
-      const float4 oj = oj_n;
-      if (t + 1 < cnt) {
-        ent_n = nw.list[nbr_slot(n, i, t + 1)];
-        oj_n = b.off[ent_n & kNbrIndexMask];
+    uint32_t e[8];
+    for (uint32_t m; (m = mk.next(e)) != 0u;) {
+      float4 o[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u)
+        if (u < m) o[u] = b.off[e[u] & kNbrIndexMask];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        if (u < m) {
+          float dx, dy2, dz2;
+          entry_vec(P, dtab, e[u], oi, o[u], dx, dy2, dz2);
+          const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+          const float q = sqrtf(r2) * P.inv_h_f;
+          const float t1 = 1.f - 0.5f * q;
+          const float t2 = t1 * t1;
+          const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);
+          acc.add(P.mr_f[o[u].w == 0.f ? 0 : 1] * W);
+          lw.push(e[u], true);
+        }
       }
-      float dx, dy2, dz2;
-      entry_vec(P, dtab, ent, oi, oj, dx, dy2, dz2);
-      const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-      const float q = sqrtf(r2) * P.inv_h_f;
-      const float t1 = 1.f - 0.5f * q;
-      const float t2 = t1 * t1;
-      const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);
-      acc.add(P.mr_f[oj.w == 0.f ? 0 : 1] * W);
+      if (lw.pend >= (uint32_t)kDrainAt) lw.drain();
     }
+    cnt = lw.finish();
+    if (lw.overflow()) latch(err, ERR_NEIGHBORS);
     delta = acc.value();
   }
   nw.count[i] = cnt;
@@ -323,7 +311,9 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
 
 // ------------------------------------------------------------------ pair pass
 
-template <int BLOCK>
+// kLiteral: some instance uses the literal F_sn (coefficient of v_ij); the
+// default form has none and drops that term at compile time.
+template <int BLOCK, bool kLiteral>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                uint32_t* err) {
@@ -354,109 +344,130 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float kB = (fl & SPH_TERM_ROT) ? P.B_f : 0.f;
   const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
   const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
-  const bool lit = (fl & SPH_SN_LITERAL) != 0;
+  const bool lit = kLiteral && (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
+  // The species factors of the pair terms depend on j only through whether
+  // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
+  // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
+  // rotational); walls count as viscous.
+  const float mX0 = inv_i ? 0.f : 1.f;  // j inviscid
+  const float mX1 = inv_i ? 1.f : 0.f;  // j viscous or wall
+  const float mV1 = inv_i ? 0.f : 1.f;  // (mV = 0 for an inviscid j)
+  const float cP0 = kP * (m_i * P.m_f[0]), cP1 = kP * (m_i * P.m_f[1]);
+  const float cT0 = kT * mX0, cT1 = kT * mX1;
+  const float cBA1 = mV1 != 0.f ? kB - kA : 0.f;
+  const float cB0 = -kB * 0.f, cB1 = -kB * mV1;
+  const float cN0 = -kN * mX0, cN1 = -kN * mX1;
   // absolute position of i about the rotation axis (wall torque only)
   const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
   const double zi = P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z;
   const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
-  // compensated sums across groups of 8 neighbours (one list group), plain
-  // FP32 sums inside a group
+  // compensated sums across groups of 8 neighbours, plain FP32 sums inside
+  // a group
   Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
   float gfx = 0.f, gfy = 0.f, gfz = 0.f, gtx = 0.f, gty = 0.f, gtz = 0.f;
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const uint32_t cnt = nw.count[i];
-  // software pipeline: the list entry two ahead and the neighbour record one
-  // ahead are in flight while the current pair is evaluated
+  // The list is read one group of 8 entries (one 32-byte sector) at a time,
+  // the next group while the current one is evaluated; the neighbour record
+  // of the next entry is loaded one pair ahead.
+  const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t ent_n = cnt > 0 ? nw.list[nbr_slot(n, i, 0)] : 0u;
-  uint32_t ent_nn = cnt > 1 ? nw.list[nbr_slot(n, i, 1)] : 0u;
+  uint4 ga = make_uint4(0u, 0u, 0u, 0u), gb = ga;
   float4 oj_n = zero4, vj_n = zero4, wj_n = zero4;
   if (cnt > 0) {
-    const uint32_t j0 = ent_n & kNbrIndexMask;
+    ga = groups[2 * i];
+    gb = groups[2 * i + 1];
+    const uint32_t j0 = ga.x & kNbrIndexMask;
     oj_n = b.off[j0];
     vj_n = b.vel[j0];
     wj_n = b.spin[j0];
   }
-  for (uint32_t t = 0; t < cnt; ++t) {
-    const uint32_t ent = ent_n;
-    const float4 oj = oj_n, vj = vj_n, wj = wj_n;
-    ent_n = ent_nn;
-    if (t + 1 < cnt) {
-      const uint32_t jn = ent_n & kNbrIndexMask;
-      oj_n = b.off[jn];
-      vj_n = b.vel[jn];
-      wj_n = b.spin[jn];
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    if (t0 + 8 < cnt) {
+      const int64_t g = 2 * ((int64_t)((t0 >> 3) + 1) * n + i);
+      ga = groups[g];
+      gb = groups[g + 1];
     }
-    if (t + 2 < cnt) ent_nn = nw.list[nbr_slot(n, i, t + 2)];
-    float dx, dy, dz;
-    entry_vec(P, dtab, ent, oi, oj, dx, dy, dz);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 > 0.f) {  // coincident particles: density only
-    const float inv_r = rsqrtf(r2);
-    const float r = r2 * inv_r;
-    const float inv_r2 = inv_r * inv_r;
-    const float q = r * P.inv_h_f;
-    const float t1 = 1.f - 0.5f * q;
-    const float t2 = t1 * t1;
-    const float F = P.cF_f * (t2 * t1);
-    const float W = P.aD_f * (t2 * t2) * (2.f * q + 1.f);
-    const bool inv_j = oj.w == 0.f;
-    const float mX = (inv_i != inv_j) ? 1.f : 0.f;
-    const float mV = (!inv_i && !inv_j) ? 1.f : 0.f;
-    const float m_j = P.m_f[inv_j ? 0 : 1];
-    // symmetric pair scalars (products taken in an order independent of i, j)
-    const float VV = vi.w * vj.w;
-    const float MM = m_i * m_j;
-    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-    const float sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
-    const float ux = vx + 0.5f * (dy * sz - dz * sy);
-    const float uy = vy + 0.5f * (dz * sx - dx * sz);
-    const float uz = vz + 0.5f * (dx * sy - dy * sx);
-    const float dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij (symmetric)
-    // the five terms collected along r_ij, u_ij and (literal F_sn) v_ij:
-    // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F dv/r^2 r_ij
-    const float VF = VV * F;
-    const float aP = kP * MM * ((wi.w + wj.w) * F);
-    const float aT = kT * mX * VF;
-    // r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij
-    const float aV = VF * mV * inv_r2 * ((kB - kA) * dv);
-    const float bR = -kB * mV * VF;
-    const float bN = -kN * mX * (VV * W);
-    const float al = aP + aT + aV;
-    const float alz = aP + hz * aT + aV;
-    const float bu = lit ? bR : bR + bN;
-    const float bv = lit ? bN : 0.f;
-    const float pfx = al * dx + bu * ux + bv * vx;
-    const float pfy = al * dy + bu * uy + bv * vy;
-    const float pfz = alz * dz + bu * uz + bv * vz;
-    gfx += pfx;
-    gfy += pfy;
-    gfz += pfz;
-    // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
-    const float hb = -0.5f * bu;
-    const float qx = hb * (dy * uz - dz * uy);
-    const float qy = hb * (dz * ux - dx * uz);
-    const float qz = hb * (dx * uy - dy * ux);
-    gtx += qx;
-    gty += qy;
-    gtz += qz;
-    if (oj.w >= 2.f) {
-      wx += pyi * pfz - pzi * pfy + qx;
-      wy += pzi * pfx - pxi * pfz + qy;
-      wz += pxi * pfy - pyi * pfx + qz;
+    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      if (u >= m) break;
+      const uint32_t ent = e[u];
+      const float4 oj = oj_n, vj = vj_n, wj = wj_n;
+      if (t0 + u + 1 < cnt) {
+        const uint32_t jn = (u < 7 ? e[u + 1] : ga.x) & kNbrIndexMask;
+        oj_n = b.off[jn];
+        vj_n = b.vel[jn];
+        wj_n = b.spin[jn];
+      }
+      float dx, dy, dz;
+      entry_vec(P, dtab, ent, oi, oj, dx, dy, dz);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 > 0.f)) continue;  // coincident particles: density only
+      const float inv_r = rsqrtf(r2);
+      const float r = r2 * inv_r;
+      const float inv_r2 = inv_r * inv_r;
+      const float q = r * P.inv_h_f;
+      const float t1 = 1.f - 0.5f * q;
+      const float t2 = t1 * t1;
+      const float F = P.cF_f * (t2 * t1);
+      const float W = P.aD_f * (t2 * t2) * (2.f * q + 1.f);
+      const bool vis_j = oj.w != 0.f;
+      // symmetric pair scalars (products taken in an order independent of i, j)
+      const float VV = vi.w * vj.w;
+      const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+      const float sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
+      const float ux = vx + 0.5f * (dy * sz - dz * sy);
+      const float uy = vy + 0.5f * (dz * sx - dx * sz);
+      const float uz = vz + 0.5f * (dx * sy - dy * sx);
+      const float dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij (symmetric)
+      // the five terms collected along r_ij, u_ij and (literal F_sn) v_ij:
+      // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F dv/r^2 r_ij
+      // (r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij)
+      const float VF = VV * F;
+      const float aP = (vis_j ? cP1 : cP0) * ((wi.w + wj.w) * F);
+      const float aT = (vis_j ? cT1 : cT0) * VF;
+      const float aV = (VF * inv_r2) * ((vis_j ? cBA1 : 0.f) * dv);
+      const float bR = (vis_j ? cB1 : cB0) * VF;
+      const float bN = (vis_j ? cN1 : cN0) * (VV * W);
+      const float al = aP + aT + aV;
+      const float alz = aP + hz * aT + aV;
+      const float bu = lit ? bR : bR + bN;
+      float pfx = al * dx + bu * ux;
+      float pfy = al * dy + bu * uy;
+      float pfz = alz * dz + bu * uz;
+      if (kLiteral && lit) {
+        pfx += bN * vx;
+        pfy += bN * vy;
+        pfz += bN * vz;
+      }
+      gfx += pfx;
+      gfy += pfy;
+      gfz += pfz;
+      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
+      const float hb = -0.5f * bu;
+      const float qx = hb * (dy * uz - dz * uy);
+      const float qy = hb * (dz * ux - dx * uz);
+      const float qz = hb * (dx * uy - dy * ux);
+      gtx += qx;
+      gty += qy;
+      gtz += qz;
+      if (oj.w >= 2.f) {
+        wx += pyi * pfz - pzi * pfy + qx;
+        wy += pzi * pfx - pxi * pfz + qy;
+        wz += pxi * pfy - pyi * pfx + qz;
+      }
     }
-    }
-    if ((t & 7u) == 7u || t + 1 == cnt) {
-      fx.add(gfx);
-      fy.add(gfy);
-      fz.add(gfz);
-      tx.add(gtx);
-      ty.add(gty);
-      tz.add(gtz);
-      gfx = gfy = gfz = gtx = gty = gtz = 0.f;
-    }
+    fx.add(gfx);
+    fy.add(gfy);
+    fz.add(gfz);
+    tx.add(gtx);
+    ty.add(gty);
+    tz.add(gtz);
+    gfx = gfy = gfz = gtx = gty = gtz = 0.f;
   }
   const float inv_m = P.inv_m_f[si], inv_I = P.inv_I_f[si];
   const float ax = fx.value(), ay = fy.value(), az = fz.value();
@@ -563,16 +574,12 @@ cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                  uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                  int* launches) {
-  if (lc.block_density == 256) {
-    k_density_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
-  } else if (lc.block_density == 64) {
-    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
-  } else {
-    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err,
-                                                                   lc.density_window);
-  }
+  if (lc.block_density == 32)
+    k_density_mixed<32><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+  else if (lc.block_density == 64)
+    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+  else
+    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -580,12 +587,22 @@ cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
 cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  if (lc.block_forces == 256) {
-    k_forces_mixed<256><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, f, inst, nw, err);
-  } else if (lc.block_forces == 64) {
-    k_forces_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, nw, err);
+  const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
+                 g64 = (unsigned)((n + 63) / 64);
+  if (lc.any_literal) {
+    if (lc.block_forces == 256)
+      k_forces_mixed<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+    else if (lc.block_forces == 64)
+      k_forces_mixed<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+    else
+      k_forces_mixed<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   } else {
-    k_forces_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
+    if (lc.block_forces == 256)
+      k_forces_mixed<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+    else if (lc.block_forces == 64)
+      k_forces_mixed<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+    else
+      k_forces_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   }
   if (launches) ++*launches;
   return cudaGetLastError();

@@ -1,0 +1,230 @@
+// Neighbour search of the density pass (Sec. 2.3: all particles within the
+// kernel support 2h), one warp per grid cell, shared by both state forms.
+//
+// Every particle of a cell has the same 27-cell candidate set: the 9 rows
+// (dy, dz) of x-adjacent cells cx-1..cx+1, each row one contiguous run of the
+// sorted order per cell.  A warp takes one cell, writes its candidate
+// sequence (rows dz, dy, cells kc, index j) once as the cell's candidate
+// table, and tests the candidates with the lanes spread over the CANDIDATES:
+// for each target particle t of the cell, the 32 lanes test 32 candidates at
+// once and a ballot gives the 32-bit hit mask of (t, chunk), so no lane idles
+// on a short cell and the control flow never diverges.  The output is one
+// bit per (particle, candidate): mask word k of particle i covers candidates
+// 32k .. 32k+31 of its cell's table.  The density pass walks these bits in
+// order, which is the neighbour order of the lists it writes for the pair
+// pass.
+//
+// Mixed form: the test is exact, r^2 < (2h)^2 in FP32 on the pair vector
+// (c_i - c_j) L + (o_i - o_j), which every later use of the entry recomputes
+// bit for bit; the test of (j, i) negates that of (i, j), so the neighbour
+// sets are symmetric.  Table entries carry the cell-displacement code.
+// FP64 form: an FP32 prefilter on rounded absolute positions (the periodic
+// image in z taken per run) against a widened bound, a superset of the FP64
+// neighbours; the density pass re-tests every candidate it is given in FP64.
+#include "sph_kernels.h"
+
+namespace sphgb {
+namespace {
+
+constexpr int kSeg = 256;                      // candidates staged at a time
+constexpr int kSegChunks = kSeg / 32;
+constexpr int kMaskStride = kSegChunks + 1;    // odd: lane t reads bank (9 t + k) % 32
+constexpr int kMaxSearchWarps = 8;
+static_assert(kMaxCand % kSeg == 0, "segments tile the candidate table");
+
+struct WarpSmem {
+  uint32_t ent[kSeg];                 // candidate index | cell-displacement code
+  float4 tgt[32];                     // records of the current targets
+  uint32_t mask[32 * kMaskStride];    // hit mask of (target, chunk)
+};
+
+__device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
+  if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
+}
+
+// rec: per sorted particle (x, y, z, species); mixed: the offset inside the
+// cell, FP64 form: the FP32-rounded absolute position.
+template <bool kMixed>
+__global__ void __launch_bounds__(32 * kMaxSearchWarps, 3)
+k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restrict__ inst,
+              CellWs cw, NbrWs nw, uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  const InstDev& P = inst[blockIdx.y];
+  const int64_t l = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= (int64_t)P.nx * P.ny * P.nz) return;
+  const int S = P.slabs;
+  const int64_t key0 = P.cell_base + l * S;
+  const uint32_t i0 = cw.start[key0], i1 = cw.start[key0 + S];
+  if (i0 == i1) return;
+  const int cx = (int)(l % P.nx);
+  const int cy = (int)((l / P.nx) % P.ny);
+  const int cz = (int)(l / ((int64_t)P.nx * P.ny));
+
+  // run table: lane r < 27 holds run r = (dz + 1) 9 + (dy + 1) 3 + kc, the
+  // particles of cell (cx - 1 + kc, cy + dy, cz + dz)
+  uint32_t rj0 = 0, rlen = 0, rcode = 0;
+  if (lane < 27) {
+    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, kc = lane % 3;
+    int z2 = cz + dz;
+    if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
+    const int64_t key =
+        P.cell_base +
+        ((int64_t)(cx - 1 + kc) + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2)) * S;
+    rj0 = cw.start[key];
+    rlen = cw.start[key + S] - rj0;
+    rcode = ((uint32_t)(2 - kc) | ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4))
+            << kNbrIndexBits;
+  }
+  uint32_t incl = rlen;  // inclusive scan of the run lengths over the lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(~0u, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t rpre = incl - rlen;
+  uint32_t total = __shfl_sync(~0u, incl, 31);
+  const int64_t g = key0 / S;  // grid cell over all instances
+  if (total > (uint32_t)kMaxCand) {  // more candidates than the table holds
+    if (lane == 0) latch(err, ERR_NEIGHBORS);
+    total = kMaxCand;
+  }
+  if (lane == 0) nw.ncand[g] = total;
+  uint32_t* __restrict__ table = nw.cand + g * kMaxCand;
+  const uint32_t pre_self = __shfl_sync(~0u, rpre, 13);  // the cell's own run
+  const float cut2 = kMixed ? P.cut2_f : P.cut2f_margin;
+
+  bool table_done = false;
+  for (uint32_t tb = i0; tb < i1; tb += 32) {
+    const uint32_t nt = min(32u, i1 - tb);
+    const uint32_t i = tb + lane;
+    float4 mine = make_float4(0.f, 0.f, 0.f, 3.f);
+    if (lane < nt) mine = rec[i];
+    sm.tgt[lane] = mine;
+    const bool active = lane < nt && mine.w != 3.f;  // outer-wall particles keep no list
+    if (__ballot_sync(~0u, active) == 0u) {
+      if (lane < nt) nw.count[i] = 0u;
+      continue;
+    }
+    const uint32_t self_q = pre_self + (i - i0);  // candidate position of i itself
+    uint32_t hits = 0;
+    for (uint32_t s0 = 0; s0 < total; s0 += kSeg) {
+      const uint32_t nseg = min((uint32_t)kSeg, total - s0);
+      __syncwarp();
+      if (lane < 27) {  // lane r writes the entries of run r that fall in this segment
+        const uint32_t e0 = s0 > rpre ? s0 - rpre : 0u;
+        const uint32_t end = s0 + nseg - rpre;  // used only if the run starts before it
+        const uint32_t e1 = s0 + nseg > rpre ? (rlen < end ? rlen : end) : 0u;
+        for (uint32_t e = e0; e < e1; ++e) sm.ent[rpre + e - s0] = (rj0 + e) | rcode;
+      }
+      __syncwarp();
+      if (!table_done)  // the cell's candidate table, once per cell
+        for (uint32_t q = lane; q < nseg; q += 32) table[s0 + q] = sm.ent[q];
+      const uint32_t nch = (nseg + 31) >> 5;
+      // each lane's candidate record, the next chunk's loaded one chunk ahead
+      uint32_t ent_n = sm.ent[lane < nseg ? lane : 0u];
+      float4 c_n = rec[ent_n & kNbrIndexMask];
+      for (uint32_t k = 0; k < nch; ++k) {
+        const uint32_t q = (k << 5) + lane;
+        const bool valid = q < nseg;
+        const uint32_t ent = ent_n;
+        float4 c = c_n;
+        if (k + 1 < nch) {
+          const uint32_t qn = q + 32u;
+          ent_n = sm.ent[qn < nseg ? qn : 0u];
+          c_n = rec[ent_n & kNbrIndexMask];
+        }
+        const uint32_t code = ent >> kNbrIndexBits;
+        float ex = 0.f, ey = 0.f, ez = 0.f;
+        if (kMixed) {  // (c_i - c_j) L per axis; exact
+          ex = (float)((int)(code & 3u) - 1) * P.cellf[0];
+          ey = (float)((int)((code >> 2) & 3u) - 1) * P.cellf[1];
+          ez = (float)((int)(code >> 4) - 1) * P.cellf[2];
+        } else if (P.periodic_z) {  // image of a candidate across the z period
+          const int z2 = cz + 1 - (int)(code >> 4);
+          if (z2 < 0) c.z -= P.Hzf;
+          else if (z2 >= P.nz) c.z += P.Hzf;
+        }
+        // the pair vector e + (o_t - c) of the mixed form is the one every
+        // later use of the entry recomputes; four targets per round keep
+        // four independent chains in flight ahead of their ballots
+        auto hit = [&](const float4& o) {
+          float dx = o.x - c.x, dy = o.y - c.y, dz = o.z - c.z;
+          if (kMixed) {
+            dx = ex + dx;
+            dy = ey + dy;
+            dz = ez + dz;
+          }
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          return valid && r2 < cut2;
+        };
+        uint32_t* mk = sm.mask + k;
+        uint32_t t = 0;
+        for (; t + 4 <= nt; t += 4) {
+          const bool h0 = hit(sm.tgt[t]), h1 = hit(sm.tgt[t + 1]);
+          const bool h2 = hit(sm.tgt[t + 2]), h3 = hit(sm.tgt[t + 3]);
+          const uint32_t m0 = __ballot_sync(~0u, h0), m1 = __ballot_sync(~0u, h1);
+          const uint32_t m2 = __ballot_sync(~0u, h2), m3 = __ballot_sync(~0u, h3);
+          if (lane == 0) {
+            mk[t * kMaskStride] = m0;
+            mk[(t + 1) * kMaskStride] = m1;
+            mk[(t + 2) * kMaskStride] = m2;
+            mk[(t + 3) * kMaskStride] = m3;
+          }
+        }
+        for (; t < nt; ++t) {
+          const uint32_t m0 = __ballot_sync(~0u, hit(sm.tgt[t]));
+          if (lane == 0) mk[t * kMaskStride] = m0;
+        }
+      }
+      __syncwarp();
+      if (active) {  // lane t stores its mask words, without the self bit
+        const uint32_t* mrow = sm.mask + lane * kMaskStride;
+        uint32_t* out = nw.mask + (int64_t)(s0 >> 5) * n + i;
+        for (uint32_t k = 0; k < nch; ++k) {
+          uint32_t m = mrow[k];
+          const uint32_t qs = self_q - s0 - (k << 5);  // < 32 iff i itself is in chunk k
+          if (qs < 32u) m &= ~(1u << qs);
+          out[(int64_t)k * n] = m;
+          hits += __popc(m);
+        }
+      }
+    }
+    table_done = true;
+    if (lane < nt) nw.count[i] = hits;
+  }
+}
+
+size_t search_smem(int warps) { return sizeof(WarpSmem) * (size_t)warps; }
+
+}  // namespace
+
+int search_max_warps() { return kMaxSearchWarps; }
+
+cudaError_t prepare_search_kernels() {
+  const int bytes = (int)search_smem(kMaxSearchWarps);
+  cudaError_t e = cudaFuncSetAttribute(k_cell_search<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cell_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec, const InstDev* inst,
+                               int32_t n_inst, int64_t max_cells, const CellWs& cw,
+                               const NbrWs& nw, uint32_t* err, cudaStream_t s,
+                               const LaunchCfg& lc, int* launches) {
+  int warps = lc.search_warps;
+  if (warps < 1 || warps > kMaxSearchWarps) warps = 4;
+  const dim3 grid((unsigned)((max_cells + warps - 1) / warps), (unsigned)n_inst);
+  const size_t smem = search_smem(warps);
+  if (mixed_form)
+    k_cell_search<true><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+  else
+    k_cell_search<false><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace sphgb
