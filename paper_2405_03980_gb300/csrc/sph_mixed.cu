@@ -244,13 +244,13 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
 // test is exact in this form, so every set bit is a neighbour), which are
 // also written, in order, as the particle's neighbour list for the pair pass.
 // The walk takes 8 neighbours at a time: their table entries, then their
-// offset records, are loaded together before the 8 pairs are summed.
+// offset records, are loaded together before the 8 pairs are summed, and the
+// 8 entries are stored as one 32-byte list group.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
                 NbrWs nw, uint32_t* err) {
   __shared__ uint32_t smask[BLOCK * kMaxCandWords];
-  __shared__ uint32_t stage[BLOCK * kStageStride];
   __shared__ float4 dtab[64];
   fill_disp_table(dtab);
   __syncthreads();
@@ -266,12 +266,19 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     delta = 0.f;
   } else {
     MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
-    ListWriter lw(nw, n, i, stage + threadIdx.x * kStageStride);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
-    uint32_t e[8];
-    for (uint32_t m; (m = mk.next(e)) != 0u;) {
+    const uint32_t groups = (uint32_t)nw.cap >> 3;
+    uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
+      // every batch but the last holds 8 neighbours: it is list group g
+      if (g < groups) {
+        uint4* dst = reinterpret_cast<uint4*>(nw.list + nbr_slot(n, i, g << 3));
+        dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
+        dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
+      }
+      cnt += m;
       float4 o[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u)
@@ -287,13 +294,13 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
           const float t2 = t1 * t1;
           const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);
           acc.add(P.mr_f[o[u].w == 0.f ? 0 : 1] * W);
-          lw.push(e[u], true);
         }
       }
-      if (lw.pend >= (uint32_t)kDrainAt) lw.drain();
     }
-    cnt = lw.finish();
-    if (lw.overflow()) latch(err, ERR_NEIGHBORS);
+    if (cnt > (groups << 3)) {
+      latch(err, ERR_NEIGHBORS);
+      cnt = groups << 3;
+    }
     delta = acc.value();
   }
   nw.count[i] = cnt;
