@@ -50,6 +50,38 @@ DENSITY_FLOPS_PER_PAIR = {"fp64": 20, "mixed": 31}
 # wall), counted on the host from the initial positions (candidate_tests).
 SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per particle of
+# one launch, from the ncu captures summarised in profiles/ (2,525,900-particle
+# cylinder; the traffic grows with the particle count).  Each figure holds
+# only while the kernel's sources hash to the values recorded with it; after
+# any change the roofline reports traffic null until it is re-measured.
+DRAM_BYTES_PER_PARTICLE = {
+    "k_cell_search<true>": (167.0, {"sph_search.cu": "25d1ca680aace19b"}),
+    "k_cell_search<false>": (None, {}),
+    "k_density_mixed": (553.7, {"sph_mixed.cu": "eac4f928232bf250",
+                                "sph_internal.h": "bff276d2739b8616"}),
+    "k_forces_mixed": (414.4, {"sph_mixed.cu": "eac4f928232bf250",
+                               "sph_internal.h": "bff276d2739b8616"}),
+    "k_density_fp64": (640.7, {"sph_fp64.cu": "07bc608c6c1f09a3",
+                               "sph_internal.h": "bff276d2739b8616"}),
+    "k_forces_fp64": (508.0, {"sph_fp64.cu": "07bc608c6c1f09a3",
+                              "sph_internal.h": "bff276d2739b8616"}),
+}
+
+
+def measured_traffic(kernel, n_particles):
+    """Per-launch DRAM bytes of kernel at n_particles, or None when no capture
+    matches the current sources."""
+    import hashlib
+    per, srcs = DRAM_BYTES_PER_PARTICLE.get(kernel, (None, {}))
+    if per is None:
+        return None
+    for f, h in srcs.items():
+        path = os.path.join(ROOT, "paper_2405_03980_gb300", "csrc", f)
+        if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
+            return None
+    return per * n_particles
+
 
 def candidate_tests(insts):
     """Sum over the particles that keep a neighbour list of the particle count
@@ -391,7 +423,9 @@ def run_ours(args, dist):
             ach = fpp * units / t / 1e12
             roofs.setdefault(f, {})[stage] = {
                 "kernel": kern, "bound": "alu", "achieved": ach, "peak": pk,
-                "unit": "TFLOP/s", "frac": ach / pk, "traffic": None, "peak_source": src,
+                "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": measured_traffic(kern, n_part), "traffic_unit": "bytes per launch",
+                "peak_source": src,
                 "work": f"{fpp} {u} flop x {units} {what} per launch",
                 "launch_ms": results[f]["stages"][stage]}
     dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
