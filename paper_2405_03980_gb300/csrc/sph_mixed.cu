@@ -289,7 +289,8 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
           float dx, dy2, dz2;
           entry_vec(P, dtab, e[u], oi, o[u], dx, dy2, dz2);
           const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          const float q = sqrtf(r2) * P.inv_h_f;
+          // r = r2 / sqrt(r2) from the approximate reciprocal square root
+          const float q = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * P.inv_h_f;
           const float t1 = 1.f - 0.5f * q;
           const float t2 = t1 * t1;
           const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);

@@ -28,14 +28,15 @@ namespace {
 
 constexpr int kSeg = 256;                      // candidates staged at a time
 constexpr int kSegChunks = kSeg / 32;
-constexpr int kMaskStride = kSegChunks + 1;    // odd: lane t reads bank (9 t + k) % 32
+constexpr int kMaskRow = 36;  // mask words of one chunk: 4 targets per 16-byte store, and
+                              // lane t reading word t of chunk k hits bank (4k + t) % 32
 constexpr int kMaxSearchWarps = 8;
 static_assert(kMaxCand % kSeg == 0, "segments tile the candidate table");
 
 struct WarpSmem {
   uint32_t ent[kSeg];                 // candidate index | cell-displacement code
   float4 tgt[32];                     // records of the current targets
-  uint32_t mask[32 * kMaskStride];    // hit mask of (target, chunk)
+  alignas(16) uint32_t mask[kSegChunks * kMaskRow];  // hit mask of (chunk, target)
 };
 
 __device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
@@ -159,7 +160,7 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
           const float r2 = dx * dx + dy * dy + dz * dz;
           return valid && r2 < cut2;
         };
-        uint32_t* mk = sm.mask + k;
+        uint32_t* mk = sm.mask + k * kMaskRow;
         uint32_t t = 0;
         for (; t + 4 <= nt; t += 4) {
           const bool h0 = hit(sm.tgt[t]), h1 = hit(sm.tgt[t + 1]);
@@ -167,23 +168,20 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
           const uint32_t m0 = __ballot_sync(~0u, h0), m1 = __ballot_sync(~0u, h1);
           const uint32_t m2 = __ballot_sync(~0u, h2), m3 = __ballot_sync(~0u, h3);
           if (lane == 0) {
-            mk[t * kMaskStride] = m0;
-            mk[(t + 1) * kMaskStride] = m1;
-            mk[(t + 2) * kMaskStride] = m2;
-            mk[(t + 3) * kMaskStride] = m3;
+            *reinterpret_cast<uint4*>(mk + t) = make_uint4(m0, m1, m2, m3);
           }
         }
         for (; t < nt; ++t) {
           const uint32_t m0 = __ballot_sync(~0u, hit(sm.tgt[t]));
-          if (lane == 0) mk[t * kMaskStride] = m0;
+          if (lane == 0) mk[t] = m0;
         }
       }
       __syncwarp();
       if (active) {  // lane t stores its mask words, without the self bit
-        const uint32_t* mrow = sm.mask + lane * kMaskStride;
+        const uint32_t* mcol = sm.mask + lane;
         uint32_t* out = nw.mask + (int64_t)(s0 >> 5) * n + i;
         for (uint32_t k = 0; k < nch; ++k) {
-          uint32_t m = mrow[k];
+          uint32_t m = mcol[k * kMaskRow];
           const uint32_t qs = self_q - s0 - (k << 5);  // < 32 iff i itself is in chunk k
           if (qs < 32u) m &= ~(1u << qs);
           out[(int64_t)k * n] = m;

@@ -233,7 +233,7 @@ def test_autotune_leaves_state_and_results_unchanged(precision):
     a.step(2)
     b.step(2)
     bd, bf = b.autotune(2)
-    assert bd in (64, 128, 256) and bf in (64, 128, 256)
+    assert bd in (32, 64, 128) and bf in (64, 128, 256)
     sa, sb = a.state_arrays(), b.state_arrays()
     for f in sa:
         assert np.array_equal(sa[f], sb[f]), f
