@@ -67,3 +67,27 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_candidate_test_count_matches_brute_force():
+    """bench.candidate_tests (the work unit of the neighbour-search roofline)
+    equals a direct count: for every particle that keeps a list, the
+    particles whose grid cell lies within one cell of its own on each axis
+    (periodic in z), itself included."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2405_03980_gb300 import synth
+    c = synth.workload("cyl_8960")
+    p = c.params
+    lo = np.array(p["box_lo"], dtype=float)
+    hi = np.array(p["box_hi"], dtype=float)
+    ncell = np.maximum(np.floor((hi - lo) / (2.0 * p["h"])), 1).astype(int)
+    cell = np.clip(np.floor((c.pos - lo) / ((hi - lo) / ncell)).astype(int), 0, ncell - 1)
+    rows = np.nonzero(c.species != 3)[0]
+    total = 0
+    for k in range(0, len(rows), 512):  # blocks of rows keep the memory small
+        d = np.abs(cell[rows[k:k + 512], None, :] - cell[None, :, :]).astype(np.int32)
+        d[:, :, 2] = np.minimum(d[:, :, 2], ncell[2] - d[:, :, 2])
+        total += int((d <= 1).all(axis=2).sum())
+    assert bench.candidate_tests([c]) == total

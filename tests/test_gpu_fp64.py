@@ -223,6 +223,35 @@ def test_device_errors_are_latched_not_trapped():
 
 
 @pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
+def test_neighbour_overflows_are_latched(precision):
+    """About 80 neighbours against a list capacity of 64, and a cluster whose
+    27-cell stencil holds more particles than the candidate table (1024):
+    both are reported as SPH_ERR_NEIGHBORS, without a fault, and the context
+    stays usable."""
+    c = synth.workload("cyl_8960")
+    with pytest.raises(B.SphError) as e:
+        s = sim_of(c, precision=precision, nbr_cap=64)
+        s.check()
+    assert e.value.status == -9
+    if precision == B.SPH_FP64:
+        # 1200 fluid particles packed into one cell of side 2h at the centre
+        rng = np.random.default_rng(3)
+        pos = c.pos.copy()
+        fluid = np.nonzero(c.species < 2)[0][:1200]
+        h = c.params["h"]
+        pos[fluid] = rng.uniform(-0.9 * h, 0.9 * h, size=(len(fluid), 3)) + [0.0, 0.0, 10.0]
+        dense = synth.Cylinder(**{**c.__dict__, "pos": pos})
+        with pytest.raises(B.SphError) as e:
+            s = sim_of(dense, precision=precision, nbr_cap=1024)
+            s.check()
+        assert e.value.status == -9
+    ok = sim_of(c, precision=precision)
+    ok.step(1)
+    ok.check()
+    ok.close()
+
+
+@pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
 def test_autotune_leaves_state_and_results_unchanged(precision):
     """The autotuner times launch shapes on the current state; per-particle
     results do not depend on the block size, so the state after tuning and the
