@@ -172,6 +172,20 @@ __global__ void k_reorder_fp64(int64_t n, Fp64Buf src, Fp64Buf dst, CellWs cw, N
   }
 }
 
+// Species and wrap tests without FP64 instructions (the FP64 pipe is the
+// bottleneck of this form): the species codes 0..3 are stored as doubles, so
+// the high word orders them (0.0 -> 0, 1.0 -> 0x3ff00000, 2.0 -> 0x40000000,
+// 3.0 -> 0x40080000).
+__device__ __forceinline__ bool inviscid(double w) { return __double2hiint(w) == 0; }
+__device__ __forceinline__ bool is_wall(double w) { return __double2hiint(w) >= 0x40000000; }
+// z period crossed by the pair (i, j): +1 if j's image lies one period above
+// i's cell row (i in the bottom row, cell code dz + 1 = 2), -1 if below (i in
+// the top row, code 0), else 0.  The code is c_i - c_j + 1 per axis.
+__device__ __forceinline__ int z_wrap(uint32_t ent, int cz_i, int nz) {
+  const uint32_t cz = ent >> (kNbrIndexBits + 4);
+  return (cz_i == 0 && cz == 2u) ? 1 : ((cz_i == nz - 1 && cz == 0u) ? -1 : 0);
+}
+
 // -------------------------------------------------------------------- density
 
 __device__ __forceinline__ double ipow(double x, int e) {
@@ -204,7 +218,10 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   if (sp == 3) {
     rho = P.rho0;
   } else {
-    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
+    const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
+    const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
+    const bool per = P.periodic_z != 0;
+    MaskWalk mk(nw, n, i, g, smask + threadIdx.x, BLOCK);
     ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
     rho = m_i * P.aD;  // self term W(0)
     uint32_t e[4];
@@ -219,19 +236,20 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
           const double dx = __dsub_rn(pi.x, pj[u].x);
           const double dy = __dsub_rn(pi.y, pj[u].y);
           double dz = __dsub_rn(pi.z, pj[u].z);
-          if (P.periodic_z) {
-            if (dz > P.half_Hz) dz = __dsub_rn(dz, P.Hz);
-            else if (dz < -P.half_Hz) dz = __dadd_rn(dz, P.Hz);
+          if (per) {  // minimum image across the z period
+            const int wz = z_wrap(e[u], cz_i, P.nz);
+            if (wz > 0) dz = __dadd_rn(dz, P.Hz);
+            else if (wz < 0) dz = __dsub_rn(dz, P.Hz);
           }
           const double r2 =
               __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
           const bool keep = r2 < P.cut2;
-          out.push(e[u] & kNbrIndexMask, keep);
+          out.push(e[u], keep);  // index and cell-displacement code
           if (keep) {
             const double q = sqrt(r2) * P.inv_h;
             const double t1 = 1.0 - 0.5 * q;
             const double t2 = t1 * t1;
-            const double m_j = pj[u].w == 0.0 ? P.m_s : P.m_n;
+            const double m_j = inviscid(pj[u].w) ? P.m_s : P.m_n;
             rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
           }
         }
@@ -257,7 +275,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 template <int BLOCK, bool kLiteral>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
-              NbrWs nw, uint32_t* err) {
+              CellWs cw, NbrWs nw, uint32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const dvec4 pi = b.pos[i];
@@ -295,6 +313,9 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double cBA1 = mV1 != 0.0 ? cB - cA : 0.0;
   const double cB1 = -cB * mV1;
   const double cN0 = -cN * mX0, cN1 = -cN * mX1;
+  const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
+  const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
+  const bool per = P.periodic_z != 0;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   double tx = 0.0, ty = 0.0, tz = 0.0;
   double wx = 0.0, wy = 0.0, wz = 0.0;
@@ -315,12 +336,16 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const dvec4 wj = b.spin[j];
       const double dx = pi.x - pj.x, dy = pi.y - pj.y;
       double dz = pi.z - pj.z;
-      if (P.periodic_z) {
-        if (dz > P.half_Hz) dz -= P.Hz;
-        else if (dz < -P.half_Hz) dz += P.Hz;
+      if (per) {  // minimum image across the z period
+        const int wz = z_wrap(e[u], cz_i, P.nz);
+        if (wz > 0) dz += P.Hz;
+        else if (wz < 0) dz -= P.Hz;
       }
       const double r2 = dx * dx + dy * dy + dz * dz;
-      if (!(r2 > 0.0)) continue;  // coincident particles: density only
+      // coincident particles (r2 = 0) count for the density only; r2 > 0 is
+      // tested on the bits (r2 >= 0 or NaN)
+      const long long r2b = __double_as_longlong(r2);
+      if (!(r2b > 0 && r2b <= 0x7ff0000000000000LL)) continue;
       const double inv_r = rsqrt(r2);
       const double r = r2 * inv_r;
       const double inv_r2 = inv_r * inv_r;
@@ -329,7 +354,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double t2 = t1 * t1;
       const double F = P.cF * t2 * t1;
       const double W = P.aD * t2 * t2 * (2.0 * q + 1.0);
-      const bool vis_j = pj.w != 0.0;
+      const bool vis_j = !inviscid(pj.w);
       // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
       const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
       const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
@@ -369,7 +394,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       tx += qx;
       ty += qy;
       tz += qz;
-      if (pj.w >= 2.0) {  // torque exerted by the wall on particle i
+      if (is_wall(pj.w)) {  // torque exerted by the wall on particle i
         wx += pi.y * pfz - pi.z * pfy + qx;
         wy += pi.z * pfx - pi.x * pfz + qy;
         wz += pi.x * pfy - pi.y * pfx + qz;
@@ -476,24 +501,25 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
 }
 
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
-                               const InstDev* inst, const NbrWs& nw, uint32_t* err,
-                               cudaStream_t s, const LaunchCfg& lc, int* launches) {
+                               const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                               uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                               int* launches) {
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
   if (lc.any_literal) {
     if (lc.block_forces == 256)
-      k_forces_fp64<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
     else if (lc.block_forces == 64)
-      k_forces_fp64<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
     else
-      k_forces_fp64<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   } else {
     if (lc.block_forces == 256)
-      k_forces_fp64<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
     else if (lc.block_forces == 64)
-      k_forces_fp64<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
     else
-      k_forces_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   }
   if (launches) ++*launches;
   return cudaGetLastError();

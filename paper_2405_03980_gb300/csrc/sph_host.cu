@@ -443,7 +443,8 @@ sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches
     CK(launch_forces_mixed(c->n, c->mbuf[k], c->mf, c->inst, c->nw, c->err, s, c->lc,
                            launches));
   else
-    CK(launch_forces_fp64(c->n, c->buf[k], c->f, c->inst, c->nw, c->err, s, c->lc, launches));
+    CK(launch_forces_fp64(c->n, c->buf[k], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
+                          launches));
   mark(m, s);
   if (advance) {
     if (mixed(c))

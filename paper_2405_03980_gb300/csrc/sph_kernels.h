@@ -53,7 +53,8 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches);
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
-                               const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                               const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                               uint32_t* err,
                                cudaStream_t s, const LaunchCfg& lc, int* launches);
 cudaError_t launch_kick_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                              const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
