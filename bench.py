@@ -56,15 +56,16 @@ SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (167.0, {"sph_search.cu": "25d1ca680aace19b"}),
+    "k_cell_search<true>": (167.2, {"sph_search.cu": "95a0e3df5866f820",
+                                    "sph_internal.h": "bff276d2739b8616"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (553.7, {"sph_mixed.cu": "eac4f928232bf250",
+    "k_density_mixed": (553.7, {"sph_mixed.cu": "e29fca062b0b9188",
                                 "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_mixed": (414.4, {"sph_mixed.cu": "eac4f928232bf250",
+    "k_forces_mixed": (414.1, {"sph_mixed.cu": "e29fca062b0b9188",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_density_fp64": (640.7, {"sph_fp64.cu": "07bc608c6c1f09a3",
+    "k_density_fp64": (641.4, {"sph_fp64.cu": "f331d5406f7cf1cf",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_fp64": (508.0, {"sph_fp64.cu": "07bc608c6c1f09a3",
+    "k_forces_fp64": (511.8, {"sph_fp64.cu": "f331d5406f7cf1cf",
                               "sph_internal.h": "bff276d2739b8616"}),
 }
 
