@@ -70,6 +70,43 @@ DRAM_BYTES_PER_PARTICLE = {
 }
 
 
+# Algorithmic DRAM bytes per particle of the streaming stages (plain, mixed):
+# the state each reads and writes once (section 8 of the design notes).
+STREAM_BYTES_PER_PARTICLE = {
+    "kick_drift_keys": {"fp64": 224, "mixed": 120},
+    "cell_scan": {"fp64": 0, "mixed": 0},            # 8 B per cell, below
+    "scatter_cell_sort": {"fp64": 16, "mixed": 16},
+    "reorder": {"fp64": 240, "mixed": 144},
+    "kick": {"fp64": 192, "mixed": 96},
+    "wall_torque": {"fp64": 32, "mixed": 16},
+}
+
+
+def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, hbm_gbs):
+    """Lower bound of one step: every stage at its own roof (the streaming
+    stages at the measured HBM bandwidth with their algorithmic bytes, the
+    search, density and pair passes at the measured FMA rate with their
+    algorithmic flops), summed, and the fraction of it the measured step
+    reaches."""
+    bound = {}
+    for st, b in STREAM_BYTES_PER_PARTICLE.items():
+        by = b[form] * n_particles + (8 * n_cells if st == "cell_scan" else 0)
+        bound[st] = by / (hbm_gbs * 1e9) * 1e3
+    flops = {"cell_search": SEARCH_FLOPS_PER_TEST[form] * tests,
+             "density": DENSITY_FLOPS_PER_PAIR[form] * pairs,
+             "forces": FORCE_FLOPS_PER_PAIR[form] * pairs}
+    for st, fl in flops.items():
+        pk = peak_alu["mixed"] if st == "cell_search" else peak_alu[form]  # search is FP32
+        bound[st] = fl / (pk * 1e12) * 1e3
+    tb = sum(bound.values())
+    tm = sum(stage_ms.values())
+    return {"bound_ms": tb, "measured_ms": tm, "frac": tb / tm,
+            "per_stage_bound_ms": bound, "hbm_gbs": hbm_gbs,
+            "note": "sum over stages of algorithmic bytes / measured HBM bandwidth or "
+                    "algorithmic flops / measured FMA rate; measured_ms sums the per-stage "
+                    "event times"}
+
+
 def measured_traffic(kernel, n_particles):
     """Per-launch DRAM bytes of kernel at n_particles, or None when no capture
     matches the current sources."""
@@ -431,6 +468,16 @@ def run_ours(args, dist):
                 "launch_ms": results[f]["stages"][stage]}
     dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
     roof = roofs[best][dom_stage]
+    hbm = 6695.5
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    n_cells = sum(float((np.floor((np.array(c.params["box_hi"]) - np.array(c.params["box_lo"]))
+                                  / (2.0 * c.params["h"])) + [2, 2, 0]).prod()) for c in insts)
+    steps_roof = {f: step_roofline(results[f]["stages"], f, n_part, n_cells,
+                                   results[f]["diag"]["n_pairs"], tests, peaks, hbm)
+                  for f in results}
 
     # end-to-end through the C ABI with host buffers
     e2e = None
@@ -482,6 +529,7 @@ def run_ours(args, dist):
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,
             "roofline": roof,
+            "step_roofline": steps_roof,
             "roofline_by_form": roofs,
             "cpu_baseline": cpu,
             "e2e": e2e,
