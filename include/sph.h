@@ -178,6 +178,17 @@ SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
 /* FP64 diagnostics of instance inst (synchronises). */
 SPH_API sph_status sph_diagnostics(sph_ctx* ctx, int32_t inst, sph_diag* out);
 
+/* Force breakdown of instance inst (Sec. 4, which reports the share of the
+ * pressure, temperature-gradient, shear, rotational and mutual-friction
+ * forces): out[q] = sum over the fluid particles i of |sum_j f_ij^q|, for
+ * q = 0 pressure (M3), 1 interfacial (M4), 2 shear (M5), 3 rotational (M6),
+ * 4 local interaction (M7), each term summed separately over i's neighbour
+ * list, in FP64, from the current state: positions, velocities and spins as
+ * stored, density and pressure of the last density pass (its neighbour
+ * lists).  Terms switched off by the flags give 0.  Needs a density pass
+ * since the last reorder (SPH_ERR_STATE otherwise); synchronises. */
+SPH_API sph_status sph_force_breakdown(sph_ctx* ctx, int32_t inst, double out[5]);
+
 /* Copy the state out in input order (synchronises).  Any pointer may be NULL.
  * pos, vel, spin, acc, dspin: 3n doubles; rho, P: n doubles. */
 SPH_API sph_status sph_get_state(sph_ctx* ctx, double* pos, double* vel, double* spin,

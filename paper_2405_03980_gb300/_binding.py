@@ -87,6 +87,7 @@ def lib(build_if_missing: bool = True):
                 "sph_forces": (C.c_int, [vp]),
                 "sph_step": (C.c_int, [vp, C.c_int32]),
                 "sph_diagnostics": (C.c_int, [vp, C.c_int32, C.POINTER(SphDiag)]),
+                "sph_force_breakdown": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_get_state": (C.c_int, [vp] + [vp] * 7),
                 "sph_get_neighbors": (C.c_int, [vp, i64p, i64p, C.c_int64]),
                 "sph_check": (C.c_int, [vp]),
@@ -115,7 +116,7 @@ def exported_symbols() -> list[str]:
     """Names this binding expects the library to export."""
     return ["sph_params_default", "sph_state_bytes", "sph_workspace_bytes", "sph_init",
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
-            "sph_diagnostics", "sph_get_state", "sph_get_neighbors", "sph_check",
+            "sph_diagnostics", "sph_force_breakdown", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
             "sph_autotune", "sph_get_launch_config",
             "sph_fma_peak", "sph_diag_sums_noalloc", "sph_destroy", "sph_status_string"]
@@ -225,6 +226,14 @@ def sph_diagnostics(ctx, inst: int = 0) -> dict:
     d = SphDiag()
     _ck(lib().sph_diagnostics(ctx, int(inst), C.byref(d)), "sph_diagnostics")
     return d.as_dict()
+
+
+def sph_force_breakdown(ctx, inst: int = 0) -> np.ndarray:
+    """sum_i |f_i^term| for the pressure, interfacial, shear, rotational and
+    local-interaction terms of instance inst (FP64, current state)."""
+    out = (C.c_double * 5)()
+    _ck(lib().sph_force_breakdown(ctx, int(inst), out), "sph_force_breakdown")
+    return np.array(out[:], dtype=np.float64)
 
 
 def sph_get_state(ctx, pos=None, vel=None, spin=None, rho=None, P=None, acc=None, dspin=None):

@@ -759,6 +759,20 @@ sph_status sph_check(sph_ctx* c) {
   return decode_err(e);
 }
 
+sph_status sph_force_breakdown(sph_ctx* c, int32_t inst, double out[5]) {
+  if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
+  if (!c->lists_valid) return SPH_ERR_STATE;  // needs the lists of a density pass
+  if (mixed(c))
+    CK(launch_breakdown_mixed(c->n_inst, c->n, c->total_chunks, c->inst, c->mbuf[c->cur], c->mf,
+                              c->nw, c->part_diag, c->diag_out, c->stream));
+  else
+    CK(launch_breakdown_fp64(c->n_inst, c->n, c->total_chunks, c->inst, c->buf[c->cur], c->f,
+                             c->nw, c->part_diag, c->diag_out, c->stream));
+  CK(cudaMemcpyAsync(out, c->diag_out + (int64_t)inst * kDiagFields, sizeof(double) * 5,
+                     cudaMemcpyDeviceToHost, c->stream));
+  return sph_check(c);
+}
+
 sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
   if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
   if (mixed(c))

@@ -116,4 +116,17 @@ cudaError_t launch_diag_fp64(int32_t n_inst, int64_t total_chunks, const InstDev
                              const Fp64Buf& b, const Fp64Fields& f, const NbrWs& nw,
                              double* partials, double* out, cudaStream_t s);
 
+// Per-instance force breakdown: out[k * kDiagFields + q] = sum over the fluid
+// particles of instance k of |sum_j f_ij^q| for the pair terms q = pressure,
+// interfacial, shear, rotational, local interaction (FP64, current state and
+// neighbour lists).
+cudaError_t launch_breakdown_fp64(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                  const InstDev* inst, const Fp64Buf& b, const Fp64Fields& f,
+                                  const NbrWs& nw, double* partials, double* out,
+                                  cudaStream_t s);
+cudaError_t launch_breakdown_mixed(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                   const InstDev* inst, const MixBuf& b, const MixFields& f,
+                                   const NbrWs& nw, double* partials, double* out,
+                                   cudaStream_t s);
+
 }  // namespace sphgb

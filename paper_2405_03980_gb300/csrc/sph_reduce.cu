@@ -42,11 +42,20 @@ struct Fp64View {
     v[2] = p.z;
   }
   __device__ __forceinline__ double rho(int64_t i, const InstDev&) const { return f.rho[i]; }
-  __device__ __forceinline__ void tw(int64_t i, double* v) const {
+  __device__ __forceinline__ double pres(int64_t i) const { return f.P[i]; }
+  // The wall torque of particle i, if it is not zero (it is zero for every
+  // particle without a wall neighbour, walls included); the test looks at
+  // the bits, so that no FP64 instruction is spent on the zeros.
+  __device__ __forceinline__ bool tw_nonzero(int64_t i, double* v) const {
     const dvec4 p = f.tw[i];
+    const unsigned long long any = ((unsigned long long)__double_as_longlong(p.x) |
+                                    (unsigned long long)__double_as_longlong(p.y) |
+                                    (unsigned long long)__double_as_longlong(p.z)) << 1;
+    if (any == 0ull) return false;  // +0 or -0 in every component
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
+    return true;
   }
 };
 
@@ -79,11 +88,15 @@ struct MixView {
   __device__ __forceinline__ double rho(int64_t i, const InstDev& P) const {
     return P.rho0 * (1.0 + (double)f.delta[i]);
   }
-  __device__ __forceinline__ void tw(int64_t i, double* v) const {
+  __device__ __forceinline__ double pres(int64_t i) const { return (double)f.P[i]; }
+  // The wall torque of particle i, if it is not zero (see Fp64View).
+  __device__ __forceinline__ bool tw_nonzero(int64_t i, double* v) const {
     const float4 p = f.tw[i];
+    if (p.x == 0.f && p.y == 0.f && p.z == 0.f) return false;
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
+    return true;
   }
 };
 
@@ -129,13 +142,25 @@ k_wall_torque_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V,
   __shared__ double sh[3 * kRedThreads];
   const ChunkRange r = chunk_range(inst, n_inst, blockIdx.x);
   double v[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
-    if (V.species(i) >= 2) continue;
-    double t[3];
-    V.tw(i, t);
-    v[0] += t[0];
-    v[1] += t[1];
-    v[2] += t[2];
+  // walls carry a zero wall torque, as does every particle without a wall
+  // neighbour: only the others are added (adding a zero changes no sum).
+  // Four records per round are loaded before they are added, in the same
+  // order as one at a time.
+  for (int64_t i0 = r.begin + threadIdx.x; i0 < r.end; i0 += 4 * kRedThreads) {
+    double t[4][3];
+    bool nz[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + (int64_t)u * kRedThreads;
+      nz[u] = i < r.end && V.tw_nonzero(i, t[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!nz[u]) continue;
+      v[0] += t[u][0];
+      v[1] += t[u][1];
+      v[2] += t[u][2];
+    }
   }
   block_sum<3>(v, sh);
   if (threadIdx.x < 3)
@@ -197,13 +222,14 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
   double v[kSumFields];
 #pragma unroll
   for (int a = 0; a < kSumFields; ++a) v[a] = 0.0;
-  double rmin = INFINITY, rmax = -INFINITY, vmax = 0.0;
+  double rmin = INFINITY, rmax = -INFINITY, vmax2 = 0.0;
+  const double I_s = 1.0 / P.inv_I_s, I_n = 1.0 / P.inv_I_n;  // spin inertia per species
   for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
     const int sp = V.species(i);
     if (sp >= 2) continue;
     const bool inv = sp == 0;
     const double m = inv ? P.m_s : P.m_n;
-    const double I = 1.0 / (inv ? P.inv_I_s : P.inv_I_n);
+    const double I = inv ? I_s : I_n;
     double p[3], u[3], w[3];
     V.pos(i, P, p);
     V.vel(i, u);
@@ -230,8 +256,9 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
     v[15] += (double)nw.count[i];
     rmin = fmin(rmin, rho);
     rmax = fmax(rmax, rho);
-    vmax = fmax(vmax, sqrt(u2));
+    vmax2 = fmax(vmax2, u2);  // the square root of the largest, once
   }
+  const double vmax = sqrt(vmax2);
   block_sum<kSumFields>(v, sh);
   const int t = threadIdx.x;
   mx[0][t] = rmin;
@@ -296,6 +323,120 @@ cudaError_t diag(int32_t n_inst, int64_t total_chunks, const InstDev* inst, cons
   return cudaGetLastError();
 }
 
+// Per-term force magnitudes (the force breakdown the paper reports for its
+// runs, Sec. 4): for every fluid particle i the five pair terms (pressure
+// M3, interfacial M4, shear M5, rotational M6, local interaction M7) are
+// summed separately over i's neighbour list, in FP64 from the state as
+// stored, and sum_i |f_i^term| is accumulated per term.
+template <class View>
+__global__ void __launch_bounds__(kRedThreads)
+k_breakdown_chunks(int32_t n_inst, int64_t n, const InstDev* __restrict__ inst, View V,
+                   NbrWs nw, double* __restrict__ partials) {
+  __shared__ double sh[5 * kRedThreads];
+  const ChunkRange r = chunk_range(inst, n_inst, blockIdx.x);
+  const InstDev& P = inst[r.inst];
+  const uint32_t fl = P.flags;
+  double mag[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
+    const int sp_i = V.species(i);
+    if (sp_i >= 2) continue;
+    const bool inv_i = sp_i == 0;
+    double pi[3], vi[3], wi[3];
+    V.pos(i, P, pi);
+    V.vel(i, vi);
+    V.spin(i, wi);
+    const double rho_i = V.rho(i, P);
+    const double m_i = inv_i ? P.m_s : P.m_n;
+    const double Vi = m_i / rho_i, Pri = V.pres(i) / (rho_i * rho_i);
+    double fs[5][3];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) fs[q][0] = fs[q][1] = fs[q][2] = 0.0;
+    const uint32_t cnt = nw.count[i];
+    for (uint32_t t = 0; t < cnt; ++t) {
+      const uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
+      double pj[3], vj[3], wj[3];
+      V.pos(j, P, pj);
+      V.vel(j, vj);
+      V.spin(j, wj);
+      double d[3] = {pi[0] - pj[0], pi[1] - pj[1], pi[2] - pj[2]};
+      if (P.periodic_z) {
+        if (d[2] > P.half_Hz) d[2] -= P.Hz;
+        else if (d[2] < -P.half_Hz) d[2] += P.Hz;
+      }
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 > 0.0)) continue;
+      const double rr = sqrt(r2);
+      const double e[3] = {d[0] / rr, d[1] / rr, d[2] / rr};
+      const double q = rr * P.inv_h, t1 = 1.0 - 0.5 * q, t2 = t1 * t1;
+      const double F = P.cF * t2 * t1, W = P.aD * t2 * t2 * (2.0 * q + 1.0);
+      const int sp_j = V.species(j);
+      const bool inv_j = sp_j == 0;
+      const double m_j = inv_j ? P.m_s : P.m_n;
+      const double rho_j = V.rho(j, P);
+      const double Vj = m_j / rho_j, Prj = V.pres(j) / (rho_j * rho_j);
+      const bool chiX = inv_i != inv_j, chiV = !inv_i && !inv_j;
+      const double vij[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
+      const double ws[3] = {wi[0] + wj[0], wi[1] + wj[1], wi[2] + wj[2]};
+      const double u[3] = {vij[0] + 0.5 * (d[1] * ws[2] - d[2] * ws[1]),
+                           vij[1] + 0.5 * (d[2] * ws[0] - d[0] * ws[2]),
+                           vij[2] + 0.5 * (d[0] * ws[1] - d[1] * ws[0])};
+      if (fl & SPH_TERM_P) {  // M3
+        const double sP = m_i * m_j * (Pri + Prj) * F;
+        for (int a = 0; a < 3; ++a) fs[0][a] += sP * d[a];
+      }
+      if ((fl & SPH_TERM_T) && chiX) {  // M4, horizontal unless disabled
+        const double sT = P.C_T * Vi * Vj * F;
+        fs[1][0] += sT * d[0];
+        fs[1][1] += sT * d[1];
+        if (!(fl & SPH_HPROJ)) fs[1][2] += sT * d[2];
+      }
+      if ((fl & SPH_TERM_SH) && chiV) {  // M5
+        const double ev = e[0] * vij[0] + e[1] * vij[1] + e[2] * vij[2];
+        const double sA = -P.A * Vi * Vj * F * ev;
+        for (int a = 0; a < 3; ++a) fs[2][a] += sA * e[a];
+      }
+      if ((fl & SPH_TERM_ROT) && chiV) {  // M6
+        const double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        const double sB = -P.B * Vi * Vj * F;
+        for (int a = 0; a < 3; ++a) fs[3][a] += sB * (u[a] - eu * e[a]);
+      }
+      if ((fl & SPH_TERM_SN) && chiX) {  // M7
+        const double sN = -P.C_l * Vi * Vj * W;
+        const double* w = (fl & SPH_SN_LITERAL) ? vij : u;
+        for (int a = 0; a < 3; ++a) fs[4][a] += sN * w[a];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      mag[q] += sqrt(fs[q][0] * fs[q][0] + fs[q][1] * fs[q][1] + fs[q][2] * fs[q][2]);
+  }
+  block_sum<5>(mag, sh);
+  if (threadIdx.x < 5)
+    partials[(int64_t)blockIdx.x * kDiagFields + threadIdx.x] = sh[threadIdx.x * kRedThreads];
+}
+
+// Per-instance sums of the chunk partials, in chunk order.
+__global__ void k_breakdown_final(int32_t n_inst, const InstDev* __restrict__ inst,
+                                  const double* __restrict__ partials, double* __restrict__ out) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_inst) return;
+  const InstDev& P = inst[k];
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t c = 0; c < P.n_chunks; ++c)
+    for (int a = 0; a < 5; ++a) s[a] += partials[(P.chunk_base + c) * kDiagFields + a];
+  for (int a = 0; a < 5; ++a) out[(int64_t)k * kDiagFields + a] = s[a];
+}
+
+template <class View>
+cudaError_t breakdown(int32_t n_inst, int64_t n, int64_t total_chunks, const InstDev* inst,
+                      const View& V, const NbrWs& nw, double* partials, double* out,
+                      cudaStream_t s) {
+  k_breakdown_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, n, inst, V, nw,
+                                                                          partials);
+  k_breakdown_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, partials, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
@@ -324,6 +465,20 @@ cudaError_t launch_diag_mixed(int32_t n_inst, int64_t total_chunks, const InstDe
                               const MixBuf& b, const MixFields& f, const NbrWs& nw,
                               double* partials, double* out, cudaStream_t s) {
   return diag(n_inst, total_chunks, inst, MixView{b, f}, nw, partials, out, s);
+}
+
+cudaError_t launch_breakdown_fp64(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                  const InstDev* inst, const Fp64Buf& b, const Fp64Fields& f,
+                                  const NbrWs& nw, double* partials, double* out,
+                                  cudaStream_t s) {
+  return breakdown(n_inst, n, total_chunks, inst, Fp64View{b, f}, nw, partials, out, s);
+}
+
+cudaError_t launch_breakdown_mixed(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                   const InstDev* inst, const MixBuf& b, const MixFields& f,
+                                   const NbrWs& nw, double* partials, double* out,
+                                   cudaStream_t s) {
+  return breakdown(n_inst, n, total_chunks, inst, MixView{b, f}, nw, partials, out, s);
 }
 
 }  // namespace sphgb

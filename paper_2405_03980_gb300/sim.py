@@ -75,6 +75,9 @@ class Simulation:
     def diagnostics(self, inst: int = 0) -> dict:
         return B.sph_diagnostics(self.ctx, inst)
 
+    def force_breakdown(self, inst: int = 0):
+        return B.sph_force_breakdown(self.ctx, inst)
+
     def state_arrays(self) -> dict:
         n = self.n
         out = {k: np.zeros((n, 3)) for k in ("pos", "vel", "spin", "acc", "dspin")}

@@ -124,11 +124,19 @@ def cylinder(R: float, H: int, Omega: float = 0.1, f_v: float = 0.3,
 
 # Named workloads: the 8,960-particle parity cylinder, the 2.4M and the 19.6M
 # cylinders (R:H = 1:2), and the near-inviscid low-temperature stress case.
+# The paper_* cylinders have the paper's vessel shape (Sec. 3: diameter five
+# times the height, R:H = 2.5:1) at its three resolutions, 2.45M, 8.62M and
+# 19.6M fluid particles (2,454,000, 8,620,224 and 19,636,400 here), with the
+# species drawn in proportion to the density ratio rho_s / rho_n = 5 (a
+# viscous particle with probability 1/6, equal particle masses).
 WORKLOADS = {
     "cyl_8960": dict(R=10.0, H=20, Omega=0.1, f_v=0.3),
     "cyl_2525900": dict(R=72.5, H=145, Omega=0.1, f_v=0.3),
     "cyl_20100112": dict(R=146.0, H=292, Omega=0.1, f_v=0.3),
     "cyl_2525900_lowT": dict(R=72.5, H=145, Omega=0.2, f_v=0.01),
+    "paper_2534800": dict(R=125.0, H=50, Omega=0.1, f_v=1.0 / 6.0),
+    "paper_8802016": dict(R=190.0, H=76, Omega=0.1, f_v=1.0 / 6.0),
+    "paper_19949600": dict(R=250.0, H=100, Omega=0.1, f_v=1.0 / 6.0),
 }
 
 

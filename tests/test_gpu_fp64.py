@@ -57,7 +57,6 @@ def check_fields(st, o, fluid, tol=TOL, fields=("pos", "vel", "spin", "rho", "P"
 
 def compare_neighbours(sim, species, p):
     st = sim.state_arrays()
-    # lists were staged over by get_state: rebuild them for the same positions
     sim.density()
     off_g, nbr_g = sim.neighbors()
     off_o, nbr_o = oracle.neighbors(p, st["pos"])
@@ -220,6 +219,27 @@ def test_device_errors_are_latched_not_trapped():
     ok.step(1)
     ok.check()
     ok.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(B.SPH_FP64, 1e-10), (B.SPH_MIXED, 1e-4)])
+def test_force_breakdown_matches_oracle(precision, tol):
+    """sph_force_breakdown: sum_i |f_i^term| of the pressure, interfacial,
+    shear, rotational and local-interaction terms (the force breakdown of
+    Sec. 4) equals the oracle's term sums for the same state.  The FP64 form
+    agrees to round-off; the mixed form's state is FP32, read the same way by
+    both sides, and its neighbour sets differ from the FP64 ones only at the
+    cutoff, where the terms vanish."""
+    c = synth.workload("cyl_8960")
+    sim = sim_of(c, precision=precision)
+    sim.step(3)
+    got = sim.force_breakdown()
+    st = sim.state_arrays()
+    p = oracle.make_params(c.params)
+    _, _, _, mag = oracle.forces(p, st["pos"], st["vel"], st["spin"], c.species, st["rho"],
+                                 st["P"], term_mag=True)
+    sim.close()
+    assert np.all(mag > 0)
+    assert np.all(np.abs(got - mag) <= tol * mag), (got, mag)
 
 
 @pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
