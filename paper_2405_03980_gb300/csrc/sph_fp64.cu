@@ -308,11 +308,14 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   // rotational); walls count as viscous.
   const double mX0 = inv_i ? 0.0 : 1.0, mX1 = inv_i ? 1.0 : 0.0;
   const double mV1 = inv_i ? 0.0 : 1.0;
-  const double cP0 = cP * P.m_s, cP1 = cP * P.m_n;
-  const double cT0 = cT * mX0, cT1 = cT * mX1;
-  const double cBA1 = mV1 != 0.0 ? cB - cA : 0.0;
-  const double cB1 = -cB * mV1;
-  const double cN0 = -cN * mX0, cN1 = -cN * mX1;
+  // The kernel constants cF (in F) and aD (in W) are folded in here, so
+  // that the pair loop forms only the shapes t^3 and t^4 (2q + 1).
+  const double cP0 = cP * P.m_s * P.cF, cP1 = cP * P.m_n * P.cF;
+  const double cT0 = cT * mX0 * P.cF, cT1 = cT * mX1 * P.cF;
+  const double cBA1 = mV1 != 0.0 ? (cB - cA) * P.cF : 0.0;
+  const double cB1 = -cB * mV1 * P.cF;
+  const double cN0 = -cN * mX0 * P.aD, cN1 = -cN * mX1 * P.aD;
+  const bool hproj = hz == 0.0;
   const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
   const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
   const bool per = P.periodic_z != 0;
@@ -352,8 +355,8 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double q = r * P.inv_h;
       const double t1 = 1.0 - 0.5 * q;
       const double t2 = t1 * t1;
-      const double F = P.cF * t2 * t1;
-      const double W = P.aD * t2 * t2 * (2.0 * q + 1.0);
+      const double F = t2 * t1;                    // F / cF
+      const double W = t2 * t2 * (2.0 * q + 1.0);  // W / aD
       const bool vis_j = !inviscid(pj.w);
       // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
       const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
@@ -373,7 +376,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double bR = vis_j ? cB1 * VF : 0.0;
       const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
       const double al = aP + aT + aV;
-      const double alz = aP + hz * aT + aV;
+      const double alz = hproj ? aP + aV : al;
       const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
       double pfx = al * dx + bu * ux;
       double pfy = al * dy + bu * uy;

@@ -361,11 +361,15 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float mX0 = inv_i ? 0.f : 1.f;  // j inviscid
   const float mX1 = inv_i ? 1.f : 0.f;  // j viscous or wall
   const float mV1 = inv_i ? 0.f : 1.f;  // (mV = 0 for an inviscid j)
-  const float cP0 = kP * (m_i * P.m_f[0]), cP1 = kP * (m_i * P.m_f[1]);
-  const float cT0 = kT * mX0, cT1 = kT * mX1;
-  const float cBA1 = mV1 != 0.f ? kB - kA : 0.f;
-  const float cB0 = -kB * 0.f, cB1 = -kB * mV1;
-  const float cN0 = -kN * mX0, cN1 = -kN * mX1;
+  // The kernel constants cF (in F) and aD (in W) are folded in here, so
+  // that the pair loop forms only the shapes t^3 and t^4 (2q + 1).
+  const float cF = P.cF_f, aD = P.aD_f;
+  const float cP0 = kP * (m_i * P.m_f[0]) * cF, cP1 = kP * (m_i * P.m_f[1]) * cF;
+  const float cT0 = kT * mX0 * cF, cT1 = kT * mX1 * cF;
+  const float cBA1 = mV1 != 0.f ? (kB - kA) * cF : 0.f;
+  const float cB0 = -kB * 0.f, cB1 = -kB * mV1 * cF;
+  const float cN0 = -kN * mX0 * aD, cN1 = -kN * mX1 * aD;
+  const bool hproj = hz == 0.f;
   // absolute position of i about the rotation axis (wall torque only)
   const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
@@ -421,8 +425,8 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float q = r * P.inv_h_f;
       const float t1 = 1.f - 0.5f * q;
       const float t2 = t1 * t1;
-      const float F = P.cF_f * (t2 * t1);
-      const float W = P.aD_f * (t2 * t2) * (2.f * q + 1.f);
+      const float F = t2 * t1;                    // F / cF
+      const float W = (t2 * t2) * (2.f * q + 1.f);  // W / aD
       const bool vis_j = oj.w != 0.f;
       // symmetric pair scalars (products taken in an order independent of i, j)
       const float VV = vi.w * vj.w;
@@ -442,7 +446,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float bR = (vis_j ? cB1 : cB0) * VF;
       const float bN = (vis_j ? cN1 : cN0) * (VV * W);
       const float al = aP + aT + aV;
-      const float alz = aP + hz * aT + aV;
+      const float alz = hproj ? aP + aV : al;
       const float bu = lit ? bR : bR + bN;
       float pfx = al * dx + bu * ux;
       float pfy = al * dy + bu * uy;
