@@ -38,12 +38,12 @@ UNIT = "particle-steps/s"
 # FP64 operations per neighbour pair of the pair pass, counted from the kernel
 # source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
 # work of one force launch is this times the number of fluid neighbour pairs.
-FORCE_FLOPS_PER_PAIR = {"fp64": 90, "mixed": 99}   # mixed adds cell offsets and Kahan
+FORCE_FLOPS_PER_PAIR = {"fp64": 88, "mixed": 97}   # mixed adds cell offsets and Kahan
 # Density pass: operations per neighbour pair of the density sum (pair vector,
 # r^2, sqrt, Wendland W, accumulation; the mixed form adds the cell offsets
 # and the Kahan update).  The candidate tests that find the neighbours are
 # not counted as algorithmic work.
-DENSITY_FLOPS_PER_PAIR = {"fp64": 20, "mixed": 31}
+DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
 # Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
 # mixed form adds the cell displacement).  Its work is the candidate tests of
 # the 27-cell stencil of every particle that keeps a list (fluid and inner

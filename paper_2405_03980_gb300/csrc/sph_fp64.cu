@@ -223,6 +223,8 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     const bool per = P.periodic_z != 0;
     MaskWalk mk(nw, n, i, g, smask + threadIdx.x, BLOCK);
     ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
+    const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
+    const double mD_s = P.m_s * P.aD, mD_n = P.m_n * P.aD;
     rho = m_i * P.aD;  // self term W(0)
     uint32_t e[4];
     for (uint32_t m; (m = mk.next(e)) != 0u;) {
@@ -246,11 +248,12 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
           const bool keep = r2 < P.cut2;
           out.push(e[u], keep);  // index and cell-displacement code
           if (keep) {
-            const double q = sqrt(r2) * P.inv_h;
-            const double t1 = 1.0 - 0.5 * q;
+            // m_j W(r) = (m_j aD) t^4 (2q + 1), t = 1 - q/2, q = r / h
+            const double r = sqrt(r2);
+            const double t1 = fma(-half_inv_h, r, 1.0);
             const double t2 = t1 * t1;
-            const double m_j = inviscid(pj[u].w) ? P.m_s : P.m_n;
-            rho += m_j * (P.aD * t2 * t2 * (2.0 * q + 1.0));
+            const double mD = inviscid(pj[u].w) ? mD_s : mD_n;
+            rho += mD * (t2 * t2 * fma(two_inv_h, r, 1.0));
           }
         }
       }
@@ -316,6 +319,8 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double cB1 = -cB * mV1 * P.cF;
   const double cN0 = -cN * mX0 * P.aD, cN1 = -cN * mX1 * P.aD;
   const bool hproj = hz == 0.0;
+  const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
+  const double hwx = 0.5 * wi.x, hwy = 0.5 * wi.y, hwz = 0.5 * wi.z;
   const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
   const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
   const bool per = P.periodic_z != 0;
@@ -352,18 +357,18 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double inv_r = rsqrt(r2);
       const double r = r2 * inv_r;
       const double inv_r2 = inv_r * inv_r;
-      const double q = r * P.inv_h;
-      const double t1 = 1.0 - 0.5 * q;
+      const double t1 = fma(-half_inv_h, r, 1.0);          // 1 - q/2
       const double t2 = t1 * t1;
-      const double F = t2 * t1;                    // F / cF
-      const double W = t2 * t2 * (2.0 * q + 1.0);  // W / aD
+      const double F = t2 * t1;                             // F / cF
+      const double W = t2 * t2 * fma(two_inv_h, r, 1.0);    // W / aD
       const bool vis_j = !inviscid(pj.w);
-      // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j)
+      // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j),
+      // with s = (w_i + w_j) / 2
       const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-      const double sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
-      const double ux = vx + 0.5 * (dy * sz - dz * sy);
-      const double uy = vy + 0.5 * (dz * sx - dx * sz);
-      const double uz = vz + 0.5 * (dx * sy - dy * sx);
+      const double sx = fma(0.5, wj.x, hwx), sy = fma(0.5, wj.y, hwy), sz = fma(0.5, wj.z, hwz);
+      const double ux = fma(dy, sz, fma(-dz, sy, vx));
+      const double uy = fma(dz, sx, fma(-dx, sz, vy));
+      const double uz = fma(dx, sy, fma(-dy, sx, vz));
       const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
       // The five pair terms collected along r_ij and u_ij (and v_ij for the
       // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
@@ -389,23 +394,26 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       fx += pfx;
       fy += pfy;
       fz += pfz;
-      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
-      const double hb = -0.5 * bu;
-      const double qx = hb * (dy * uz - dz * uy);
-      const double qy = hb * (dz * ux - dx * uz);
-      const double qz = hb * (dx * uy - dy * ux);
+      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij); the
+      // factor -1/2 (exact) is applied to the sums
+      const double qx = bu * (dy * uz - dz * uy);
+      const double qy = bu * (dz * ux - dx * uz);
+      const double qz = bu * (dx * uy - dy * ux);
       tx += qx;
       ty += qy;
       tz += qz;
       if (is_wall(pj.w)) {  // torque exerted by the wall on particle i
-        wx += pi.y * pfz - pi.z * pfy + qx;
-        wy += pi.z * pfx - pi.x * pfz + qy;
-        wz += pi.x * pfy - pi.y * pfx + qz;
+        wx += fma(-0.5, qx, pi.y * pfz - pi.z * pfy);
+        wy += fma(-0.5, qy, pi.z * pfx - pi.x * pfz);
+        wz += fma(-0.5, qz, pi.x * pfy - pi.y * pfx);
       }
     }
   }
   const double inv_m = 1.0 / m_i;
   f.acc[i] = dvec4{fx * inv_m, fy * inv_m, fz * inv_m, 0.0};
+  tx *= -0.5;
+  ty *= -0.5;
+  tz *= -0.5;
   f.dspin[i] = dvec4{tx * inv_I, ty * inv_I, tz * inv_I, 0.0};
   f.tw[i] = dvec4{wx, wy, wz, 0.0};
   if (!finite3(fx, fy, fz) || !finite3(tx, ty, tz)) latch(err, ERR_NONFINITE);

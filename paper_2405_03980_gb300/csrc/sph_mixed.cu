@@ -270,6 +270,8 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
     const uint32_t groups = (uint32_t)nw.cap >> 3;
+    const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
+    const float mrD0 = P.mr_f[0] * P.aD_f, mrD1 = P.mr_f[1] * P.aD_f;
     uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
       // every batch but the last holds 8 neighbours: it is list group g
@@ -290,11 +292,12 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
           entry_vec(P, dtab, e[u], oi, o[u], dx, dy2, dz2);
           const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
           // r = r2 / sqrt(r2) from the approximate reciprocal square root
-          const float q = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * P.inv_h_f;
-          const float t1 = 1.f - 0.5f * q;
+          const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+          // (m_j / rho0) W(r) = (m_j aD / rho0) t^4 (2q + 1), t = 1 - q/2
+          const float t1 = fmaf(-half_inv_h, r, 1.f);
           const float t2 = t1 * t1;
-          const float W = P.aD_f * t2 * t2 * (2.f * q + 1.f);
-          acc.add(P.mr_f[o[u].w == 0.f ? 0 : 1] * W);
+          const float Wt = t2 * t2 * fmaf(two_inv_h, r, 1.f);
+          acc.add((o[u].w == 0.f ? mrD0 : mrD1) * Wt);
         }
       }
     }
@@ -370,6 +373,8 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float cB0 = -kB * 0.f, cB1 = -kB * mV1 * cF;
   const float cN0 = -kN * mX0 * aD, cN1 = -kN * mX1 * aD;
   const bool hproj = hz == 0.f;
+  const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
+  const float hwx = 0.5f * wi.x, hwy = 0.5f * wi.y, hwz = 0.5f * wi.z;
   // absolute position of i about the rotation axis (wall torque only)
   const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
@@ -422,19 +427,20 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float inv_r = rsqrtf(r2);
       const float r = r2 * inv_r;
       const float inv_r2 = inv_r * inv_r;
-      const float q = r * P.inv_h_f;
-      const float t1 = 1.f - 0.5f * q;
+      const float t1 = fmaf(-half_inv_h, r, 1.f);         // 1 - q/2
       const float t2 = t1 * t1;
-      const float F = t2 * t1;                    // F / cF
-      const float W = (t2 * t2) * (2.f * q + 1.f);  // W / aD
+      const float F = t2 * t1;                            // F / cF
+      const float W = (t2 * t2) * fmaf(two_inv_h, r, 1.f);  // W / aD
       const bool vis_j = oj.w != 0.f;
       // symmetric pair scalars (products taken in an order independent of i, j)
       const float VV = vi.w * vj.w;
       const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-      const float sx = wi.x + wj.x, sy = wi.y + wj.y, sz = wi.z + wj.z;
-      const float ux = vx + 0.5f * (dy * sz - dz * sy);
-      const float uy = vy + 0.5f * (dz * sx - dx * sz);
-      const float uz = vz + 0.5f * (dx * sy - dy * sx);
+      // half the spin sum, (w_i + w_j) / 2, the same bits from either side
+      const float sx = fmaf(0.5f, wj.x, hwx), sy = fmaf(0.5f, wj.y, hwy),
+                  sz = fmaf(0.5f, wj.z, hwz);
+      const float ux = fmaf(dy, sz, fmaf(-dz, sy, vx));
+      const float uy = fmaf(dz, sx, fmaf(-dx, sz, vy));
+      const float uz = fmaf(dx, sy, fmaf(-dy, sx, vz));
       const float dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij (symmetric)
       // the five terms collected along r_ij, u_ij and (literal F_sn) v_ij:
       // shear -A VV F dv/r^2 r_ij; rotational -B VV F u_ij + B VV F dv/r^2 r_ij
@@ -459,18 +465,18 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       gfx += pfx;
       gfy += pfy;
       gfz += pfz;
-      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij)
-      const float hb = -0.5f * bu;
-      const float qx = hb * (dy * uz - dz * uy);
-      const float qy = hb * (dz * ux - dx * uz);
-      const float qz = hb * (dx * uy - dy * ux);
+      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij); the
+      // factor -1/2 (exact) is applied to the sums
+      const float qx = bu * (dy * uz - dz * uy);
+      const float qy = bu * (dz * ux - dx * uz);
+      const float qz = bu * (dx * uy - dy * ux);
       gtx += qx;
       gty += qy;
       gtz += qz;
       if (oj.w >= 2.f) {
-        wx += pyi * pfz - pzi * pfy + qx;
-        wy += pzi * pfx - pxi * pfz + qy;
-        wz += pxi * pfy - pyi * pfx + qz;
+        wx += fmaf(-0.5f, qx, pyi * pfz - pzi * pfy);
+        wy += fmaf(-0.5f, qy, pzi * pfx - pxi * pfz);
+        wz += fmaf(-0.5f, qz, pxi * pfy - pyi * pfx);
       }
     }
     fx.add(gfx);
@@ -483,7 +489,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   }
   const float inv_m = P.inv_m_f[si], inv_I = P.inv_I_f[si];
   const float ax = fx.value(), ay = fy.value(), az = fz.value();
-  const float bx = tx.value(), by = ty.value(), bz = tz.value();
+  const float bx = -0.5f * tx.value(), by = -0.5f * ty.value(), bz = -0.5f * tz.value();
   f.acc[i] = make_float4(ax * inv_m, ay * inv_m, az * inv_m, 0.f);
   f.dspin[i] = make_float4(bx * inv_I, by * inv_I, bz * inv_I, 0.f);
   f.tw[i] = make_float4(wx, wy, wz, 0.f);
