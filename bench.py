@@ -56,16 +56,16 @@ SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (167.2, {"sph_search.cu": "95a0e3df5866f820",
+    "k_cell_search<true>": (167.0, {"sph_search.cu": "95a0e3df5866f820",
                                     "sph_internal.h": "bff276d2739b8616"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (553.7, {"sph_mixed.cu": "e29fca062b0b9188",
+    "k_density_mixed": (554.1, {"sph_mixed.cu": "5621333ff6ac699e",
                                 "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_mixed": (414.1, {"sph_mixed.cu": "e29fca062b0b9188",
+    "k_forces_mixed": (414.3, {"sph_mixed.cu": "5621333ff6ac699e",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_density_fp64": (641.4, {"sph_fp64.cu": "f331d5406f7cf1cf",
+    "k_density_fp64": (641.4, {"sph_fp64.cu": "965849b256680e96",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_fp64": (511.8, {"sph_fp64.cu": "f331d5406f7cf1cf",
+    "k_forces_fp64": (511.6, {"sph_fp64.cu": "965849b256680e96",
                               "sph_internal.h": "bff276d2739b8616"}),
 }
 
