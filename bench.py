@@ -38,7 +38,7 @@ UNIT = "particle-steps/s"
 # FP64 operations per neighbour pair of the pair pass, counted from the kernel
 # source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
 # work of one force launch is this times the number of fluid neighbour pairs.
-FORCE_FLOPS_PER_PAIR = {"fp64": 88, "mixed": 97}   # mixed adds cell offsets and Kahan
+FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # mixed adds cell offsets and Kahan
 # Density pass: operations per neighbour pair of the density sum (pair vector,
 # r^2, sqrt, Wendland W, accumulation; the mixed form adds the cell offsets
 # and the Kahan update).  The candidate tests that find the neighbours are

@@ -380,8 +380,9 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double aV = vis_j ? VF * inv_r2 * (cBA1 * dv) : 0.0;
       const double bR = vis_j ? cB1 * VF : 0.0;
       const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
-      const double al = aP + aT + aV;
-      const double alz = hproj ? aP + aV : al;
+      const double base = aP + aV;  // the z component drops aT under the projection
+      const double al = base + aT;
+      const double alz = hproj ? base : al;
       const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
       double pfx = al * dx + bu * ux;
       double pfy = al * dy + bu * uy;
@@ -483,7 +484,7 @@ cudaError_t launch_kick_drift_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields
                                    const InstDev* inst, const InstState* ist,
                                    const CellWs& cw, uint32_t* err, int mode,
                                    cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  k_kick_drift_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, ist, cw,
+  k_kick_drift_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, ist, cw,
                                                                        err, mode);
   if (launches) ++*launches;
   return cudaGetLastError();
@@ -492,7 +493,7 @@ cudaError_t launch_kick_drift_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields
 cudaError_t launch_reorder_fp64(int64_t n, const Fp64Buf& src, const Fp64Buf& dst,
                                 const CellWs& cw, const NbrWs& nw, cudaStream_t s,
                                 const LaunchCfg& lc, int* launches) {
-  k_reorder_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, cw, nw);
+  k_reorder_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, cw, nw);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -539,7 +540,7 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
 cudaError_t launch_kick_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                              const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
                              int* launches) {
-  k_kick_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst);
+  k_kick_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -548,7 +549,7 @@ cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                double* pos, double* vel, double* spin, double* rho,
                                double* P, double* acc, double* dspin, cudaStream_t s,
                                const LaunchCfg& lc) {
-  k_unsort_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, pos, vel, spin, rho,
+  k_unsort_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, pos, vel, spin, rho,
                                                                    P, acc, dspin);
   return cudaGetLastError();
 }
@@ -556,7 +557,7 @@ cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
 cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
                              const double* vel, const double* spin, const uint8_t* sp,
                              const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc) {
-  k_load_fp64<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, pos, vel, spin, sp,
+  k_load_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, pos, vel, spin, sp,
                                                                  inst_of);
   return cudaGetLastError();
 }

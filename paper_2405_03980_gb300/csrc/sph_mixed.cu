@@ -451,8 +451,9 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float aV = (VF * inv_r2) * ((vis_j ? cBA1 : 0.f) * dv);
       const float bR = (vis_j ? cB1 : cB0) * VF;
       const float bN = (vis_j ? cN1 : cN0) * (VV * W);
-      const float al = aP + aT + aV;
-      const float alz = hproj ? aP + aV : al;
+      const float base = aP + aV;  // the z component drops aT under the projection
+      const float al = base + aT;
+      const float alz = hproj ? base : al;
       const float bu = lit ? bR : bR + bN;
       float pfx = al * dx + bu * ux;
       float pfy = al * dy + bu * uy;
@@ -574,7 +575,7 @@ cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields&
                                     const InstDev* inst, const InstState* ist, const CellWs& cw,
                                     uint32_t* err, int mode, cudaStream_t s, const LaunchCfg& lc,
                                     int* launches) {
-  k_kick_drift_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, ist, cw,
+  k_kick_drift_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, ist, cw,
                                                                         err, mode);
   if (launches) ++*launches;
   return cudaGetLastError();
@@ -583,7 +584,7 @@ cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields&
 cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
                                  const CellWs& cw, cudaStream_t s, const LaunchCfg& lc,
                                  int* launches) {
-  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, cw);
+  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, cw);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -629,7 +630,7 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
 cudaError_t launch_kick_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                               const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
                               int* launches) {
-  k_kick_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst);
+  k_kick_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -638,7 +639,7 @@ cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, c
                               const double* vel, const double* spin, const uint8_t* sp,
                               const uint32_t* inst_of, uint32_t* err, cudaStream_t s,
                               const LaunchCfg& lc) {
-  k_load_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, inst, pos, vel, spin, sp,
+  k_load_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, inst, pos, vel, spin, sp,
                                                                   inst_of, err);
   return cudaGetLastError();
 }
@@ -647,7 +648,7 @@ cudaError_t launch_unsort_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 const InstDev* inst, double* pos, double* vel, double* spin,
                                 double* rho, double* P, double* acc, double* dspin,
                                 cudaStream_t s, const LaunchCfg& lc) {
-  k_unsort_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, f, inst, pos, vel, spin,
+  k_unsort_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, pos, vel, spin,
                                                                     rho, P, acc, dspin);
   return cudaGetLastError();
 }

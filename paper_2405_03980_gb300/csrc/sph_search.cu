@@ -26,7 +26,7 @@
 namespace sphgb {
 namespace {
 
-constexpr int kSeg = 256;                      // candidates staged at a time
+constexpr int kSeg = 512;                      // candidates staged at a time
 constexpr int kSegChunks = kSeg / 32;
 constexpr int kMaskRow = 36;  // mask words of one chunk: 4 targets per 16-byte store, and
                               // lane t reading word t of chunk k hits bank (4k + t) % 32
