@@ -56,16 +56,16 @@ SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (167.0, {"sph_search.cu": "95a0e3df5866f820",
+    "k_cell_search<true>": (167.1, {"sph_search.cu": "849b66d6f39eb77d",
                                     "sph_internal.h": "bff276d2739b8616"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (554.1, {"sph_mixed.cu": "5621333ff6ac699e",
+    "k_density_mixed": (554.0, {"sph_mixed.cu": "0bb71ba10a69fbde",
                                 "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_mixed": (414.3, {"sph_mixed.cu": "5621333ff6ac699e",
+    "k_forces_mixed": (414.3, {"sph_mixed.cu": "0bb71ba10a69fbde",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_density_fp64": (641.4, {"sph_fp64.cu": "965849b256680e96",
+    "k_density_fp64": (641.0, {"sph_fp64.cu": "b897b4dd574330b3",
                                "sph_internal.h": "bff276d2739b8616"}),
-    "k_forces_fp64": (511.6, {"sph_fp64.cu": "965849b256680e96",
+    "k_forces_fp64": (511.6, {"sph_fp64.cu": "b897b4dd574330b3",
                               "sph_internal.h": "bff276d2739b8616"}),
 }
 
