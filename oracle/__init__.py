@@ -22,6 +22,7 @@ _lib = None
 
 TERM_P, TERM_T, TERM_SH, TERM_ROT, TERM_SN = 1, 2, 4, 8, 16
 HPROJ, SN_LITERAL = 32, 64
+PFILTER, COLLISION = 128, 256
 TERMS_ALL = 31
 DEFAULT_FLAGS = TERMS_ALL | HPROJ
 
@@ -30,7 +31,8 @@ class OrcParams(C.Structure):
     _fields_ = [(k, C.c_double) for k in (
         "dx", "h", "rho0", "alpha_P", "p0", "beta_P", "eta_bar", "eta_r",
         "xi_bar", "C_l", "C_T", "C_omega", "mass_ratio", "inertia_coef",
-        "Omega", "dt", "Hz")] + [("periodic_z", C.c_int), ("flags", C.c_uint)]
+        "Omega", "dt", "col_dist", "col_e", "Hz")] + [("periodic_z", C.c_int),
+                                                      ("flags", C.c_uint)]
 
 
 class OrcDiag(C.Structure):
@@ -93,6 +95,9 @@ def lib():
             L.orc_neighbors.argtypes = [P, C.c_int64, dp, i64p, i64p, C.c_int64]
             L.orc_density.restype = None
             L.orc_density.argtypes = [P, C.c_int64, dp, u8p, i64p, C.c_int64, dp, dp]
+            L.orc_pressure_filter.restype = None
+            L.orc_pressure_filter.argtypes = [P, C.c_int64, dp, u8p, dp, dp, i64p, C.c_int64,
+                                              dp]
             L.orc_forces.restype = None
             L.orc_forces.argtypes = [P, C.c_int64, dp, dp, dp, u8p, dp, dp, i64p,
                                      C.c_int64, dp, dp, dp, dp]
@@ -129,6 +134,8 @@ def make_params(p: dict, flags: int = DEFAULT_FLAGS) -> OrcParams:
               "xi_bar", "C_l", "C_T", "C_omega", "mass_ratio", "inertia_coef",
               "Omega", "dt"):
         setattr(o, k, float(p[k]))
+    o.col_dist = float(p.get("col_dist", 0.0))
+    o.col_e = float(p.get("col_e", 0.0))
     o.Hz = float(p["box_hi"][2] - p["box_lo"][2])
     o.periodic_z = int(p.get("periodic_z", 1))
     o.flags = int(p.get("flags", flags))
@@ -175,6 +182,20 @@ def density(p: OrcParams, pos, species, rows=None):
     nr = n if rows is None else r.shape[0]
     lib().orc_density(C.byref(p), n, _d(pos), _u8(species), _i64(r), nr, _d(rho), _d(P))
     return rho, P
+
+
+def pressure_filter(p: OrcParams, pos, species, rho, P, rows=None):
+    """Filtered pressure of the listed rows (others are returned unchanged)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.uint8)
+    rho, P = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, P))
+    n = pos.shape[0]
+    Pf = P.copy()
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = n if rows is None else r.shape[0]
+    lib().orc_pressure_filter(C.byref(p), n, _d(pos), _u8(species), _d(rho), _d(P), _i64(r),
+                              nr, _d(Pf))
+    return Pf
 
 
 def forces(p: OrcParams, pos, vel, spin, species, rho, P, rows=None, term_mag=False):

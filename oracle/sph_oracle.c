@@ -24,6 +24,17 @@
  *       orbital + spin angular momentum is conserved; I_i dw_i/dt = tau_i.
  *   M9  kick-drift-kick velocity Verlet; rigid rotating walls; periodic z.
  * Walls are viscous ("normal fluid") particles in every species test.
+ *
+ * Two optional steps of Algorithm 1 whose formulas the paper does not print,
+ * in the reading stated in sph_oracle.h:
+ *   pressure filter  Pf_i = sum_j V_j P_j W_ij / sum_j V_j W_ij over i itself
+ *                    and its neighbours (outer walls excluded), applied right
+ *                    after the equation of state;
+ *   collision model  for a pair closer than col_dist whose distance shrinks
+ *                    (r_ij . v_ij < 0), the impulse of a binary collision of
+ *                    two spheres with restitution col_e along e = r_ij / r:
+ *                    dv_i = -(1 + col_e) m_j / (m_i + m_j) (e . v_ij) e,
+ *                    entered in the pair pass as the force m_i dv_i / dt.
  */
 #include "sph_oracle.h"
 
@@ -134,6 +145,34 @@ void orc_density(const orc_params* p, int64_t n, const double* pos,
   }
 }
 
+void orc_pressure_filter(const orc_params* p, int64_t n, const double* pos,
+                         const uint8_t* species, const double* rho, const double* P,
+                         const int64_t* rows, int64_t nrows, double* Pf) {
+  double c2 = cutoff2(p);
+  double m_n = orc_mass(p, 1), m_s = orc_mass(p, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < nrows; ++k) {
+    int64_t i = rows ? rows[k] : k;
+    if (species[i] == 3) {
+      Pf[i] = P[i];
+      continue;
+    }
+    double num = 0.0, den = 0.0;
+    for (int64_t j = 0; j < n; ++j) { /* j = i gives the self term W(0) */
+      if (species[j] == 3) continue;
+      double d[3];
+      orc_pair_delta(p, pos + 3 * i, pos + 3 * j, d);
+      double q2 = norm2(d);
+      if (!(q2 < c2)) continue;
+      double Vj = (species[j] == 0 ? m_s : m_n) / rho[j];
+      double w = Vj * orc_W(p, sqrt(q2));
+      num += w * P[j];
+      den += w;
+    }
+    Pf[i] = num / den;
+  }
+}
+
 static void cross(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
@@ -148,6 +187,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
   double c2 = cutoff2(p);
   double m_n = orc_mass(p, 1), m_s = orc_mass(p, 0);
   double A = 10.0 * (p->eta_bar - 0.6 * p->eta_r); /* M5 */
+  double col2 = p->col_dist * p->col_dist;          /* collision model */
   double B = 4.0 * p->eta_r;                       /* M6 */
   unsigned fl = p->flags;
   double mag[5] = {0, 0, 0, 0, 0};
@@ -165,7 +205,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
     double Vi = mi / rho[i];
     double Pri = P[i] / (rho[i] * rho[i]);
     int inv_i = species[i] == 0;
-    double fsum[5][3];
+    double fsum[6][3]; /* the five terms of M3-M7, then the collision force */
     memset(fsum, 0, sizeof fsum);
     double tau[3] = {0, 0, 0};
     double Tw[3] = {0, 0, 0};
@@ -184,7 +224,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
       int inv_j = species[j] == 0;
       int chiX = inv_i != inv_j;
       int chiV = !inv_i && !inv_j;
-      double f[5][3];
+      double f[6][3];
       memset(f, 0, sizeof f);
       /* M3 pressure */
       if (fl & ORC_TERM_P) {
@@ -231,6 +271,16 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
         f[4][1] = s * w[1];
         f[4][2] = s * w[2];
       }
+      /* collision model: approaching pair closer than col_dist */
+      if ((fl & ORC_COLLISION) && r2 < col2) {
+        double ev = e[0] * vij[0] + e[1] * vij[1] + e[2] * vij[2];
+        if (ev < 0.0) {
+          double s = -(1.0 + p->col_e) * (mi * mj / (mi + mj)) * ev / p->dt;
+          f[5][0] = s * e[0];
+          f[5][1] = s * e[1];
+          f[5][2] = s * e[2];
+        }
+      }
       /* M8 spin torque */
       double fs[3] = {f[3][0], f[3][1], f[3][2]};
       if (!(fl & ORC_SN_LITERAL)) {
@@ -244,12 +294,12 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
       t[1] *= -0.5;
       t[2] *= -0.5;
       for (int a = 0; a < 3; ++a) tau[a] += t[a];
-      for (int q = 0; q < 5; ++q)
+      for (int q = 0; q < 6; ++q)
         for (int a = 0; a < 3; ++a) fsum[q][a] += f[q][a];
       if (species[j] >= 2) {
-        double ft[3] = {f[0][0] + f[1][0] + f[2][0] + f[3][0] + f[4][0],
-                        f[0][1] + f[1][1] + f[2][1] + f[3][1] + f[4][1],
-                        f[0][2] + f[1][2] + f[2][2] + f[3][2] + f[4][2]};
+        double ft[3] = {f[0][0] + f[1][0] + f[2][0] + f[3][0] + f[4][0] + f[5][0],
+                        f[0][1] + f[1][1] + f[2][1] + f[3][1] + f[4][1] + f[5][1],
+                        f[0][2] + f[1][2] + f[2][2] + f[3][2] + f[4][2] + f[5][2]};
         double o[3];
         cross(pos + 3 * i, ft, o);
         for (int a = 0; a < 3; ++a) Tw[a] += o[a] + t[a];
@@ -257,7 +307,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
     }
     double Ii = p->inertia_coef * mi * p->dx * p->dx;
     for (int a = 0; a < 3; ++a) {
-      double ft = fsum[0][a] + fsum[1][a] + fsum[2][a] + fsum[3][a] + fsum[4][a];
+      double ft = fsum[0][a] + fsum[1][a] + fsum[2][a] + fsum[3][a] + fsum[4][a] + fsum[5][a];
       ai[a] = ft / mi;
       bi[a] = tau[a] / Ii;
       if (Ti) Ti[a] = Tw[a];
@@ -308,6 +358,12 @@ static void evaluate(const orc_params* p, int64_t n, const double* pos,
                      double* rho, double* P, double* acc, double* dspin,
                      double* T_wall_sum) {
   orc_density(p, n, pos, species, NULL, n, rho, P);
+  if (p->flags & ORC_PFILTER) {
+    double* Pf = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    orc_pressure_filter(p, n, pos, species, rho, P, NULL, n, Pf);
+    memcpy(P, Pf, sizeof(double) * (size_t)n);
+    free(Pf);
+  }
   double* wT = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   orc_forces(p, n, pos, vel, spin, species, rho, P, NULL, n, acc, dspin, wT, NULL);
   sum_wall_torque(n, species, wT, T_wall_sum);

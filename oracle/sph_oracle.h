@@ -20,6 +20,16 @@
  * interfacial and local-interaction coefficients C_T and C_l follow a reading
  * of Sec. 2.1 (the paper prints their continuum form only); their sign and
  * antisymmetry are pinned, their magnitude is a free parameter.
+ *
+ * The pressure filter and the collision model are named in Algorithm 1 but
+ * their formulas are not printed; they follow a reading (a zeroth-order
+ * kernel average of P; a binary inelastic collision along the line of
+ * centres of approaching pairs closer than col_dist, with restitution col_e,
+ * applied as the acceleration that gives that velocity change over one
+ * step).  The reading is pinned by closed forms and invariants (constant and
+ * linear fields, the spike response on the lattice, the two-body collision
+ * law, momentum and angular-momentum conservation); whether it is the
+ * paper's own form cannot be checked.
  */
 #ifndef SPH_ORACLE_H
 #define SPH_ORACLE_H
@@ -37,6 +47,8 @@ enum {
   ORC_TERM_SN = 16u,     /* local interaction force F_sn                 */
   ORC_HPROJ = 32u,       /* interfacial force acts horizontally only     */
   ORC_SN_LITERAL = 64u,  /* F_sn on plain v_ij (no spin coupling/torque) */
+  ORC_PFILTER = 128u,    /* pressure filter after the equation of state  */
+  ORC_COLLISION = 256u,  /* collision model in the pair pass             */
   ORC_TERMS_ALL = 31u
 };
 
@@ -50,6 +62,9 @@ typedef struct {
   double mass_ratio;               /* m_s / m_n                                */
   double inertia_coef;             /* I_i = inertia_coef m_i dx^2              */
   double Omega, dt;
+  double col_dist;                 /* collision model: pair distance below     */
+  double col_e;                    /*   which approaching pairs collide, and   */
+                                   /*   the restitution coefficient            */
   double Hz;                       /* z period                                 */
   int periodic_z;
   unsigned flags;
@@ -87,9 +102,20 @@ void orc_density(const orc_params* p, int64_t n, const double* pos,
                  const uint8_t* species, const int64_t* rows, int64_t nrows,
                  double* rho, double* P);
 
+/* Pressure filter (Algorithm 1, after the equation of state) for the listed
+ * rows: the kernel-weighted volume average of the pressure,
+ *   Pf_i = sum_j V_j P_j W_ij / sum_j V_j W_ij,  V_j = m_j / rho_j,
+ * over j = i and the neighbours r < 2h of i, outer-wall particles excluded
+ * (their pressure is not computed); outer-wall rows keep their P.  rho and P
+ * are read for every particle. */
+void orc_pressure_filter(const orc_params* p, int64_t n, const double* pos,
+                         const uint8_t* species, const double* rho, const double* P,
+                         const int64_t* rows, int64_t nrows, double* Pf);
+
 /* Pair forces for the listed rows: acc = f/m, dspin = tau/I; wall_T receives
  * the torque (orbital about the z axis + spin) exerted by wall neighbours.
- * term_mag (optional, 5 doubles) accumulates sum_i |f_i^term| per term. */
+ * term_mag (optional, 5 doubles) accumulates sum_i |f_i^term| per term
+ * (the collision force, when on, is not one of the five). */
 void orc_forces(const orc_params* p, int64_t n, const double* pos,
                 const double* vel, const double* spin, const uint8_t* species,
                 const double* rho, const double* P, const int64_t* rows,
@@ -101,7 +127,8 @@ void orc_place_walls(const orc_params* p, int64_t n, const uint8_t* species,
                      const double* wall_ref, double theta, double* pos,
                      double* vel, double* spin);
 
-/* Initial evaluation: walls at theta, density, forces (a_0, alpha_0). */
+/* Initial evaluation: walls at theta, density (+ the pressure filter when
+ * on), forces (a_0, alpha_0). */
 void orc_init(const orc_params* p, int64_t n, double* pos, double* vel,
               double* spin, const uint8_t* species, const double* wall_ref,
               double theta, double* rho, double* P, double* acc, double* dspin,

@@ -27,6 +27,16 @@ MUTATIONS = {
     "wall_rotation_sign": ("double y = s * x0 + c * y0;", "double y = -s * x0 + c * y0;"),
     "wall_torque_without_spin": ("Tw[a] += o[a] + t[a];", "Tw[a] += o[a];"),
     "half_drift": ("pos[3 * i + a] += p->dt * vel[3 * i + a];", "pos[3 * i + a] += 0.5 * p->dt * vel[3 * i + a];"),
+    "filter_without_self": ("if (species[j] == 3) continue;\n      double d[3];",
+                            "if (species[j] == 3 || j == i) continue;\n      double d[3];"),
+    "filter_weight_gradient": ("double w = Vj * orc_W(p, sqrt(q2));", "double w = Vj * orc_F(p, sqrt(q2));"),
+    "filter_includes_outer_walls": ("if (species[j] == 3) continue;\n      double d[3];",
+                                    "if (species[j] == 4) continue;\n      double d[3];"),
+    "filter_row_pressure": ("num += w * P[j];", "num += w * P[i];"),
+    "collision_without_restitution": ("-(1.0 + p->col_e) * (mi * mj", "-(1.0) * (mi * mj"),
+    "collision_full_mass": ("(mi * mj / (mi + mj))", "(mj)"),
+    "collision_on_separating_pairs": ("if (ev < 0.0) {", "if (ev != 0.0) {"),
+    "collision_not_on_walls": ("+ f[4][0] + f[5][0],", "+ f[4][0],"),
     "unit_vector_index": ("double e[3] = {d[0] / r, d[1] / r, d[2] / r};",
                           "double e[3] = {d[0] / r, d[2] / r, d[1] / r};"),
 }

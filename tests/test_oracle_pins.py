@@ -434,3 +434,171 @@ def test_rotating_walls_and_angular_momentum_budget():
     assert d1["mass"] == d0["mass"]
     fl = c.species < 2
     assert np.all(s.pos[fl, 2] >= 0.0) and np.all(s.pos[fl, 2] < c.H)
+
+
+# ------------------------------------------- pressure filter (Algorithm 1)
+# The filter's formula is not printed; the oracle reads it as the zeroth-order
+# kernel average Pf_i = sum_j V_j P_j W_ij / sum_j V_j W_ij (i itself included,
+# outer walls excluded).  These pins fix what that reading implies.
+
+def test_pressure_filter_keeps_constant_and_linear_fields():
+    c = synth.workload("cyl_8960")
+    p = oracle.make_params(c.params)
+    rho, _ = oracle.density(p, c.pos, c.species)
+    keep = c.species != 3
+    # a constant field is a fixed point for any positive weights
+    Pc = np.full(c.n, 0.37)
+    Pf = oracle.pressure_filter(p, c.pos, c.species, rho, Pc)
+    assert np.abs(Pf[keep] - 0.37).max() < 1e-15 * 0.37 * 8
+    # on an unjittered lattice with uniform volumes, the neighbourhood of an
+    # interior particle is point-symmetric, so a linear field is kept exactly
+    q = oracle.make_params(_params(periodic_z=0))
+    pos = _lattice(11)
+    sp = np.ones(len(pos), np.uint8)
+    P = 0.3 * pos[:, 0] - 1.1 * pos[:, 1] + 0.7 * pos[:, 2] + 2.0
+    Pf = oracle.pressure_filter(q, pos, sp, np.ones(len(pos)), P)
+    inner = np.all(np.abs(pos) <= 2.0 + 1e-9, axis=1)
+    assert inner.sum() == 125
+    assert np.abs(Pf[inner] - P[inner]).max() < 1e-13
+    # the boundary rows see a one-sided neighbourhood and move (the field's
+    # slope is not symmetric there): the test above is not vacuous
+    assert np.abs(Pf - P).max() > 1e-2
+
+
+def test_pressure_filter_unit_impulse_response_on_lattice():
+    """P = 1 at one lattice particle, 0 elsewhere, uniform density: with the
+    lattice mass m = rho0 / sum_n W(|n| dx) the weights of every interior row
+    sum to one, so the filtered field is (m / rho0) W(r) around the impulse:
+    (m / rho0) W(0) at the impulse itself and zero beyond 2h."""
+    q = oracle.make_params(_params(periodic_z=0, rho0=2.5))
+    pos = _lattice(13)
+    n = len(pos)
+    sp = np.ones(n, np.uint8)
+    k = int(np.argmin((pos ** 2).sum(1)))
+    P = np.zeros(n)
+    P[k] = 1.0
+    Pf = oracle.pressure_filter(q, pos, sp, np.full(n, 2.5), P)
+    r = np.sqrt((pos ** 2).sum(1))
+    S = oracle.lattice_sum(q)
+    near = r < 2.0 * q.h
+    want = np.array([oracle.W(q, x) for x in r[near]]) / S
+    assert np.abs(Pf[near] - want).max() < 1e-15
+    assert Pf[k] == pytest.approx(oracle.W(q, 0.0) / S, rel=1e-14)
+    assert np.all(Pf[~near] == 0.0)
+
+
+def test_pressure_filter_bounds_and_outer_wall_exclusion():
+    c = synth.workload("cyl_8960")
+    p = oracle.make_params(c.params)
+    rho, _ = oracle.density(p, c.pos, c.species)
+    rng = np.random.default_rng(4)
+    P = rng.normal(size=c.n)
+    P[c.species == 3] = 0.0
+    Pf = oracle.pressure_filter(p, c.pos, c.species, rho, P)
+    off, nbr = oracle.neighbors(p, c.pos)
+    for i in range(0, c.n, 37):
+        if c.species[i] == 3:
+            assert Pf[i] == P[i]
+            continue
+        js = np.append(nbr[off[i]:off[i + 1]], i)
+        js = js[c.species[js] != 3]
+        assert P[js].min() - 1e-14 <= Pf[i] <= P[js].max() + 1e-14
+    # the outer-wall pressures do not enter any row
+    P2 = P.copy()
+    P2[c.species == 3] = 1e3
+    Pf2 = oracle.pressure_filter(p, c.pos, c.species, rho, P2)
+    keep = c.species != 3
+    assert np.array_equal(Pf2[keep], Pf[keep])
+
+
+# -------------------------------------------- collision model (Algorithm 1)
+# Read as the binary inelastic collision of two spheres along the line of
+# centres, for pairs closer than col_dist that approach; the velocity change
+# enters the pair pass as the force m_i dv_i / dt.
+
+def _two_body(mass_ratio=3.0, e=0.3, d=0.7, flip=False, seed=8):
+    rng = np.random.default_rng(seed)
+    prm = _params(periodic_z=0, mass_ratio=mass_ratio, col_dist=0.9, col_e=e, dt=0.01)
+    p = oracle.make_params(prm, flags=oracle.COLLISION)
+    n_hat = rng.normal(size=3)
+    n_hat /= np.linalg.norm(n_hat)
+    pos = np.array([[0.0, 0.0, 0.0], d * n_hat]) + 5.0
+    vel = rng.normal(size=(2, 3))
+    vn = (vel[0] - vel[1]) @ (pos[0] - pos[1])
+    if (vn > 0) != flip:  # make the pair approach (or separate, if flip)
+        vel = vel[::-1].copy()
+    spin = rng.normal(size=(2, 3))
+    sp = np.array([0, 1], np.uint8)
+    rho = np.array([1.3, 0.8])
+    acc, dsp, _ = oracle.forces(p, pos, vel, spin, sp, rho, np.zeros(2))
+    m = np.array([oracle.mass(p, 0), oracle.mass(p, 1)])
+    return p, pos, vel, acc, dsp, m
+
+
+def test_collision_two_body_law():
+    """Textbook binary collision: after dv = a dt the normal relative velocity
+    is -e times the one before, the tangential one is unchanged, momentum is
+    conserved and no spin torque arises."""
+    p, pos, vel, acc, dsp, m = _two_body()
+    assert m[0] == pytest.approx(3.0 * m[1], rel=1e-15)
+    dv = acc * p.dt
+    e_hat = (pos[0] - pos[1]) / np.linalg.norm(pos[0] - pos[1])
+    v0 = vel[0] - vel[1]
+    v1 = (vel[0] + dv[0]) - (vel[1] + dv[1])
+    assert v0 @ e_hat < 0.0
+    assert v1 @ e_hat == pytest.approx(-p.col_e * (v0 @ e_hat), rel=1e-12)
+    t0 = v0 - (v0 @ e_hat) * e_hat
+    t1 = v1 - (v1 @ e_hat) * e_hat
+    assert np.abs(t1 - t0).max() < 1e-13
+    assert np.abs(m[0] * dv[0] + m[1] * dv[1]).max() < 1e-15
+    assert np.all(dsp == 0.0)
+    # kinetic energy does not grow (restitution below one)
+    E0 = 0.5 * (m * (vel ** 2).sum(1)).sum()
+    E1 = 0.5 * (m * ((vel + dv) ** 2).sum(1)).sum()
+    assert E1 < E0
+
+
+def test_collision_only_for_close_approaching_pairs():
+    _, _, _, acc, _, _ = _two_body(flip=True)
+    assert np.all(acc == 0.0)
+    _, _, _, acc, _, _ = _two_body(d=0.95)
+    assert np.all(acc == 0.0)
+    _, _, _, acc, _, _ = _two_body(e=1.0)
+    assert np.abs(acc).max() > 0.0
+
+
+def test_collision_conserves_momentum_and_angular_momentum():
+    pos, vel, spin, sp = _block(5, 5, 5, seed=21)
+    pos = pos - pos.mean(0)
+    prm = _params(periodic_z=0, mass_ratio=2.0, col_dist=1.02, col_e=0.2)
+    p = oracle.make_params(prm, flags=oracle.COLLISION)
+    rho, P = oracle.density(p, pos, sp)
+    acc, dsp, _ = oracle.forces(p, pos, vel, spin, sp, rho, P)
+    m = np.where(sp == 0, oracle.mass(p, 0), oracle.mass(p, 1))[:, None]
+    f = m * acc
+    hit = np.any(acc != 0.0, axis=1)
+    assert hit.sum() > 20
+    scale = np.abs(f).sum()
+    assert np.abs(f.sum(0)).max() < 1e-13 * scale
+    assert np.abs(np.cross(pos, f).sum(0)).max() < 1e-13 * np.abs(np.cross(pos, f)).sum()
+    assert np.all(dsp == 0.0)
+
+
+def test_filter_and_collision_keep_the_wall_budget():
+    """With the pressure filter and the collision model on, fluid-wall
+    collisions act on the walls too: L_z(t) - L_z(0) still equals the torque
+    impulse of the walls."""
+    c = synth.workload("cyl_8960")
+    prm = dict(c.params, col_dist=0.95, col_e=0.2)
+    fl = oracle.DEFAULT_FLAGS | oracle.PFILTER | oracle.COLLISION
+    s = oracle.Sim(prm, c.pos, c.vel, c.spin, c.species, flags=fl)
+    base = oracle.Sim(c.params, c.pos, c.vel, c.spin, c.species)
+    d0 = s.diagnostics()
+    s.step(3)
+    base.step(3)
+    d1 = s.diagnostics()
+    dL = (d1["L_orb"][2] + d1["L_spin"][2]) - (d0["L_orb"][2] + d0["L_spin"][2])
+    assert dL == pytest.approx(d1["J_wall"][2], rel=1e-9, abs=1e-9 * abs(d0["L_orb"][2]))
+    # both optional steps changed the state
+    assert np.abs(s.P - base.P).max() > 1e-6 * np.abs(base.P).max()
+    assert np.abs(s.vel - base.vel).max() > 0.0
