@@ -44,6 +44,13 @@ FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # mixed adds cell offsets and
 # and the Kahan update).  The candidate tests that find the neighbours are
 # not counted as algorithmic work.
 DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
+# Optional steps of Algorithm 1 (--extras): the pressure filter's operations
+# per neighbour pair (pair vector, r^2, sqrt, W shape, two weighted sums), and
+# the one add per pair that the collision model puts in the pair pass (the
+# products of the rare colliding pairs are not counted).
+FILTER_FLOPS_PER_PAIR = {"fp64": 20, "mixed": 27}
+COLLISION_FLOPS_PER_PAIR = 1
+EXTRAS = {"pfilter": 128, "collision": 256}
 # Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
 # mixed form adds the cell displacement).  Its work is the candidate tests of
 # the 27-cell stencil of every particle that keeps a list (fluid and inner
@@ -82,7 +89,8 @@ STREAM_BYTES_PER_PARTICLE = {
 }
 
 
-def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, hbm_gbs):
+def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, hbm_gbs,
+                  extras=()):
     """Lower bound of one step: every stage at its own roof (the streaming
     stages at the measured HBM bandwidth with their algorithmic bytes, the
     search, density and pair passes at the measured FMA rate with their
@@ -94,7 +102,9 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, 
         bound[st] = by / (hbm_gbs * 1e9) * 1e3
     flops = {"cell_search": SEARCH_FLOPS_PER_TEST[form] * tests,
              "density": DENSITY_FLOPS_PER_PAIR[form] * pairs,
-             "forces": FORCE_FLOPS_PER_PAIR[form] * pairs}
+             "forces": force_flops(form, extras) * pairs}
+    if "pfilter" in extras:
+        flops["pressure_filter"] = FILTER_FLOPS_PER_PAIR[form] * pairs
     for st, fl in flops.items():
         pk = peak_alu["mixed"] if st == "cell_search" else peak_alu[form]  # search is FP32
         bound[st] = fl / (pk * 1e12) * 1e3
@@ -105,6 +115,10 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, 
             "note": "sum over stages of algorithmic bytes / measured HBM bandwidth or "
                     "algorithmic flops / measured FMA rate; measured_ms sums the per-stage "
                     "event times"}
+
+
+def force_flops(form, extras=()):
+    return FORCE_FLOPS_PER_PAIR[form] + (COLLISION_FLOPS_PER_PAIR if "collision" in extras else 0)
 
 
 def measured_traffic(kernel, n_particles):
@@ -162,6 +176,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extras", default="",
+                    help="optional steps of Algorithm 1 to switch on: pfilter, collision "
+                         "(comma list; the default step has neither)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="fluid particles in the oracle sample (0 = size for ~15 s)")
     return ap.parse_args()
@@ -407,12 +424,30 @@ def e2e_buffers(insts):
     return pos, vel, spin, sp, out_pos, out_vel, out_spin
 
 
-def load_workload(name):
-    """A named cylinder, or "ensembleK": K uneven cylinders advanced together."""
+def parse_extras(spec):
+    ex = tuple(e.strip() for e in spec.split(",") if e.strip())
+    bad = [e for e in ex if e not in EXTRAS]
+    if bad:
+        raise SystemExit(f"unknown --extras {bad}; choose from {sorted(EXTRAS)}")
+    return ex
+
+
+def load_workload(name, extras=()):
+    """A named cylinder, or "ensembleK": K uneven cylinders advanced together;
+    extras switch on optional steps of Algorithm 1 in every instance."""
+    from paper_2405_03980_gb300 import _binding as B
     from paper_2405_03980_gb300 import synth
     if name.startswith("ensemble"):
-        return synth.ensemble(int(name[len("ensemble"):] or 64))
-    return [synth.workload(name, seed=0)]
+        insts = synth.ensemble(int(name[len("ensemble"):] or 64))
+    else:
+        insts = [synth.workload(name, seed=0)]
+    if extras:
+        fl = B.SPH_FLAGS_DEFAULT
+        for e in extras:
+            fl |= EXTRAS[e]
+        for c in insts:
+            c.params = dict(c.params, flags=fl)
+    return insts
 
 
 def run_ours(args, dist):
@@ -423,7 +458,8 @@ def run_ours(args, dist):
     dev = dist.local
     torch.cuda.set_device(dev)
     B.lib(build_if_missing=True)
-    insts = load_workload(args.workload)
+    extras = parse_extras(args.extras)
+    insts = load_workload(args.workload, extras)
     n_part = sum(c.n for c in insts)
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     prec = {"fp64": B.SPH_FP64, "mixed": B.SPH_MIXED}
@@ -447,14 +483,17 @@ def run_ours(args, dist):
     for f in results:
         pr = results[f]["diag"]["n_pairs"]
         unit = "FP64" if f == "fp64" else "FP32"
-        for stage, kern, fpp, units, what, u in (
-                ("forces", f"k_forces_{f}", FORCE_FLOPS_PER_PAIR[f], pr,
-                 "fluid neighbour pairs", unit),
-                ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], pr,
-                 "fluid neighbour pairs", unit),
-                ("cell_search", f"k_cell_search<{str(f == 'mixed').lower()}>",
-                 SEARCH_FLOPS_PER_TEST[f], tests, "candidate tests (initial positions)",
-                 "FP32")):
+        stages = [("forces", f"k_forces_{f}", force_flops(f, extras), pr,
+                   "fluid neighbour pairs", unit),
+                  ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], pr,
+                   "fluid neighbour pairs", unit),
+                  ("cell_search", f"k_cell_search<{str(f == 'mixed').lower()}>",
+                   SEARCH_FLOPS_PER_TEST[f], tests, "candidate tests (initial positions)",
+                   "FP32")]
+        if "pfilter" in extras:
+            stages.append(("pressure_filter", f"k_pfilter_{f}", FILTER_FLOPS_PER_PAIR[f], pr,
+                           "fluid neighbour pairs", unit))
+        for stage, kern, fpp, units, what, u in stages:
             pk = peaks["mixed"] if u == "FP32" else peaks["fp64"]
             src = f"measured {u} FMA-chain rate of this GPU (sph_fma_peak), of measured"
             t = results[f]["stages"][stage] * 1e-3
@@ -476,7 +515,7 @@ def run_ours(args, dist):
     n_cells = sum(float((np.floor((np.array(c.params["box_hi"]) - np.array(c.params["box_lo"]))
                                   / (2.0 * c.params["h"])) + [2, 2, 0]).prod()) for c in insts)
     steps_roof = {f: step_roofline(results[f]["stages"], f, n_part, n_cells,
-                                   results[f]["diag"]["n_pairs"], tests, peaks, hbm)
+                                   results[f]["diag"]["n_pairs"], tests, peaks, hbm, extras)
                   for f in results}
 
     # end-to-end through the C ABI with host buffers
@@ -503,7 +542,8 @@ def run_ours(args, dist):
         results[f]["sim"].close()
 
     cpu = None
-    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+    # (the oracle sample times the default step, so none with extras)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline and not extras:
         cpu = cpu_baseline(max(insts, key=lambda c: c.n), n_sample=args.cpu_sample)
 
     if dist.rank == 0:
@@ -525,6 +565,7 @@ def run_ours(args, dist):
                        "R": insts[0].R if len(insts) == 1 else None,
                        "H": insts[0].H if len(insts) == 1 else None,
                        "form": best, "parallelism": "replicas",
+                       "extras": list(extras),
                        "l2": "inputs larger than L2 (state of GBs), no flush"},
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,

@@ -78,6 +78,10 @@ enum {
   SPH_TERM_SN = 16u,         /* local interaction force F_sn                  */
   SPH_HPROJ = 32u,           /* interfacial force horizontal only (Sec. 2.1)  */
   SPH_SN_LITERAL = 64u,      /* F_sn on plain v_ij: no spin coupling, no torque */
+  SPH_PFILTER = 128u,        /* pressure filter after the equation of state
+                                (Algorithm 1); off by default                  */
+  SPH_COLLISION = 256u,      /* collision model in the pair pass (Algorithm 1);
+                                off by default                                 */
   SPH_FLAGS_DEFAULT = 63u
 };
 
@@ -105,9 +109,13 @@ typedef struct sph_params {
   double box_hi[3];     /*   with period box_hi[2] - box_lo[2] if periodic_z  */
   int32_t periodic_z;   /* 1: periodic top/bottom (slip, Sec. 3); 0: open     */
   int32_t precision;    /* SPH_FP64 or SPH_MIXED (same for a whole batch)     */
-  uint32_t flags;       /* SPH_TERM_* | SPH_HPROJ | SPH_SN_LITERAL            */
+  uint32_t flags;       /* SPH_TERM_* | SPH_HPROJ | SPH_SN_LITERAL |
+                           SPH_PFILTER | SPH_COLLISION                        */
   int32_t nbr_cap;      /* neighbour slots per particle: 0 (= 160) or a
                            multiple of 8 in 64..1024                          */
+  double col_dist;      /* collision model: pairs closer than this (and less
+                           than 2h) whose distance shrinks collide            */
+  double col_e;         /* collision model: restitution coefficient in [0, 1] */
 } sph_params;
 
 /* FP64 conservation diagnostics of one instance (sums over fluid particles). */
@@ -162,12 +170,25 @@ SPH_API sph_status sph_init_batch(sph_ctx** ctx, int32_t n_inst, const sph_param
 SPH_API sph_status sph_build_cells(sph_ctx* ctx);
 
 /* Density summation and Tait pressure (Algorithm 1, density/pressure lines;
- * Eq. 4), which also records each particle's neighbour list. */
+ * Eq. 4), which also records each particle's neighbour list.  For instances
+ * with SPH_PFILTER, the pressure filter of Algorithm 1 follows: the paper
+ * names it without a formula; the library applies the kernel-weighted
+ * volume average P_i <- sum_j V_j P_j W_ij / sum_j V_j W_ij over i and its
+ * neighbours within 2h (V = m / rho, outer-wall particles excluded), to the
+ * fluid and inner-wall particles; the filtered P is the one the pair pass and
+ * sph_get_state see. */
 SPH_API sph_status sph_density(sph_ctx* ctx);
 
 /* Pair-force pass (Algorithm 1, pressure-gradient, temperature-gradient,
  * viscosity and local-interaction lines; Eqs. 1-2) writing the acceleration
- * and spin angular acceleration of every fluid particle. */
+ * and spin angular acceleration of every fluid particle.  For instances with
+ * SPH_COLLISION it also carries the collision model of Algorithm 1 (named
+ * there without a formula): a neighbour pair closer than col_dist whose
+ * distance shrinks (r_ij . v_ij < 0) receives the velocity change of a binary
+ * collision of two spheres with restitution col_e along e = r_ij / r,
+ * dv_i = -(1 + col_e) m_j / (m_i + m_j) (e . v_ij) e, entered as the force
+ * m_i dv_i / dt (central, so both momenta are kept; wall partners are rigid
+ * and their reaction enters the wall torque). */
 SPH_API sph_status sph_forces(sph_ctx* ctx);
 
 /* Advance nsteps kick-drift-kick steps (Algorithm 1 inner body), each one

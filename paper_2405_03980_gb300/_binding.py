@@ -24,6 +24,7 @@ STATUS = {0: "SPH_OK", -1: "SPH_ERR_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKS
           -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE", -9: "SPH_ERR_NEIGHBORS"}
 SPH_TERM_P, SPH_TERM_T, SPH_TERM_SH, SPH_TERM_ROT, SPH_TERM_SN = 1, 2, 4, 8, 16
 SPH_HPROJ, SPH_SN_LITERAL, SPH_FLAGS_DEFAULT = 32, 64, 63
+SPH_PFILTER, SPH_COLLISION = 128, 256
 SPH_FP64, SPH_MIXED = 0, 1
 
 
@@ -39,7 +40,7 @@ class SphParams(C.Structure):
         "C_l", "C_T", "C_omega", "mass_ratio", "inertia_coef", "Omega", "dt")] + [
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("periodic_z", C.c_int32), ("precision", C.c_int32), ("flags", C.c_uint32),
-        ("nbr_cap", C.c_int32)]
+        ("nbr_cap", C.c_int32), ("col_dist", C.c_double), ("col_e", C.c_double)]
 
 
 class SphDiag(C.Structure):
@@ -157,6 +158,8 @@ def params_from_dict(p: dict, precision: int = SPH_FP64, flags: int = SPH_FLAGS_
     s.precision = int(p.get("precision", precision))
     s.flags = int(p.get("flags", flags))
     s.nbr_cap = int(p.get("nbr_cap", nbr_cap))
+    s.col_dist = float(p.get("col_dist", 0.8 * float(p["dx"])))
+    s.col_e = float(p.get("col_e", 0.2))
     return s
 
 

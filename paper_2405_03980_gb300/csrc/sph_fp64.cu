@@ -266,16 +266,78 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   const double Pres = P.p0 * ipow(rho * P.inv_rho0, P.alphaP) - P.beta_P;
   f.rho[i] = rho;
   f.P[i] = Pres;
-  b.vel[i].w = m_i / rho;
+  const double V = m_i / rho;
+  b.vel[i].w = V;
   b.spin[i].w = Pres / (rho * rho);
+  if (P.flags & SPH_PFILTER) f.vp[i] = sp == 3 ? dvec2{0.0, 0.0} : dvec2{V, Pres};
   if (!isfinite(rho) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------ pressure filter
+
+// Pressure filter of Algorithm 1 (its formula is not printed; read as the
+// zeroth-order kernel average): P_i <- sum_j V_j P_j W_ij / sum_j V_j W_ij
+// over i itself and its neighbour list, for fluid and inner-wall particles of
+// the instances that enable it.  The inputs (V, P) come from the density
+// pass's separate array and the outputs go to f.P and spin.w, so rows never
+// read a value another row writes.  W enters through its shape t^4 (2q + 1)
+// only (the constant aD cancels).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
+               NbrWs nw, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = inst[b.inst[i]];
+  const dvec4 pi = b.pos[i];
+  if (!(P.flags & SPH_PFILTER) || pi.w == 3.0) return;  // outer walls keep P
+  const dvec2 own = f.vp[i];
+  double num = own.x * own.y, den = own.x;  // self term, W(0) / aD = 1
+  const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
+  const int64_t gc = (int64_t)cw.skey[i] / P.slabs;  // grid cell
+  const int cz_i = (int)((gc - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
+  const bool per = P.periodic_z != 0;
+  const uint32_t cnt = nw.count[i];
+  const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
+    const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
+    const uint4 ga = groups[g], gb = groups[g + 1];
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      if (u >= m) break;
+      const uint32_t j = e[u] & kNbrIndexMask;
+      const dvec4 pj = b.pos[j];
+      const dvec2 vj = f.vp[j];
+      const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+      double dz = pi.z - pj.z;
+      if (per) {  // minimum image across the z period
+        const int wz = z_wrap(e[u], cz_i, P.nz);
+        if (wz > 0) dz += P.Hz;
+        else if (wz < 0) dz -= P.Hz;
+      }
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      const double t1 = fma(-half_inv_h, r, 1.0);
+      const double t2 = t1 * t1;
+      const double w = vj.x * (t2 * t2 * fma(two_inv_h, r, 1.0));
+      num += w * vj.y;
+      den += w;
+    }
+  }
+  const double Pf = num / den;
+  const double rho = f.rho[i];
+  f.P[i] = Pf;
+  b.spin[i].w = Pf / (rho * rho);
+  if (!isfinite(Pf)) latch(err, ERR_NONFINITE);
 }
 
 // ------------------------------------------------------------------ pair pass
 
-// kLiteral: some instance uses the literal F_sn (coefficient of v_ij); the
-// default form has none and drops that term at compile time.
-template <int BLOCK, bool kLiteral>
+// kExtra: some instance uses the literal F_sn (coefficient of v_ij) or the
+// collision model; the default form has neither and drops both at compile
+// time.
+template <int BLOCK, bool kExtra>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
               CellWs cw, NbrWs nw, uint32_t* err) {
@@ -303,8 +365,13 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double cB = (fl & SPH_TERM_ROT) ? P.B * vi.w : 0.0;
   const double cN = (fl & SPH_TERM_SN) ? P.C_l * vi.w : 0.0;
   const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
-  const bool literal = kLiteral && (fl & SPH_SN_LITERAL) != 0;
+  const bool literal = kExtra && (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
+  // collision model: col_dist^2 (0 when off) and -(1 + e) mu_ij / dt of the
+  // pair's species, indexed by the species sum so both sides read one value
+  const double col2 = kExtra ? P.col2 : 0.0;
+  const double cC0 = kExtra ? P.cC[inv_i ? 0 : 1] : 0.0;
+  const double cC1 = kExtra ? P.cC[inv_i ? 1 : 2] : 0.0;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
   // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
@@ -380,14 +447,19 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double aV = vis_j ? VF * inv_r2 * (cBA1 * dv) : 0.0;
       const double bR = vis_j ? cB1 * VF : 0.0;
       const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
-      const double base = aP + aV;  // the z component drops aT under the projection
+      // collision of an approaching pair closer than col_dist: the central
+      // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij
+      double aC = 0.0;
+      if (kExtra && r2 < col2 && dv < 0.0) aC = (vis_j ? cC1 : cC0) * dv * inv_r2;
+      // the z component drops aT under the projection
+      const double base = kExtra ? (aP + aV) + aC : aP + aV;
       const double al = base + aT;
       const double alz = hproj ? base : al;
       const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
       double pfx = al * dx + bu * ux;
       double pfy = al * dy + bu * uy;
       double pfz = alz * dz + bu * uz;
-      if (kLiteral && literal) {  // coefficient bN of v_ij
+      if (kExtra && literal) {  // coefficient bN of v_ij
         pfx += bN * vx;
         pfy += bN * vy;
         pfz += bN * vz;
@@ -518,7 +590,7 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                int* launches) {
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
-  if (lc.any_literal) {
+  if (lc.any_extra) {
     if (lc.block_forces == 256)
       k_forces_fp64<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
     else if (lc.block_forces == 64)
@@ -533,6 +605,14 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
     else
       k_forces_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pfilter_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                uint32_t* err, cudaStream_t s, int* launches) {
+  k_pfilter_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -60,7 +60,10 @@ sph_status derive(const sph_params& p, InstDev& d) {
     return SPH_ERR_ARG;
   if (!(p.alpha_P >= 1 && p.alpha_P <= 16 && is_int(p.alpha_P))) return SPH_ERR_ARG;
   if (p.precision != SPH_FP64 && p.precision != SPH_MIXED) return SPH_ERR_ARG;
-  if (p.flags & ~127u) return SPH_ERR_ARG;
+  if (p.flags & ~511u) return SPH_ERR_ARG;
+  if ((p.flags & SPH_COLLISION) &&
+      !(p.col_dist > 0.0 && p.col_dist < 2.0 * p.h && p.col_e >= 0.0 && p.col_e <= 1.0))
+    return SPH_ERR_ARG;
   memset(&d, 0, sizeof d);
   const double h = p.h;
   d.h = h;
@@ -86,6 +89,14 @@ sph_status derive(const sph_params& p, InstDev& d) {
   d.hdt = 0.5 * p.dt;
   d.alphaP = (int32_t)p.alpha_P;
   d.flags = p.flags;
+  if (p.flags & SPH_COLLISION) {  // binary collision with restitution col_e
+    d.col2 = p.col_dist * p.col_dist;
+    const double ms[2] = {d.m_s, d.m_n};
+    for (int k = 0; k < 3; ++k) {
+      const double ma = ms[k > 1 ? 1 : 0], mb = ms[k > 0 ? 1 : 0];
+      d.cC[k] = -(1.0 + p.col_e) * (ma * mb / (ma + mb)) / p.dt;
+    }
+  }
   d.periodic_z = p.periodic_z ? 1 : 0;
   d.slabs = kSlabs;
   const double side = 2.0 * h;
@@ -166,6 +177,8 @@ sph_status derive(const sph_params& p, InstDev& d) {
   d.dt_f = (float)p.dt;
   d.hdt_f = (float)(0.5 * p.dt);
   d.Omega_f = (float)p.Omega;
+  d.col2_f = (float)d.col2;
+  for (int k = 0; k < 3; ++k) d.cC_f[k] = (float)d.cC[k];
   return SPH_OK;
 }
 
@@ -290,6 +303,10 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.nw.ncand = w.take<uint32_t>(n_cells / kSlabs);
   c.nw.cand = w.take<uint32_t>(n_cells / kSlabs * kMaxCand);
   c.nw.cap = cap;
+  if (precision == SPH_FP64)
+    c.f.vp = w.take<dvec2>(n);
+  else
+    c.mf.vp = w.take<float2>(n);
   c.part_tw = w.take<double>(3 * total_chunks);
   c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
   c.diag_out = w.take<double>((int64_t)kDiagFields * n_inst);
@@ -375,10 +392,10 @@ inline void mark(Marks* m, cudaStream_t s) {
   if (m) cudaEventRecord(m->ev[m->k++], s);
 }
 
-constexpr int kStages = 9;
-const char* const kStageNames[kStages] = {"kick_drift_keys", "cell_scan", "scatter_cell_sort",
-                                          "reorder",         "cell_search", "density",
-                                          "forces",          "kick",        "wall_torque"};
+constexpr int kStages = 10;
+const char* const kStageNames[kStages] = {
+    "kick_drift_keys", "cell_scan", "scatter_cell_sort", "reorder", "cell_search",
+    "density",         "pressure_filter", "forces",      "kick",    "wall_torque"};
 
 bool mixed(const sph_ctx* c) { return c->precision == SPH_MIXED; }
 
@@ -423,13 +440,27 @@ sph_status enqueue_density_only(sph_ctx* c, cudaStream_t s, int* launches) {
   return SPH_OK;
 }
 
-// Neighbour search, then density and pressure.
+// Pressure filter of the instances that enable it (nothing if none does).
+sph_status enqueue_pfilter(sph_ctx* c, cudaStream_t s, int* launches) {
+  if (!c->lc.any_filter) return SPH_OK;
+  if (mixed(c))
+    CK(launch_pfilter_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->nw, c->err, s, launches));
+  else
+    CK(launch_pfilter_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s,
+                           launches));
+  return SPH_OK;
+}
+
+// Neighbour search, then density and pressure, then the pressure filter.
 sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
   mark(m, s);
   sph_status st = enqueue_search(c, s, launches);
   if (st != SPH_OK) return st;
   mark(m, s);
   st = enqueue_density_only(c, s, launches);
+  if (st != SPH_OK) return st;
+  mark(m, s);
+  st = enqueue_pfilter(c, s, launches);
   if (st != SPH_OK) return st;
   c->lists_valid = true;
   return SPH_OK;
@@ -551,6 +582,8 @@ sph_status sph_params_default(sph_params* p, double R, double H, double Omega) {
   p->precision = SPH_FP64;
   p->flags = SPH_FLAGS_DEFAULT;
   p->nbr_cap = 160;
+  p->col_dist = 0.8 * dx;
+  p->col_e = 0.2;
   return SPH_OK;
 }
 
@@ -625,10 +658,12 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->lc.block_density = 128;
   c->lc.block_forces = 128;
   c->lc.search_warps = 4;
-  c->lc.any_literal = false;
+  c->lc.any_extra = false;
+  c->lc.any_filter = false;
   for (const InstDev& d : pl.inst) {
     c->max_cells = std::max(c->max_cells, (int64_t)d.nx * d.ny * d.nz);
-    if (d.flags & SPH_SN_LITERAL) c->lc.any_literal = true;
+    if (d.flags & (SPH_SN_LITERAL | SPH_COLLISION)) c->lc.any_extra = true;
+    if (d.flags & SPH_PFILTER) c->lc.any_filter = true;
   }
   {
     static std::once_flag once;

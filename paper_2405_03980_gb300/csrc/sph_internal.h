@@ -43,6 +43,10 @@ struct InstDev {
   double Hz, half_Hz;             // z period
   double lo[3], inv_cell[3];      // grid origin (ghost cells included), 1 / side
   double cell[3];                 // cell side per axis (>= 2h)
+  double col2;                    // collision model: col_dist^2, 0 when it is off
+  double cC[3];                   // -(1 + col_e) m_a m_b / ((m_a + m_b) dt) for the
+                                  // species pairs a + b = 0 (inviscid, inviscid),
+                                  // 1 (inviscid, other), 2 (other, other)
   float cut2f_margin;             // FP32 prefilter bound (>= every FP64 neighbour)
   float Hzf, half_Hzf;
   int32_t nx, ny, nz;             // cells per axis (ghost ring except periodic z)
@@ -67,6 +71,7 @@ struct InstDev {
   float binom[17];                // binomial coefficients C(alpha_P, k)
   float rho0_f, A_f, B_f, C_l_f, C_T_f;
   float dt_f, hdt_f, Omega_f;
+  float col2_f, cC_f[3];
 };
 
 // Mutable per-instance scalars that live on the device.
@@ -97,6 +102,8 @@ struct Fp64Fields {
   double* rho;
   double* P;
   dvec4* tw;          // torque of wall neighbours on each fluid particle
+  dvec2* vp;          // pressure filter input (V, V P) of the density pass;
+                      // (0, 0) for outer walls
 };
 
 // One copy of the sorted mixed-precision state: an integer cell plus an FP32
@@ -119,6 +126,7 @@ struct MixFields {
   float4* tw;           // torque of wall neighbours on each fluid particle
   float* delta;         // rho / rho0 - 1
   float* P;
+  float2* vp;           // pressure filter input (V, V P); (0, 0) for outer walls
 };
 
 constexpr uint32_t kCellBitsX = 11, kCellBitsY = 11, kCellBitsZ = 10;

@@ -13,7 +13,9 @@ struct LaunchCfg {
   int block_density;     // threads per block of the density pass (32, 64, 128)
   int block_forces;      // threads per block of the pair pass
   int search_warps;      // warps (cells) per block of the neighbour search
-  bool any_literal;      // some instance uses the literal F_sn (SPH_SN_LITERAL)
+  bool any_extra;        // some instance uses the literal F_sn (SPH_SN_LITERAL) or
+                         // the collision model (SPH_COLLISION)
+  bool any_filter;       // some instance uses the pressure filter (SPH_PFILTER)
 };
 
 // ---- cell build (sph_cells.cu) --------------------------------------------
@@ -52,6 +54,10 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches);
+// Pressure filter (instances with SPH_PFILTER) over the density pass's lists.
+cudaError_t launch_pfilter_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
+                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
+                                uint32_t* err, cudaStream_t s, int* launches);
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                uint32_t* err,
@@ -81,6 +87,9 @@ cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                  uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                  int* launches);
+cudaError_t launch_pfilter_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                 cudaStream_t s, int* launches);
 cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches);

@@ -315,16 +315,86 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   const float rho = P.rho0_f * (1.f + delta);
   f.delta[i] = delta;
   f.P[i] = Pres;
-  b.vel[i].w = P.m_f[si] / rho;
+  const float V = P.m_f[si] / rho;
+  b.vel[i].w = V;
   b.spin[i].w = Pres / (rho * rho);
+  if (P.flags & SPH_PFILTER) f.vp[i] = sp == 3 ? make_float2(0.f, 0.f) : make_float2(V, Pres);
   if (!isfinite(delta) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------ pressure filter
+
+// Pressure filter of Algorithm 1 (its formula is not printed; read as the
+// zeroth-order kernel average): P_i <- sum_j V_j P_j W_ij / sum_j V_j W_ij
+// over i itself and its neighbour list, for fluid and inner-wall particles of
+// the instances that enable it.  The inputs (V, P) come from the density
+// pass's separate array and the outputs go to f.P and spin.w, so rows never
+// read a value another row writes.  W enters through its shape t^4 (2q + 1)
+// only (the constant aD cancels); the sums are compensated across groups of
+// 8 neighbours like the pair pass.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
+                uint32_t* err) {
+  __shared__ float4 dtab[64];
+  fill_disp_table(dtab);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = inst[b.inst[i]];
+  const float4 oi = b.off[i];
+  if (!(P.flags & SPH_PFILTER) || oi.w == 3.f) return;  // outer walls keep P
+  const float2 own = f.vp[i];
+  Kahan num{own.x * own.y, 0.f}, den{own.x, 0.f};  // self term, W(0) / aD = 1
+  const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
+  const uint32_t cnt = nw.count[i];
+  const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
+    const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
+    const uint4 ga = groups[g], gb = groups[g + 1];
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+    float4 oj[8];
+    float2 vj[8];
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      if (u < m) {
+        const uint32_t j = e[u] & kNbrIndexMask;
+        oj[u] = b.off[j];
+        vj[u] = f.vp[j];
+      }
+    }
+    float gn = 0.f, gd = 0.f;
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      if (u < m) {
+        float dx, dy, dz;
+        entry_vec(P, dtab, e[u], oi, oj[u], dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+        const float t1 = fmaf(-half_inv_h, r, 1.f);
+        const float t2 = t1 * t1;
+        const float w = vj[u].x * (t2 * t2 * fmaf(two_inv_h, r, 1.f));
+        gn += w * vj[u].y;
+        gd += w;
+      }
+    }
+    num.add(gn);
+    den.add(gd);
+  }
+  const float Pf = num.value() / den.value();
+  const float rho = P.rho0_f * (1.f + f.delta[i]);
+  f.P[i] = Pf;
+  b.spin[i].w = Pf / (rho * rho);
+  if (!isfinite(Pf)) latch(err, ERR_NONFINITE);
 }
 
 // ------------------------------------------------------------------ pair pass
 
-// kLiteral: some instance uses the literal F_sn (coefficient of v_ij); the
-// default form has none and drops that term at compile time.
-template <int BLOCK, bool kLiteral>
+// kExtra: some instance uses the literal F_sn (coefficient of v_ij) or the
+// collision model; the default form has neither and drops both at compile
+// time.
+template <int BLOCK, bool kExtra>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                uint32_t* err) {
@@ -355,7 +425,11 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float kB = (fl & SPH_TERM_ROT) ? P.B_f : 0.f;
   const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
   const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
-  const bool lit = kLiteral && (fl & SPH_SN_LITERAL) != 0;
+  const bool lit = kExtra && (fl & SPH_SN_LITERAL) != 0;
+  // collision model: col_dist^2 (0 when off) and -(1 + e) mu_ij / dt of the
+  // pair's species, indexed by the species sum so both sides read one value
+  const float col2 = kExtra ? P.col2_f : 0.f;
+  const float cC0 = kExtra ? P.cC_f[si] : 0.f, cC1 = kExtra ? P.cC_f[si + 1] : 0.f;
   const bool inv_i = sp_i == 0;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
@@ -451,14 +525,19 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float aV = (VF * inv_r2) * ((vis_j ? cBA1 : 0.f) * dv);
       const float bR = (vis_j ? cB1 : cB0) * VF;
       const float bN = (vis_j ? cN1 : cN0) * (VV * W);
-      const float base = aP + aV;  // the z component drops aT under the projection
+      // collision of an approaching pair closer than col_dist: the central
+      // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij
+      float aC = 0.f;
+      if (kExtra && r2 < col2 && dv < 0.f) aC = (vis_j ? cC1 : cC0) * (dv * inv_r2);
+      // the z component drops aT under the projection
+      const float base = kExtra ? (aP + aV) + aC : aP + aV;
       const float al = base + aT;
       const float alz = hproj ? base : al;
       const float bu = lit ? bR : bR + bN;
       float pfx = al * dx + bu * ux;
       float pfy = al * dy + bu * uy;
       float pfz = alz * dz + bu * uz;
-      if (kLiteral && lit) {
+      if (kExtra && lit) {
         pfx += bN * vx;
         pfy += bN * vy;
         pfz += bN * vz;
@@ -608,7 +687,7 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches) {
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
-  if (lc.any_literal) {
+  if (lc.any_extra) {
     if (lc.block_forces == 256)
       k_forces_mixed<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
     else if (lc.block_forces == 64)
@@ -623,6 +702,14 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
     else
       k_forces_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pfilter_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                 cudaStream_t s, int* launches) {
+  k_pfilter_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

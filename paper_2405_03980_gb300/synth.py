@@ -63,7 +63,9 @@ def workload_params(R: float, H: float, Omega: float, dx: float = 1.0,
     c_s = 10 Omega R, p0 = beta_P = rho0 c_s^2 / gamma (so P(rho0) = 0),
     eta_bar = eta_r = rho0 Omega R^2 / Re, dt = 0.25 h / c_s,
     C_T = 0.01 p0, C_l = 1e-3 rho0 Omega, C_omega = 0.016 (recorded only),
-    unit species mass ratio and spin inertia I = 0.1 m dx^2.
+    unit species mass ratio and spin inertia I = 0.1 m dx^2; for the optional
+    collision model (off unless its flag is set) a collision distance of
+    0.8 dx and a restitution coefficient of 0.2.
     These are workload choices (the paper prints no dimensionless values).
     """
     h = h_over_dx * dx
@@ -76,7 +78,7 @@ def workload_params(R: float, H: float, Omega: float, dx: float = 1.0,
         dx=dx, h=h, rho0=rho0, alpha_P=float(gamma), p0=p0, beta_P=p0,
         eta_bar=eta, eta_r=eta, xi_bar=0.0, C_l=1e-3 * rho0 * Omega,
         C_T=0.01 * p0, C_omega=0.016, mass_ratio=1.0, inertia_coef=0.1,
-        Omega=Omega, dt=dt_factor * h / cs,
+        Omega=Omega, dt=dt_factor * h / cs, col_dist=0.8 * dx, col_e=0.2,
         box_lo=(-ext, -ext, 0.0), box_hi=(ext, ext, float(H)), periodic_z=1,
     )
 

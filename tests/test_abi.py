@@ -43,7 +43,8 @@ def test_params_default_matches_workload_recipe(lib):
     p = B.sph_params_default(10.0, 20.0, 0.1)
     w = synth.workload_params(10.0, 20, 0.1)
     for k in ("dx", "h", "rho0", "alpha_P", "p0", "beta_P", "eta_bar", "eta_r", "C_l",
-              "C_T", "C_omega", "mass_ratio", "inertia_coef", "Omega", "dt"):
+              "C_T", "C_omega", "mass_ratio", "inertia_coef", "Omega", "dt", "col_dist",
+              "col_e"):
         assert getattr(p, k) == pytest.approx(w[k], rel=1e-15), k
     assert list(p.box_lo) == pytest.approx(list(w["box_lo"]))
     assert list(p.box_hi) == pytest.approx(list(w["box_hi"]))
@@ -66,6 +67,17 @@ def test_buffer_sizes_scale_and_validate(lib):
     # a periodic z period shorter than three cells of side 2h is rejected
     bad = B.params_from_dict(dict(c.params, box_hi=(c.params["box_hi"][0], c.params["box_hi"][1], 6.0)))
     assert B.sph_state_bytes(bad, [c.n]) == 0
+    # unknown flag bits, and a collision model outside (0, 2h) x [0, 1]
+    bad = B.params_from_dict(c.params, flags=512)
+    assert B.sph_state_bytes(bad, [c.n]) == 0
+    col = B.SPH_FLAGS_DEFAULT | B.SPH_COLLISION | B.SPH_PFILTER
+    assert B.sph_state_bytes(B.params_from_dict(c.params, flags=col), [c.n]) > 0
+    for kw in (dict(col_dist=2.0 * c.params["h"]), dict(col_dist=0.0), dict(col_e=1.5),
+               dict(col_e=-0.1)):
+        bad = B.params_from_dict(dict(c.params, **kw), flags=col)
+        assert B.sph_state_bytes(bad, [c.n]) == 0, kw
+    # (the collision parameters are not checked while the model is off)
+    assert B.sph_state_bytes(B.params_from_dict(dict(c.params, col_e=3.0)), [c.n]) > 0
     # mixed precision within one batch is rejected
     q = B.params_from_dict(c.params, precision=B.SPH_MIXED)
     assert B.sph_state_bytes([p, q], [c.n, c.n]) == 0
@@ -80,3 +92,21 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert st == -1 and not ctx.value
     assert lib.sph_step(None, 1) == -1
     assert lib.sph_destroy(None) == 0
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of sph_params has the C layout of include/sph.h."""
+    prog = tmp_path / "layout.c"
+    fields = [f for f, _ in B.SphParams._fields_]
+    body = "\n".join(f'  printf("%zu\\n", offsetof(sph_params, {f}));' for f in fields)
+    prog.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"sph.h\"\n"
+                    "int main(void) {\n" + body +
+                    '\n  printf("%zu\\n", sizeof(sph_params));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(prog), "-o",
+                    str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [getattr(B.SphParams, f).offset for f in fields] + [C.sizeof(B.SphParams)]
+    assert out == want
