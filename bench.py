@@ -44,11 +44,16 @@ FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # mixed adds cell offsets and
 # and the Kahan update).  The candidate tests that find the neighbours are
 # not counted as algorithmic work.
 DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
-# Optional steps of Algorithm 1 (--extras): the pressure filter's operations
-# per neighbour pair (pair vector, r^2, sqrt, W shape, two weighted sums), and
-# the one add per pair that the collision model puts in the pair pass (the
-# products of the rare colliding pairs are not counted).
-FILTER_FLOPS_PER_PAIR = {"fp64": 20, "mixed": 27}
+# Optional steps of Algorithm 1 (--extras).  The pressure filter streams each
+# fluid/inner-wall row's neighbour list and the kernel shapes the density
+# pass stored beside it (4 B + 4 B mixed, 4 B + 8 B FP64 per neighbour) and
+# gathers (V, P) from chip-resident records: an HBM-bound pass whose
+# algorithmic bytes are those streams plus, per particle, its count, its own
+# (V, P) and the P and P/rho^2 it writes.  The collision model puts one add
+# per pair in the pair pass (the products of the rare colliding pairs are
+# not counted).
+FILTER_BYTES_PER_PAIR = {"fp64": 12, "mixed": 8}
+FILTER_BYTES_PER_PARTICLE = {"fp64": 4 + 16 + 8 + 8, "mixed": 4 + 8 + 4 + 4}
 COLLISION_FLOPS_PER_PAIR = 1
 EXTRAS = {"pfilter": 128, "collision": 256}
 # Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
@@ -104,7 +109,8 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, 
              "density": DENSITY_FLOPS_PER_PAIR[form] * pairs,
              "forces": force_flops(form, extras) * pairs}
     if "pfilter" in extras:
-        flops["pressure_filter"] = FILTER_FLOPS_PER_PAIR[form] * pairs
+        by = filter_bytes(form, pairs, n_particles)
+        bound["pressure_filter"] = by / (hbm_gbs * 1e9) * 1e3
     for st, fl in flops.items():
         pk = peak_alu["mixed"] if st == "cell_search" else peak_alu[form]  # search is FP32
         bound[st] = fl / (pk * 1e12) * 1e3
@@ -115,6 +121,18 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, 
             "note": "sum over stages of algorithmic bytes / measured HBM bandwidth or "
                     "algorithmic flops / measured FMA rate; measured_ms sums the per-stage "
                     "event times"}
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s)."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6695.5
+
+
+def filter_bytes(form, pairs, n_particles):
+    return FILTER_BYTES_PER_PAIR[form] * pairs + FILTER_BYTES_PER_PARTICLE[form] * n_particles
 
 
 def force_flops(form, extras=()):
@@ -491,8 +509,16 @@ def run_ours(args, dist):
                    SEARCH_FLOPS_PER_TEST[f], tests, "candidate tests (initial positions)",
                    "FP32")]
         if "pfilter" in extras:
-            stages.append(("pressure_filter", f"k_pfilter_{f}", FILTER_FLOPS_PER_PAIR[f], pr,
-                           "fluid neighbour pairs", unit))
+            t = results[f]["stages"]["pressure_filter"]
+            by = filter_bytes(f, pr, n_part)
+            roofs.setdefault(f, {})["pressure_filter"] = {
+                "kernel": f"k_pfilter_{f}", "bound": "hbm", "achieved": by / (t * 1e-3) / 1e9,
+                "peak": hbm_peak(), "unit": "GB/s", "frac": by / (t * 1e-3) / 1e9 / hbm_peak(),
+                "traffic": measured_traffic(f"k_pfilter_{f}", n_part),
+                "traffic_unit": "bytes per launch", "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured",
+                "work": f"{FILTER_BYTES_PER_PAIR[f]} B x {pr} fluid neighbour pairs + "
+                        f"{FILTER_BYTES_PER_PARTICLE[f]} B x {n_part} particles per launch",
+                "launch_ms": t}
         for stage, kern, fpp, units, what, u in stages:
             pk = peaks["mixed"] if u == "FP32" else peaks["fp64"]
             src = f"measured {u} FMA-chain rate of this GPU (sph_fma_peak), of measured"
@@ -507,11 +533,7 @@ def run_ours(args, dist):
                 "launch_ms": results[f]["stages"][stage]}
     dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
     roof = roofs[best][dom_stage]
-    hbm = 6695.5
-    try:
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except (OSError, KeyError, ValueError):
-        pass
+    hbm = hbm_peak()
     n_cells = sum(float((np.floor((np.array(c.params["box_hi"]) - np.array(c.params["box_lo"]))
                                   / (2.0 * c.params["h"])) + [2, 2, 0]).prod()) for c in insts)
     steps_roof = {f: step_roofline(results[f]["stages"], f, n_part, n_cells,

@@ -201,7 +201,9 @@ __device__ __forceinline__ double ipow(double x, int e) {
 // candidate order, as i's neighbour list for the pair pass.  The walk takes
 // 4 candidates at a time: their table entries, then their position records,
 // are loaded together before they are tested.
-template <int BLOCK>
+// kFilter: some instance uses the pressure filter; the kernel shape of every
+// list entry is then stored beside the list (nw.wsh_d) for the filter.
+template <int BLOCK, bool kFilter>
 __global__ void __launch_bounds__(BLOCK)
 k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
                NbrWs nw, uint32_t* err) {
@@ -253,7 +255,12 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
             const double t1 = fma(-half_inv_h, r, 1.0);
             const double t2 = t1 * t1;
             const double mD = inviscid(pj[u].w) ? mD_s : mD_n;
-            rho += mD * (t2 * t2 * fma(two_inv_h, r, 1.0));
+            const double Wt = t2 * t2 * fma(two_inv_h, r, 1.0);
+            rho += mD * Wt;
+            if (kFilter) {  // the shape of this list entry, in the list's layout
+              const uint32_t t = out.total() - 1u;
+              if (t < (uint32_t)nw.cap) nw.wsh_d[nbr_slot(n, i, t)] = Wt;
+            }
           }
         }
       }
@@ -281,46 +288,36 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 // the instances that enable it.  The inputs (V, P) come from the density
 // pass's separate array and the outputs go to f.P and spin.w, so rows never
 // read a value another row writes.  W enters through its shape t^4 (2q + 1)
-// only (the constant aD cancels).
+// (the constant aD cancels), which the density pass stored for every list
+// entry: the pass streams the list and the shapes and gathers (V, P) only,
+// leaving three FP64 operations per neighbour.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
-               NbrWs nw, uint32_t* err) {
+k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, NbrWs nw,
+               uint32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
-  const dvec4 pi = b.pos[i];
-  if (!(P.flags & SPH_PFILTER) || pi.w == 3.0) return;  // outer walls keep P
+  if (!(P.flags & SPH_PFILTER) || b.pos[i].w == 3.0) return;  // outer walls keep P
   const dvec2 own = f.vp[i];
   double num = own.x * own.y, den = own.x;  // self term, W(0) / aD = 1
-  const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
-  const int64_t gc = (int64_t)cw.skey[i] / P.slabs;  // grid cell
-  const int cz_i = (int)((gc - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
-  const bool per = P.periodic_z != 0;
   const uint32_t cnt = nw.count[i];
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  const dvec2* __restrict__ shapes = reinterpret_cast<const dvec2*>(nw.wsh_d);
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
-    const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
-    const uint4 ga = groups[g], gb = groups[g + 1];
+    const int64_t g = (int64_t)(t0 >> 3) * n + i;
+    const uint4 ga = groups[2 * g], gb = groups[2 * g + 1];
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
     const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+    dvec2 w2[4];
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q)
+      if (2 * q < m) w2[q] = shapes[4 * g + q];
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
       if (u >= m) break;
-      const uint32_t j = e[u] & kNbrIndexMask;
-      const dvec4 pj = b.pos[j];
-      const dvec2 vj = f.vp[j];
-      const double dx = pi.x - pj.x, dy = pi.y - pj.y;
-      double dz = pi.z - pj.z;
-      if (per) {  // minimum image across the z period
-        const int wz = z_wrap(e[u], cz_i, P.nz);
-        if (wz > 0) dz += P.Hz;
-        else if (wz < 0) dz -= P.Hz;
-      }
-      const double r = sqrt(dx * dx + dy * dy + dz * dz);
-      const double t1 = fma(-half_inv_h, r, 1.0);
-      const double t2 = t1 * t1;
-      const double w = vj.x * (t2 * t2 * fma(two_inv_h, r, 1.0));
+      const dvec2 vj = f.vp[e[u] & kNbrIndexMask];
+      const double w = vj.x * ((u & 1) ? w2[u >> 1].y : w2[u >> 1].x);
       num += w * vj.y;
       den += w;
     }
@@ -338,7 +335,7 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 // collision model; the default form has neither and drops both at compile
 // time.
 template <int BLOCK, bool kExtra>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, kExtra ? 512 / BLOCK : 0)
 k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
               CellWs cw, NbrWs nw, uint32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -367,11 +364,12 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
   const bool literal = kExtra && (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
-  // collision model: col_dist^2 (0 when off) and -(1 + e) mu_ij / dt of the
-  // pair's species, indexed by the species sum so both sides read one value
-  const double col2 = kExtra ? P.col2 : 0.0;
-  const double cC0 = kExtra ? P.cC[inv_i ? 0 : 1] : 0.0;
-  const double cC1 = kExtra ? P.cC[inv_i ? 1 : 2] : 0.0;
+  // collision model: the bits of col_dist^2 (0 when off; r^2 > 0 orders like
+  // its bits); its coefficient -(1 + e) mu_ij / dt is read, for the rare
+  // colliding pair only, from the table indexed by the species sum, so both
+  // sides of a pair read one value
+  const long long col2b = kExtra ? __double_as_longlong(P.col2) : 0ll;
+  const int si = inv_i ? 0 : 1;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
   // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
@@ -447,12 +445,12 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double aV = vis_j ? VF * inv_r2 * (cBA1 * dv) : 0.0;
       const double bR = vis_j ? cB1 * VF : 0.0;
       const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
+      double base = aP + aV;  // the z component drops aT under the projection
       // collision of an approaching pair closer than col_dist: the central
-      // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij
-      double aC = 0.0;
-      if (kExtra && r2 < col2 && dv < 0.0) aC = (vis_j ? cC1 : cC0) * dv * inv_r2;
-      // the z component drops aT under the projection
-      const double base = kExtra ? (aP + aV) + aC : aP + aV;
+      // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij;
+      // both tests on the bits (dv < 0: its sign bit; -0 adds nothing)
+      if (kExtra && r2b < col2b && __double2hiint(dv) < 0)
+        base += P.cC[si + (vis_j ? 1 : 0)] * dv * inv_r2;
       const double al = base + aT;
       const double alz = hproj ? base : al;
       const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
@@ -574,12 +572,23 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                 int* launches) {
-  if (lc.block_density == 32)
-    k_density_fp64<32><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(n, b, f, inst, cw, nw, err);
-  else if (lc.block_density == 64)
-    k_density_fp64<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
-  else
-    k_density_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  const unsigned g32 = (unsigned)((n + 31) / 32), g64 = (unsigned)((n + 63) / 64),
+                 g128 = (unsigned)((n + 127) / 128);
+  if (lc.any_filter) {
+    if (lc.block_density == 32)
+      k_density_fp64<32, true><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else if (lc.block_density == 64)
+      k_density_fp64<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else
+      k_density_fp64<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  } else {
+    if (lc.block_density == 32)
+      k_density_fp64<32, false><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else if (lc.block_density == 64)
+      k_density_fp64<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else
+      k_density_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -610,9 +619,9 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
 }
 
 cudaError_t launch_pfilter_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
-                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
-                                uint32_t* err, cudaStream_t s, int* launches) {
-  k_pfilter_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                cudaStream_t s, int* launches) {
+  k_pfilter_fp64<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, nw, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

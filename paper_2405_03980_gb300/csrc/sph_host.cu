@@ -248,7 +248,7 @@ int64_t backup_bytes(int32_t precision, int64_t n, int32_t n_inst) {
 }
 
 void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
-           int64_t total_chunks, int32_t cap, int32_t precision, Carved& c) {
+           int64_t total_chunks, int32_t cap, int32_t precision, bool filter, Carved& c) {
   memset(&c, 0, sizeof c);
   Carver s(state);
   c.inst = s.take<InstDev>(n_inst);
@@ -307,6 +307,12 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
     c.f.vp = w.take<dvec2>(n);
   else
     c.mf.vp = w.take<float2>(n);
+  if (filter) {  // kernel shapes of the list entries, for the pressure filter
+    if (precision == SPH_FP64)
+      c.nw.wsh_d = w.take<double>((int64_t)cap * n);
+    else
+      c.nw.wsh_f = w.take<float>((int64_t)cap * n);
+  }
   c.part_tw = w.take<double>(3 * total_chunks);
   c.part_diag = w.take<double>((int64_t)kDiagFields * total_chunks);
   c.diag_out = w.take<double>((int64_t)kDiagFields * n_inst);
@@ -323,6 +329,7 @@ struct Plan {
   int64_t n = 0, n_cells = 0, total_chunks = 0;
   int32_t cap = 160;
   int32_t precision = SPH_FP64;
+  bool any_filter = false;       // some instance uses the pressure filter
 };
 
 sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts, Plan& pl) {
@@ -338,6 +345,7 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
     if (counts[k] < 1) return SPH_ERR_ARG;
     sph_status st = derive(params[k], pl.inst[k]);
     if (st != SPH_OK) return st;
+    if (params[k].flags & SPH_PFILTER) pl.any_filter = true;
     InstDev& d = pl.inst[k];
     d.cell_base = cb;
     d.p_begin = pb;
@@ -446,8 +454,7 @@ sph_status enqueue_pfilter(sph_ctx* c, cudaStream_t s, int* launches) {
   if (mixed(c))
     CK(launch_pfilter_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->nw, c->err, s, launches));
   else
-    CK(launch_pfilter_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s,
-                           launches));
+    CK(launch_pfilter_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->nw, c->err, s, launches));
   return SPH_OK;
 }
 
@@ -591,7 +598,8 @@ size_t sph_state_bytes(int32_t n_inst, const sph_params* params, const int64_t* 
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
+        pl.any_filter, c);
   return c.state_bytes;
 }
 
@@ -599,7 +607,8 @@ size_t sph_workspace_bytes(int32_t n_inst, const sph_params* params, const int64
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
+        pl.any_filter, c);
   return c.ws_bytes;
 }
 
@@ -618,7 +627,7 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
     return SPH_ERR_WORKSPACE;
   Carved cv;
   carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
-        cv);
+        pl.any_filter, cv);
   if (state_bytes < cv.state_bytes || workspace_bytes < cv.ws_bytes) return SPH_ERR_WORKSPACE;
 
   sph_ctx* c = new (std::nothrow) sph_ctx();

@@ -177,6 +177,11 @@ struct NbrWs {
   uint32_t* mask;       // [kMaxCandWords][n] candidate hit bits
   uint32_t* cand;       // [grid cells][kMaxCand] candidate table of each cell
   uint32_t* ncand;      // [grid cells] candidates of each cell
+  // Pressure filter only (null otherwise): the kernel shape t^4 (2q + 1) of
+  // every list entry, written by the density pass in the list's layout
+  // (nbr_slot), so the filter neither gathers positions nor re-evaluates W.
+  double* wsh_d;        // FP64 form
+  float* wsh_f;         // mixed form
   int32_t cap;          // list slots per particle (multiple of 8)
 };
 

@@ -56,8 +56,8 @@ cudaError_t launch_density_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f
                                 int* launches);
 // Pressure filter (instances with SPH_PFILTER) over the density pass's lists.
 cudaError_t launch_pfilter_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
-                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
-                                uint32_t* err, cudaStream_t s, int* launches);
+                                const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                cudaStream_t s, int* launches);
 cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                uint32_t* err,

@@ -246,7 +246,9 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
 // The walk takes 8 neighbours at a time: their table entries, then their
 // offset records, are loaded together before the 8 pairs are summed, and the
 // 8 entries are stored as one 32-byte list group.
-template <int BLOCK>
+// kFilter: some instance uses the pressure filter; the kernel shape of every
+// list entry is then stored beside the list (nw.wsh_f) for the filter.
+template <int BLOCK, bool kFilter>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
                 NbrWs nw, uint32_t* err) {
@@ -285,8 +287,10 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u)
         if (u < m) o[u] = b.off[e[u] & kNbrIndexMask];
+      float wq[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u) {
+        wq[u] = 0.f;
         if (u < m) {
           float dx, dy2, dz2;
           entry_vec(P, dtab, e[u], oi, o[u], dx, dy2, dz2);
@@ -297,8 +301,14 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
           const float t1 = fmaf(-half_inv_h, r, 1.f);
           const float t2 = t1 * t1;
           const float Wt = t2 * t2 * fmaf(two_inv_h, r, 1.f);
+          wq[u] = Wt;
           acc.add((o[u].w == 0.f ? mrD0 : mrD1) * Wt);
         }
+      }
+      if (kFilter && g < groups) {  // the group's kernel shapes, beside the list group
+        float4* dw = reinterpret_cast<float4*>(nw.wsh_f + nbr_slot(n, i, g << 3));
+        dw[0] = make_float4(wq[0], wq[1], wq[2], wq[3]);
+        dw[1] = make_float4(wq[4], wq[5], wq[6], wq[7]);
       }
     }
     if (cnt > (groups << 3)) {
@@ -330,51 +340,38 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
 // the instances that enable it.  The inputs (V, P) come from the density
 // pass's separate array and the outputs go to f.P and spin.w, so rows never
 // read a value another row writes.  W enters through its shape t^4 (2q + 1)
-// only (the constant aD cancels); the sums are compensated across groups of
-// 8 neighbours like the pair pass.
+// (the constant aD cancels), which the density pass stored for every list
+// entry: the pass streams the list and the shapes and gathers (V, P) only.
+// The sums are compensated across groups of 8 neighbours like the pair pass.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                 uint32_t* err) {
-  __shared__ float4 dtab[64];
-  fill_disp_table(dtab);
-  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
-  const float4 oi = b.off[i];
-  if (!(P.flags & SPH_PFILTER) || oi.w == 3.f) return;  // outer walls keep P
+  if (!(P.flags & SPH_PFILTER) || b.off[i].w == 3.f) return;  // outer walls keep P
   const float2 own = f.vp[i];
   Kahan num{own.x * own.y, 0.f}, den{own.x, 0.f};  // self term, W(0) / aD = 1
-  const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
   const uint32_t cnt = nw.count[i];
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  const float4* __restrict__ shapes = reinterpret_cast<const float4*>(nw.wsh_f);
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
     const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
     const uint4 ga = groups[g], gb = groups[g + 1];
+    const float4 wa = shapes[g], wb = shapes[g + 1];
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    const float ws[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
     const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
-    float4 oj[8];
     float2 vj[8];
 #pragma unroll
-    for (uint32_t u = 0; u < 8; ++u) {
-      if (u < m) {
-        const uint32_t j = e[u] & kNbrIndexMask;
-        oj[u] = b.off[j];
-        vj[u] = f.vp[j];
-      }
-    }
+    for (uint32_t u = 0; u < 8; ++u)
+      if (u < m) vj[u] = f.vp[e[u] & kNbrIndexMask];
     float gn = 0.f, gd = 0.f;
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
       if (u < m) {
-        float dx, dy, dz;
-        entry_vec(P, dtab, e[u], oi, oj[u], dx, dy, dz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-        const float t1 = fmaf(-half_inv_h, r, 1.f);
-        const float t2 = t1 * t1;
-        const float w = vj[u].x * (t2 * t2 * fmaf(two_inv_h, r, 1.f));
+        const float w = vj[u].x * ws[u];
         gn += w * vj[u].y;
         gd += w;
       }
@@ -426,10 +423,10 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
   const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
   const bool lit = kExtra && (fl & SPH_SN_LITERAL) != 0;
-  // collision model: col_dist^2 (0 when off) and -(1 + e) mu_ij / dt of the
-  // pair's species, indexed by the species sum so both sides read one value
+  // collision model: col_dist^2 (0 when off); its coefficient
+  // -(1 + e) mu_ij / dt is read, for the rare colliding pair only, from the
+  // table indexed by the species sum, so both sides of a pair read one value
   const float col2 = kExtra ? P.col2_f : 0.f;
-  const float cC0 = kExtra ? P.cC_f[si] : 0.f, cC1 = kExtra ? P.cC_f[si + 1] : 0.f;
   const bool inv_i = sp_i == 0;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
@@ -525,12 +522,11 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const float aV = (VF * inv_r2) * ((vis_j ? cBA1 : 0.f) * dv);
       const float bR = (vis_j ? cB1 : cB0) * VF;
       const float bN = (vis_j ? cN1 : cN0) * (VV * W);
+      float base = aP + aV;  // the z component drops aT under the projection
       // collision of an approaching pair closer than col_dist: the central
       // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij
-      float aC = 0.f;
-      if (kExtra && r2 < col2 && dv < 0.f) aC = (vis_j ? cC1 : cC0) * (dv * inv_r2);
-      // the z component drops aT under the projection
-      const float base = kExtra ? (aP + aV) + aC : aP + aV;
+      if (kExtra && r2 < col2 && dv < 0.f)
+        base += P.cC_f[si + (vis_j ? 1 : 0)] * (dv * inv_r2);
       const float al = base + aT;
       const float alz = hproj ? base : al;
       const float bu = lit ? bR : bR + bN;
@@ -672,12 +668,23 @@ cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                  uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                  int* launches) {
-  if (lc.block_density == 32)
-    k_density_mixed<32><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(n, b, f, inst, cw, nw, err);
-  else if (lc.block_density == 64)
-    k_density_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, f, inst, cw, nw, err);
-  else
-    k_density_mixed<128><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  const unsigned g32 = (unsigned)((n + 31) / 32), g64 = (unsigned)((n + 63) / 64),
+                 g128 = (unsigned)((n + 127) / 128);
+  if (lc.any_filter) {
+    if (lc.block_density == 32)
+      k_density_mixed<32, true><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else if (lc.block_density == 64)
+      k_density_mixed<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else
+      k_density_mixed<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  } else {
+    if (lc.block_density == 32)
+      k_density_mixed<32, false><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else if (lc.block_density == 64)
+      k_density_mixed<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+    else
+      k_density_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }
