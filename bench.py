@@ -54,6 +54,10 @@ DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
 # not counted).
 FILTER_BYTES_PER_PAIR = {"fp64": 12, "mixed": 8}
 FILTER_BYTES_PER_PARTICLE = {"fp64": 4 + 16 + 8 + 8, "mixed": 4 + 8 + 4 + 4}
+# its arithmetic: two fused multiply-adds per neighbour (FP64 form, which
+# stores V and V P), three operations plus a compensated sum per group of 8
+# (mixed); on GB300's FP64 pipe the FP64 form's two FMAs outweigh its bytes.
+FILTER_FLOPS_PER_PAIR = {"fp64": 4, "mixed": 3}
 COLLISION_FLOPS_PER_PAIR = 1
 EXTRAS = {"pfilter": 128, "collision": 256}
 # Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
@@ -110,7 +114,8 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, 
              "forces": force_flops(form, extras) * pairs}
     if "pfilter" in extras:
         by = filter_bytes(form, pairs, n_particles)
-        bound["pressure_filter"] = by / (hbm_gbs * 1e9) * 1e3
+        fl = FILTER_FLOPS_PER_PAIR[form] * pairs
+        bound["pressure_filter"] = max(by / (hbm_gbs * 1e9), fl / (peak_alu[form] * 1e12)) * 1e3
     for st, fl in flops.items():
         pk = peak_alu["mixed"] if st == "cell_search" else peak_alu[form]  # search is FP32
         bound[st] = fl / (pk * 1e12) * 1e3
@@ -511,14 +516,26 @@ def run_ours(args, dist):
         if "pfilter" in extras:
             t = results[f]["stages"]["pressure_filter"]
             by = filter_bytes(f, pr, n_part)
-            roofs.setdefault(f, {})["pressure_filter"] = {
-                "kernel": f"k_pfilter_{f}", "bound": "hbm", "achieved": by / (t * 1e-3) / 1e9,
-                "peak": hbm_peak(), "unit": "GB/s", "frac": by / (t * 1e-3) / 1e9 / hbm_peak(),
-                "traffic": measured_traffic(f"k_pfilter_{f}", n_part),
-                "traffic_unit": "bytes per launch", "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured",
-                "work": f"{FILTER_BYTES_PER_PAIR[f]} B x {pr} fluid neighbour pairs + "
-                        f"{FILTER_BYTES_PER_PARTICLE[f]} B x {n_part} particles per launch",
-                "launch_ms": t}
+            fl = FILTER_FLOPS_PER_PAIR[f] * pr
+            pk = peaks["mixed"] if f == "mixed" else peaks["fp64"]
+            ent = {"kernel": f"k_pfilter_{f}",
+                   "traffic": measured_traffic(f"k_pfilter_{f}", n_part),
+                   "traffic_unit": "bytes per launch", "launch_ms": t}
+            if by / (hbm_peak() * 1e9) >= fl / (pk * 1e12):  # the HBM roof is the higher
+                ach = by / (t * 1e-3) / 1e9
+                ent.update(bound="hbm", achieved=ach, peak=hbm_peak(), unit="GB/s",
+                           frac=ach / hbm_peak(),
+                           peak_source="MEASURED_PEAKS.json hbm_gbs, of measured",
+                           work=f"{FILTER_BYTES_PER_PAIR[f]} B x {pr} fluid neighbour pairs + "
+                                f"{FILTER_BYTES_PER_PARTICLE[f]} B x {n_part} particles per launch")
+            else:
+                ach = fl / (t * 1e-3) / 1e12
+                ent.update(bound="alu", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                           peak_source=f"measured {unit} FMA-chain rate of this GPU "
+                                       "(sph_fma_peak), of measured",
+                           work=f"{FILTER_FLOPS_PER_PAIR[f]} {unit} flop x {pr} fluid neighbour "
+                                "pairs per launch")
+            roofs.setdefault(f, {})["pressure_filter"] = ent
         for stage, kern, fpp, units, what, u in stages:
             pk = peaks["mixed"] if u == "FP32" else peaks["fp64"]
             src = f"measured {u} FMA-chain rate of this GPU (sph_fma_peak), of measured"

@@ -210,6 +210,26 @@ SPH_API sph_status sph_diagnostics(sph_ctx* ctx, int32_t inst, sph_diag* out);
  * since the last reorder (SPH_ERR_STATE otherwise); synchronises. */
 SPH_API sph_status sph_force_breakdown(sph_ctx* ctx, int32_t inst, double out[5]);
 
+/* Checkpoint and resume (a production run of the paper's size takes days).
+ * A checkpoint is a small header plus a verbatim copy of the context's state
+ * buffer: the sorted particle state in its stored precision (the mixed form's
+ * cell + FP32 offset exactly, not a rounded FP64 position), the accelerations
+ * of the last pair pass that the next half kick uses, and per instance the
+ * wall phase, wall torque, torque impulse and step count.
+ *  - sph_checkpoint_bytes: size of a checkpoint of ctx (0 for NULL).
+ *  - sph_save_checkpoint: synchronises; returns the pending device error, if
+ *    one is latched, without writing; otherwise writes the checkpoint to buf
+ *    (host or device memory, at least sph_checkpoint_bytes) and leaves the
+ *    context unchanged.
+ *  - sph_load_checkpoint: restores a checkpoint into ctx, which must have
+ *    been created by this library build with the same parameters and counts
+ *    (SPH_ERR_ARG otherwise: wrong size, header or instance constants; the
+ *    context is then unchanged).  Synchronises.  Stepping on gives, bit for
+ *    bit, what the saved context would have given. */
+SPH_API size_t sph_checkpoint_bytes(const sph_ctx* ctx);
+SPH_API sph_status sph_save_checkpoint(sph_ctx* ctx, void* buf, size_t bytes);
+SPH_API sph_status sph_load_checkpoint(sph_ctx* ctx, const void* buf, size_t bytes);
+
 /* Copy the state out in input order (synchronises).  Any pointer may be NULL.
  * pos, vel, spin, acc, dspin: 3n doubles; rho, P: n doubles. */
 SPH_API sph_status sph_get_state(sph_ctx* ctx, double* pos, double* vel, double* spin,

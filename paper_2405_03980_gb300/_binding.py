@@ -102,6 +102,9 @@ def lib(build_if_missing: bool = True):
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
+                "sph_checkpoint_bytes": (C.c_size_t, [vp]),
+                "sph_save_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
+                "sph_load_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
                 "sph_destroy": (C.c_int, [vp]),
                 "sph_status_string": (C.c_char_p, [C.c_int]),
             }
@@ -120,7 +123,8 @@ def exported_symbols() -> list[str]:
             "sph_diagnostics", "sph_force_breakdown", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
             "sph_autotune", "sph_get_launch_config",
-            "sph_fma_peak", "sph_diag_sums_noalloc", "sph_destroy", "sph_status_string"]
+            "sph_fma_peak", "sph_diag_sums_noalloc", "sph_checkpoint_bytes",
+            "sph_save_checkpoint", "sph_load_checkpoint", "sph_destroy", "sph_status_string"]
 
 
 def _ck(st: int, where: str):
@@ -300,6 +304,30 @@ def sph_get_launch_config(ctx) -> dict:
     _ck(lib().sph_get_launch_config(ctx, C.byref(a), C.byref(b), C.byref(w)),
         "sph_get_launch_config")
     return {"block_density": a.value, "block_forces": b.value, "search_warps": w.value}
+
+
+def sph_checkpoint_bytes(ctx) -> int:
+    return int(lib().sph_checkpoint_bytes(ctx))
+
+
+def sph_save_checkpoint(ctx, buf=None):
+    """Write a checkpoint of ctx into buf (a uint8 numpy array or tensor of at
+    least sph_checkpoint_bytes; a new host array if None) and return buf."""
+    nb = sph_checkpoint_bytes(ctx)
+    if buf is None:
+        buf = np.empty(nb, dtype=np.uint8)
+    _ck(lib().sph_save_checkpoint(ctx, _ptr(buf), _nbytes(buf)), "sph_save_checkpoint")
+    return buf
+
+
+def sph_load_checkpoint(ctx, buf):
+    _ck(lib().sph_load_checkpoint(ctx, _ptr(buf), _nbytes(buf)), "sph_load_checkpoint")
+
+
+def _nbytes(a) -> int:
+    if isinstance(a, np.ndarray):
+        return int(a.nbytes)
+    return int(a.numel() * a.element_size())
 
 
 def sph_destroy(ctx):

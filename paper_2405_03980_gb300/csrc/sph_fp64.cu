@@ -276,7 +276,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   const double V = m_i / rho;
   b.vel[i].w = V;
   b.spin[i].w = Pres / (rho * rho);
-  if (P.flags & SPH_PFILTER) f.vp[i] = sp == 3 ? dvec2{0.0, 0.0} : dvec2{V, Pres};
+  if (P.flags & SPH_PFILTER) f.vp[i] = sp == 3 ? dvec2{0.0, 0.0} : dvec2{V, V * Pres};
   if (!isfinite(rho) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
 }
 
@@ -286,11 +286,12 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 // zeroth-order kernel average): P_i <- sum_j V_j P_j W_ij / sum_j V_j W_ij
 // over i itself and its neighbour list, for fluid and inner-wall particles of
 // the instances that enable it.  The inputs (V, P) come from the density
-// pass's separate array and the outputs go to f.P and spin.w, so rows never
-// read a value another row writes.  W enters through its shape t^4 (2q + 1)
-// (the constant aD cancels), which the density pass stored for every list
-// entry: the pass streams the list and the shapes and gathers (V, P) only,
-// leaving three FP64 operations per neighbour.
+// pass's separate array, as (V, V P), and the outputs go to f.P and spin.w,
+// so rows never read a value another row writes.  W enters through its shape
+// t^4 (2q + 1) (the constant aD cancels), which the density pass stored for
+// every list entry: the pass streams the list and the shapes and gathers
+// (V, V P) only, leaving two FP64 fused multiply-adds per neighbour (the FP64
+// pipe, not memory, bounds it).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, NbrWs nw,
@@ -300,7 +301,7 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   const InstDev& P = inst[b.inst[i]];
   if (!(P.flags & SPH_PFILTER) || b.pos[i].w == 3.0) return;  // outer walls keep P
   const dvec2 own = f.vp[i];
-  double num = own.x * own.y, den = own.x;  // self term, W(0) / aD = 1
+  double num = own.y, den = own.x;  // self term, W(0) / aD = 1
   const uint32_t cnt = nw.count[i];
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
   const dvec2* __restrict__ shapes = reinterpret_cast<const dvec2*>(nw.wsh_d);
@@ -317,9 +318,9 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     for (uint32_t u = 0; u < 8; ++u) {
       if (u >= m) break;
       const dvec2 vj = f.vp[e[u] & kNbrIndexMask];
-      const double w = vj.x * ((u & 1) ? w2[u >> 1].y : w2[u >> 1].x);
-      num += w * vj.y;
-      den += w;
+      const double w = (u & 1) ? w2[u >> 1].y : w2[u >> 1].x;
+      num = fma(w, vj.y, num);
+      den = fma(w, vj.x, den);
     }
   }
   const double Pf = num / den;

@@ -9,9 +9,24 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph_kernels.h"
 
 using namespace sphgb;
+
+namespace {
+
+// NVTX range around a public entry point (host side; the kernels a call
+// enqueues, graph replays included, are attributed to it by the profilers).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -209,6 +224,8 @@ struct sph_ctx {
   char* backup = nullptr;        // autotuner copy of acc, dspin, wall torque, InstState
   void* staging = nullptr;
   size_t staging_bytes = 0;
+  void* state = nullptr;          // the caller's state buffer (checkpoints copy it)
+  size_t state_bytes = 0;         // bytes of it in use
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -617,6 +634,7 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
                           const double* spin, const uint8_t* species, void* dev_state,
                           size_t state_bytes, void* dev_workspace, size_t workspace_bytes,
                           void* stream) {
+  NvtxRange range("sph_init");
   if (!out) return SPH_ERR_ARG;
   *out = nullptr;
   if (!pos || !vel || !spin || !species || !dev_state || !dev_workspace) return SPH_ERR_ARG;
@@ -655,6 +673,8 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->backup = cv.backup;
   c->staging = cv.staging;
   c->staging_bytes = cv.staging_bytes;
+  c->state = dev_state;
+  c->state_bytes = cv.state_bytes;
   c->stream = (cudaStream_t)stream;
   int dev = 0;
   auto fail = [&](sph_status s) {
@@ -752,6 +772,7 @@ sph_status sph_init(sph_ctx** ctx, const sph_params* params, int64_t n, const do
 }
 
 sph_status sph_build_cells(sph_ctx* c) {
+  NvtxRange range("sph_build_cells");
   if (!c) return SPH_ERR_ARG;
   sph_status st = enqueue_cells(c, c->stream, 0, nullptr);
   if (st != SPH_OK) return st;
@@ -762,11 +783,13 @@ sph_status sph_build_cells(sph_ctx* c) {
 }
 
 sph_status sph_density(sph_ctx* c) {
+  NvtxRange range("sph_density");
   if (!c) return SPH_ERR_ARG;
   return enqueue_density(c, c->stream, nullptr);
 }
 
 sph_status sph_forces(sph_ctx* c) {
+  NvtxRange range("sph_forces");
   if (!c) return SPH_ERR_ARG;
   if (!c->lists_valid) return SPH_ERR_STATE;  // needs sph_density first
   sph_status st = enqueue_forces(c, c->stream, 0, nullptr);
@@ -775,6 +798,7 @@ sph_status sph_forces(sph_ctx* c) {
 }
 
 sph_status sph_step(sph_ctx* c, int32_t nsteps) {
+  NvtxRange range("sph_step");
   if (!c || nsteps < 0) return SPH_ERR_ARG;
   if (nsteps == 0) return SPH_OK;
   if (!c->forces_valid) {
@@ -818,6 +842,7 @@ sph_status sph_force_breakdown(sph_ctx* c, int32_t inst, double out[5]) {
 }
 
 sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
+  NvtxRange range("sph_diagnostics");
   if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
   if (mixed(c))
     CK(launch_diag_mixed(c->n_inst, c->total_chunks, c->inst, c->mbuf[c->cur], c->mf, c->nw,
@@ -852,6 +877,82 @@ sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
   out->step = s.step;
   out->theta = s.theta;
   return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checkpoint header; the verbatim state buffer follows it.
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t precision;
+  int32_t n_inst;
+  int32_t cur;
+  int64_t n;
+  uint64_t state_bytes;
+  uint64_t inst_bytes;     // InstDev array at the start of the state buffer
+  uint64_t forces_valid;   // the stored accelerations belong to the stored order
+  uint64_t reserved[2];
+};
+constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+}  // namespace
+
+extern "C" {
+
+size_t sph_checkpoint_bytes(const sph_ctx* c) {
+  return c ? sizeof(CkptHeader) + c->state_bytes : 0;
+}
+
+sph_status sph_save_checkpoint(sph_ctx* c, void* buf, size_t bytes) {
+  NvtxRange range("sph_save_checkpoint");
+  if (!c || !buf || bytes < sph_checkpoint_bytes(c)) return SPH_ERR_ARG;
+  sph_status st = sph_check(c);  // synchronises; a latched error is not saved
+  if (st != SPH_OK) return st;
+  CkptHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kCkptMagic, sizeof h.magic);
+  h.version = kCkptVersion;
+  h.precision = c->precision;
+  h.n_inst = c->n_inst;
+  h.cur = c->cur;
+  h.n = c->n;
+  h.state_bytes = c->state_bytes;
+  h.inst_bytes = sizeof(InstDev) * (uint64_t)c->n_inst;
+  h.forces_valid = c->forces_valid ? 1u : 0u;
+  char* out = static_cast<char*>(buf);
+  CK(cudaMemcpyAsync(out, &h, sizeof h, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(out + sizeof h, c->state, c->state_bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SPH_OK;
+}
+
+sph_status sph_load_checkpoint(sph_ctx* c, const void* buf, size_t bytes) {
+  NvtxRange range("sph_load_checkpoint");
+  if (!c || !buf || bytes < sph_checkpoint_bytes(c)) return SPH_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  const char* in = static_cast<const char*>(buf);
+  CkptHeader h;
+  CK(cudaMemcpy(&h, in, sizeof h, cudaMemcpyDefault));
+  if (memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != kCkptVersion ||
+      h.precision != c->precision || h.n_inst != c->n_inst || h.n != c->n ||
+      h.state_bytes != c->state_bytes || (h.cur != 0 && h.cur != 1) ||
+      h.inst_bytes != sizeof(InstDev) * (uint64_t)c->n_inst ||
+      (const char*)c->inst != (const char*)c->state)
+    return SPH_ERR_ARG;
+  // the instance constants (derived from the parameters and counts) must match
+  std::vector<InstDev> saved((size_t)c->n_inst);
+  CK(cudaMemcpy(saved.data(), in + sizeof h, h.inst_bytes, cudaMemcpyDefault));
+  if (memcmp(saved.data(), c->inst_h.data(), h.inst_bytes) != 0) return SPH_ERR_ARG;
+  CK(cudaMemcpyAsync(c->state, in + sizeof h, c->state_bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cur = h.cur;
+  c->forces_valid = h.forces_valid != 0;  // the accelerations came with the state
+  c->lists_valid = false;                 // neighbour lists live in the workspace
+  return sph_check(c);
 }
 
 sph_status sph_get_state(sph_ctx* c, double* pos, double* vel, double* spin, double* rho,

@@ -126,7 +126,7 @@ struct MixFields {
   float4* tw;           // torque of wall neighbours on each fluid particle
   float* delta;         // rho / rho0 - 1
   float* P;
-  float2* vp;           // pressure filter input (V, V P); (0, 0) for outer walls
+  float2* vp;           // pressure filter input (V, P); (0, 0) for outer walls
 };
 
 constexpr uint32_t kCellBitsX = 11, kCellBitsY = 11, kCellBitsZ = 10;

@@ -102,6 +102,21 @@ class Simulation:
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)
 
+    # -- checkpoint / resume ----------------------------------------------
+    def save_checkpoint(self, path: str | None = None):
+        """The complete persistent state as a host uint8 array (also written
+        to path if given); restore it with load_checkpoint on a Simulation
+        of the same instances, parameters and precision."""
+        buf = B.sph_save_checkpoint(self.ctx)
+        if path is not None:
+            buf.tofile(path)
+        return buf
+
+    def load_checkpoint(self, src):
+        """Restore a checkpoint (array from save_checkpoint, or a file path)."""
+        buf = np.fromfile(src, dtype=np.uint8) if isinstance(src, str) else src
+        B.sph_load_checkpoint(self.ctx, buf)
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             B.sph_destroy(self.ctx)
