@@ -18,6 +18,8 @@
 //   periodic z (slip top/bottom).  Walls count as the viscous species.
 #include <math.h>
 
+#include <type_traits>
+
 #include "sph_kernels.h"
 
 namespace sphgb {
@@ -332,11 +334,11 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 
 // ------------------------------------------------------------------ pair pass
 
-// kExtra: some instance uses the literal F_sn (coefficient of v_ij) or the
-// collision model; the default form has neither and drops both at compile
-// time.
-template <int BLOCK, bool kExtra>
-__global__ void __launch_bounds__(BLOCK, kExtra ? 512 / BLOCK : 0)
+// kOpt: kOptLiteral if some instance uses the literal F_sn (coefficient of
+// v_ij), kOptCollision if some instance uses the collision model; the
+// default form (0) has neither and drops both at compile time.
+template <int BLOCK, int kOpt>
+__global__ void __launch_bounds__(BLOCK, kOpt ? 512 / BLOCK : 0)
 k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
               CellWs cw, NbrWs nw, uint32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -363,13 +365,13 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   const double cB = (fl & SPH_TERM_ROT) ? P.B * vi.w : 0.0;
   const double cN = (fl & SPH_TERM_SN) ? P.C_l * vi.w : 0.0;
   const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
-  const bool literal = kExtra && (fl & SPH_SN_LITERAL) != 0;
+  const bool literal = (kOpt & kOptLiteral) && (fl & SPH_SN_LITERAL) != 0;
   const bool inv_i = sp_i == 0;
   // collision model: the bits of col_dist^2 (0 when off; r^2 > 0 orders like
   // its bits); its coefficient -(1 + e) mu_ij / dt is read, for the rare
   // colliding pair only, from the table indexed by the species sum, so both
   // sides of a pair read one value
-  const long long col2b = kExtra ? __double_as_longlong(P.col2) : 0ll;
+  const long long col2b = (kOpt & kOptCollision) ? __double_as_longlong(P.col2) : 0ll;
   const int si = inv_i ? 0 : 1;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
@@ -450,7 +452,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       // collision of an approaching pair closer than col_dist: the central
       // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij;
       // both tests on the bits (dv < 0: its sign bit; -0 adds nothing)
-      if (kExtra && r2b < col2b && __double2hiint(dv) < 0)
+      if ((kOpt & kOptCollision) && r2b < col2b && __double2hiint(dv) < 0)
         base += P.cC[si + (vis_j ? 1 : 0)] * dv * inv_r2;
       const double al = base + aT;
       const double alz = hproj ? base : al;
@@ -458,7 +460,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       double pfx = al * dx + bu * ux;
       double pfy = al * dy + bu * uy;
       double pfz = alz * dz + bu * uz;
-      if (kExtra && literal) {  // coefficient bN of v_ij
+      if ((kOpt & kOptLiteral) && literal) {  // coefficient bN of v_ij
         pfx += bN * vx;
         pfy += bN * vy;
         pfz += bN * vz;
@@ -600,21 +602,23 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                int* launches) {
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
-  if (lc.any_extra) {
+  // the pair pass carries only the options some instance uses
+  const int opt = (lc.any_literal ? kOptLiteral : 0) | (lc.any_collision ? kOptCollision : 0);
+  auto go = [&](auto kopt) {
+    constexpr int O = decltype(kopt)::value;
     if (lc.block_forces == 256)
-      k_forces_fp64<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_forces_fp64<256, O><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
     else if (lc.block_forces == 64)
-      k_forces_fp64<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_forces_fp64<64, O><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
     else
-      k_forces_fp64<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
-  } else {
-    if (lc.block_forces == 256)
-      k_forces_fp64<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
-    else if (lc.block_forces == 64)
-      k_forces_fp64<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
-    else
-      k_forces_fp64<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
-  }
+      k_forces_fp64<128, O><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+  };
+  if (opt == 0)
+    go(std::integral_constant<int, 0>());
+  else if (opt == kOptCollision)
+    go(std::integral_constant<int, kOptCollision>());
+  else  // the literal F_sn, with or without collisions
+    go(std::integral_constant<int, kOptLiteral | kOptCollision>());
   if (launches) ++*launches;
   return cudaGetLastError();
 }

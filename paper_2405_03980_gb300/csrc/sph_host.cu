@@ -687,11 +687,13 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->lc.block_density = 128;
   c->lc.block_forces = 128;
   c->lc.search_warps = 4;
-  c->lc.any_extra = false;
+  c->lc.any_literal = false;
+  c->lc.any_collision = false;
   c->lc.any_filter = false;
   for (const InstDev& d : pl.inst) {
     c->max_cells = std::max(c->max_cells, (int64_t)d.nx * d.ny * d.nz);
-    if (d.flags & (SPH_SN_LITERAL | SPH_COLLISION)) c->lc.any_extra = true;
+    if (d.flags & SPH_SN_LITERAL) c->lc.any_literal = true;
+    if (d.flags & SPH_COLLISION) c->lc.any_collision = true;
     if (d.flags & SPH_PFILTER) c->lc.any_filter = true;
   }
   {

@@ -166,6 +166,10 @@ constexpr int kMaxCandWords = kMaxCand / 32;
 // candidate-table entry (index | displacement code).
 constexpr int kNbrGroup = 8;
 
+// Compile-time options of the pair pass (template argument kOpt).
+constexpr int kOptLiteral = 1;    // literal F_sn on v_ij (SPH_SN_LITERAL)
+constexpr int kOptCollision = 2;  // collision model (SPH_COLLISION)
+
 __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t n, int64_t i, uint32_t t) {
   return (((int64_t)(t >> 3) * n + i) << 3) + (int64_t)(t & 7u);
 }

@@ -13,8 +13,8 @@ struct LaunchCfg {
   int block_density;     // threads per block of the density pass (32, 64, 128)
   int block_forces;      // threads per block of the pair pass
   int search_warps;      // warps (cells) per block of the neighbour search
-  bool any_extra;        // some instance uses the literal F_sn (SPH_SN_LITERAL) or
-                         // the collision model (SPH_COLLISION)
+  bool any_literal;      // some instance uses the literal F_sn (SPH_SN_LITERAL)
+  bool any_collision;    // some instance uses the collision model (SPH_COLLISION)
   bool any_filter;       // some instance uses the pressure filter (SPH_PFILTER)
 };
 

@@ -16,6 +16,8 @@
 //    conservation reductions read this state in FP64 (sph_reduce.cu).
 #include <math.h>
 
+#include <type_traits>
+
 #include "sph_kernels.h"
 
 namespace sphgb {
@@ -388,10 +390,10 @@ k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
 
 // ------------------------------------------------------------------ pair pass
 
-// kExtra: some instance uses the literal F_sn (coefficient of v_ij) or the
-// collision model; the default form has neither and drops both at compile
-// time.
-template <int BLOCK, bool kExtra>
+// kOpt: kOptLiteral if some instance uses the literal F_sn (coefficient of
+// v_ij), kOptCollision if some instance uses the collision model; the
+// default form (0) has neither and drops both at compile time.
+template <int BLOCK, int kOpt>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                uint32_t* err) {
@@ -422,11 +424,11 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   const float kB = (fl & SPH_TERM_ROT) ? P.B_f : 0.f;
   const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
   const float hz = (fl & SPH_HPROJ) ? 0.f : 1.f;
-  const bool lit = kExtra && (fl & SPH_SN_LITERAL) != 0;
+  const bool lit = (kOpt & kOptLiteral) && (fl & SPH_SN_LITERAL) != 0;
   // collision model: col_dist^2 (0 when off); its coefficient
   // -(1 + e) mu_ij / dt is read, for the rare colliding pair only, from the
   // table indexed by the species sum, so both sides of a pair read one value
-  const float col2 = kExtra ? P.col2_f : 0.f;
+  const float col2 = (kOpt & kOptCollision) ? P.col2_f : 0.f;
   const bool inv_i = sp_i == 0;
   // The species factors of the pair terms depend on j only through whether
   // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
@@ -525,7 +527,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       float base = aP + aV;  // the z component drops aT under the projection
       // collision of an approaching pair closer than col_dist: the central
       // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij
-      if (kExtra && r2 < col2 && dv < 0.f)
+      if ((kOpt & kOptCollision) && r2 < col2 && dv < 0.f)
         base += P.cC_f[si + (vis_j ? 1 : 0)] * (dv * inv_r2);
       const float al = base + aT;
       const float alz = hproj ? base : al;
@@ -533,7 +535,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       float pfx = al * dx + bu * ux;
       float pfy = al * dy + bu * uy;
       float pfz = alz * dz + bu * uz;
-      if (kExtra && lit) {
+      if ((kOpt & kOptLiteral) && lit) {
         pfx += bN * vx;
         pfy += bN * vy;
         pfz += bN * vz;
@@ -694,21 +696,23 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches) {
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
-  if (lc.any_extra) {
+  // the pair pass carries only the options some instance uses
+  const int opt = (lc.any_literal ? kOptLiteral : 0) | (lc.any_collision ? kOptCollision : 0);
+  auto go = [&](auto kopt) {
+    constexpr int O = decltype(kopt)::value;
     if (lc.block_forces == 256)
-      k_forces_mixed<256, true><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_mixed<256, O><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
     else if (lc.block_forces == 64)
-      k_forces_mixed<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+      k_forces_mixed<64, O><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
     else
-      k_forces_mixed<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
-  } else {
-    if (lc.block_forces == 256)
-      k_forces_mixed<256, false><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
-    else if (lc.block_forces == 64)
-      k_forces_mixed<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
-    else
-      k_forces_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
-  }
+      k_forces_mixed<128, O><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+  };
+  if (opt == 0)
+    go(std::integral_constant<int, 0>());
+  else if (opt == kOptCollision)
+    go(std::integral_constant<int, kOptCollision>());
+  else  // the literal F_sn, with or without collisions
+    go(std::integral_constant<int, kOptLiteral | kOptCollision>());
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -272,11 +272,15 @@ def test_neighbour_overflows_are_latched(precision):
 
 
 @pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
-def test_autotune_leaves_state_and_results_unchanged(precision):
+@pytest.mark.parametrize("extras", [0, B.SPH_PFILTER | B.SPH_COLLISION])
+def test_autotune_leaves_state_and_results_unchanged(precision, extras):
     """The autotuner times launch shapes on the current state; per-particle
     results do not depend on the block size, so the state after tuning and the
-    trajectory that follows are bit-identical to an untuned run."""
+    trajectory that follows are bit-identical to an untuned run (also with
+    the pressure filter and the collision model on)."""
     c = synth.workload("cyl_8960", seed=4)
+    if extras:
+        c.params = dict(c.params, col_dist=0.95, flags=B.SPH_FLAGS_DEFAULT | extras)
     a = sim_of(c, precision=precision)
     b = sim_of(c, precision=precision)
     a.step(2)
