@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -253,7 +254,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples go to SPH_CLOCKS_DIR if set (to keep them), else to
+        # the temporary directory
+        out = os.environ.get("SPH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"sph_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
