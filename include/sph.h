@@ -56,9 +56,12 @@ typedef enum {
   SPH_ERR_NONFINITE = -6,    /* NaN or Inf in the state                        */
   SPH_ERR_TIMEOUT = -7,      /* a bounded device wait gave up                  */
   SPH_ERR_STATE = -8,        /* call out of order (e.g. step before init)      */
-  SPH_ERR_NEIGHBORS = -9     /* a neighbour list exceeded nbr_cap (truncated),
+  SPH_ERR_NEIGHBORS = -9,    /* a neighbour list exceeded nbr_cap (truncated),
                                 or a cell's 27-cell stencil held more than 1024
                                 particles (those beyond are not searched)     */
+  SPH_ERR_BOUNDS = -10       /* checked build only (compiled with SPH_CHECKED):
+                                an index taken from device data failed its
+                                bounds check; a safe index was used instead  */
 } sph_status;
 
 /* Particle species (Sec. 2.1 two components; Sec. 3 wall and dummy particles). */

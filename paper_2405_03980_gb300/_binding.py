@@ -21,7 +21,8 @@ _lib = None
 SPH_OK = 0
 STATUS = {0: "SPH_OK", -1: "SPH_ERR_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
           -4: "SPH_ERR_GRID_OVERFLOW", -5: "SPH_ERR_ESCAPED", -6: "SPH_ERR_NONFINITE",
-          -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE", -9: "SPH_ERR_NEIGHBORS"}
+          -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE", -9: "SPH_ERR_NEIGHBORS",
+          -10: "SPH_ERR_BOUNDS"}
 SPH_TERM_P, SPH_TERM_T, SPH_TERM_SH, SPH_TERM_ROT, SPH_TERM_SN = 1, 2, 4, 8, 16
 SPH_HPROJ, SPH_SN_LITERAL, SPH_FLAGS_DEFAULT = 32, 64, 63
 SPH_PFILTER, SPH_COLLISION = 128, 256
@@ -64,15 +65,19 @@ def lib_path() -> str:
 
 
 def lib(build_if_missing: bool = True):
-    """Load the sm_103a library (building it with nvcc if it is absent)."""
+    """Load the sm_103a library (building it with nvcc if it is absent).
+
+    With SPH_CHECKED=1 in the environment the checked variant is loaded
+    instead (device bounds checks that latch SPH_ERR_BOUNDS)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            checked = os.environ.get("SPH_CHECKED", "") == "1"
+            path = _build.LIB_CHECKED if checked else _build.LIB
             if not os.path.exists(path):
                 if not build_if_missing:
                     raise RuntimeError(f"CUDA library missing: {path}")
-                _build.build()
+                _build.build(checked=checked)
             L = C.CDLL(path)
             vp, P, i64p = C.c_void_p, C.POINTER(SphParams), C.POINTER(C.c_int64)
             sig = {

@@ -91,25 +91,32 @@ __global__ void k_scan_add(uint32_t* __restrict__ start, const uint32_t* __restr
 
 __global__ void k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
                           const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
-                          int64_t n) {
+                          int64_t n, int64_t n_cells, uint32_t* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    perm[start[key[i]] + slot[i]] = (uint32_t)i;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = key[i];
+    if (!bounds_ok((int64_t)k < n_cells, err)) continue;
+    const uint32_t d = start[k] + slot[i];
+    if (!bounds_ok((int64_t)d < n, err)) continue;
+    perm[d] = (uint32_t)i;
+  }
 }
 
 // Sort the entries of every cell by particle id (insertion sort; cells hold
 // about 18 particles at a cell side of 2h = 2.6 dx).
 __global__ void k_cell_sort(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
-                            const uint32_t* __restrict__ id, int64_t n_cells) {
+                            const uint32_t* __restrict__ id, int64_t n_cells, int64_t n,
+                            uint32_t* err) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = start[c], e = start[c + 1];
+    if (!bounds_ok(s <= e && (int64_t)e <= n, err)) continue;
     const uint32_t m = e - s;
     if (m <= 1) continue;
     if (m <= 32) {
       uint32_t kk[32], vv[32];
       for (uint32_t t = 0; t < m; ++t) {
-        vv[t] = perm[s + t];
+        vv[t] = checked_index(perm[s + t], n, err);
         kk[t] = id[vv[t]];
       }
       for (uint32_t t = 1; t < m; ++t) {
@@ -126,9 +133,9 @@ __global__ void k_cell_sort(const uint32_t* __restrict__ start, uint32_t* __rest
       for (uint32_t t = 0; t < m; ++t) perm[s + t] = vv[t];
     } else {
       for (uint32_t t = s + 1; t < e; ++t) {
-        uint32_t v = perm[t], k = id[v];
+        uint32_t v = checked_index(perm[t], n, err), k = id[v];
         uint32_t u = t;
-        while (u > s && id[perm[u - 1]] > k) {
+        while (u > s && id[checked_index(perm[u - 1], n, err)] > k) {
           perm[u] = perm[u - 1];
           --u;
         }
@@ -159,9 +166,9 @@ cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, int* launches) {
 cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches) {
   k_scatter<<<grid_for(n, 256, lc.sm_count, 16), 256, 0, s>>>(cw.key, cw.slot, cw.start,
-                                                                cw.perm, n);
-  k_cell_sort<<<grid_for(cw.n_cells, 128, lc.sm_count, 16), 128, 0, s>>>(cw.start, cw.perm,
-                                                                          id, cw.n_cells);
+                                                                cw.perm, n, cw.n_cells, cw.err);
+  k_cell_sort<<<grid_for(cw.n_cells, 128, lc.sm_count, 16), 128, 0, s>>>(
+      cw.start, cw.perm, id, cw.n_cells, n, cw.err);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }

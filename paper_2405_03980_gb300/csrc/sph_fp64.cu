@@ -161,7 +161,7 @@ __global__ void k_kick_fp64(int64_t n, Fp64Buf b, Fp64Fields f,
 __global__ void k_reorder_fp64(int64_t n, Fp64Buf src, Fp64Buf dst, CellWs cw, NbrWs nw) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = cw.perm[k];
+    const uint32_t j = checked_index(cw.perm[k], n, cw.err);
     const dvec4 p = src.pos[j];
     dst.pos[k] = p;
     dst.vel[k] = src.vel[j];
@@ -235,7 +235,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
       dvec4 pj[4];
 #pragma unroll
       for (uint32_t u = 0; u < 4; ++u)
-        if (u < m) pj[u] = b.pos[e[u] & kNbrIndexMask];
+        if (u < m) pj[u] = b.pos[checked_index(e[u] & kNbrIndexMask, n, err)];
 #pragma unroll
       for (uint32_t u = 0; u < 4; ++u) {
         if (u < m) {
@@ -304,7 +304,7 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   if (!(P.flags & SPH_PFILTER) || b.pos[i].w == 3.0) return;  // outer walls keep P
   const dvec2 own = f.vp[i];
   double num = own.y, den = own.x;  // self term, W(0) / aD = 1
-  const uint32_t cnt = nw.count[i];
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
   const dvec2* __restrict__ shapes = reinterpret_cast<const dvec2*>(nw.wsh_d);
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
@@ -319,7 +319,7 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
       if (u >= m) break;
-      const dvec2 vj = f.vp[e[u] & kNbrIndexMask];
+      const dvec2 vj = f.vp[checked_index(e[u] & kNbrIndexMask, n, err)];
       const double w = (u & 1) ? w2[u >> 1].y : w2[u >> 1].x;
       num = fma(w, vj.y, num);
       den = fma(w, vj.x, den);
@@ -395,7 +395,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   double fx = 0.0, fy = 0.0, fz = 0.0;
   double tx = 0.0, ty = 0.0, tz = 0.0;
   double wx = 0.0, wy = 0.0, wz = 0.0;
-  const uint32_t cnt = nw.count[i];
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
     // one group of 8 entries (a 32-byte sector) per read
@@ -406,7 +406,7 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
       if (u >= m) break;
-      const uint32_t j = e[u] & kNbrIndexMask;
+      const uint32_t j = checked_index(e[u] & kNbrIndexMask, n, err);
       const dvec4 pj = b.pos[j];
       const dvec4 vj = b.vel[j];
       const dvec4 wj = b.spin[j];

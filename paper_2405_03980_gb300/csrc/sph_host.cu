@@ -311,6 +311,7 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.cw.count = w.take<uint32_t>(n_cells);
   c.cw.start = w.take<uint32_t>(n_cells + 1);
   c.cw.n_cells = n_cells;
+  c.cw.err = c.err;
   c.cw.n_scan_blocks = (n_cells + kScanChunk - 1) / kScanChunk;
   c.cw.bsum = w.take<uint32_t>(c.cw.n_scan_blocks + 1);
   c.nw.list = w.take<uint32_t>((int64_t)cap * n);
@@ -401,6 +402,7 @@ sph_status decode_err(uint32_t e) {
   if (e & ERR_ESCAPED) return SPH_ERR_ESCAPED;
   if (e & ERR_NEIGHBORS) return SPH_ERR_NEIGHBORS;
   if (e & ERR_TIMEOUT) return SPH_ERR_TIMEOUT;
+  if (e & ERR_BOUNDS) return SPH_ERR_BOUNDS;
   return SPH_OK;
 }
 
@@ -573,6 +575,7 @@ const char* sph_status_string(sph_status s) {
     case SPH_ERR_TIMEOUT: return "a bounded device wait gave up";
     case SPH_ERR_STATE: return "call out of order";
     case SPH_ERR_NEIGHBORS: return "neighbour list overflow (raise nbr_cap)";
+    case SPH_ERR_BOUNDS: return "an index failed a bounds check (checked build)";
   }
   return "unknown status";
 }

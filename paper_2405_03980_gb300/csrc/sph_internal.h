@@ -28,6 +28,7 @@ enum : uint32_t {
   ERR_NONFINITE = 2u,
   ERR_NEIGHBORS = 4u,
   ERR_TIMEOUT = 8u,
+  ERR_BOUNDS = 16u,         // an index failed a bounds check (checked build)
 };
 
 // Derived per-instance constants (host computed, read-only on the device).
@@ -141,6 +142,7 @@ struct CellWs {
   uint32_t* bsum;       // per-chunk sums of the scan
   int64_t n_cells;
   int64_t n_scan_blocks;
+  uint32_t* err;        // the device error word (bounds checks of the checked build)
 };
 
 // Neighbour sets.  The neighbour search writes, for every grid cell, its
@@ -190,6 +192,36 @@ struct NbrWs {
 };
 
 #ifdef __CUDACC__
+// Checked build (compiled with -DSPH_CHECKED): the indices the kernels take
+// from data (cell keys, sorted positions, candidate runs, neighbour entries,
+// list lengths) are bounds-checked before use; a failed check latches
+// ERR_BOUNDS and a safe index is used instead, so the run ends with
+// SPH_ERR_BOUNDS rather than an out-of-range access.  In the default build
+// the checks compile to nothing.
+#ifdef SPH_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool bounds_ok(bool ok, uint32_t* err) {
+  if (kChecked && !ok) {
+    atomicOr(err, (uint32_t)ERR_BOUNDS);
+    return false;
+  }
+  return true;
+}
+
+// A neighbour-list length, capped at the list's capacity (checked build).
+__device__ __forceinline__ uint32_t checked_count(uint32_t c, int32_t cap, uint32_t* err) {
+  return bounds_ok(c <= (uint32_t)cap, err) ? c : (uint32_t)cap;
+}
+
+// j if j < n, else (checked build) 0 with ERR_BOUNDS latched.
+__device__ __forceinline__ uint32_t checked_index(uint32_t j, int64_t n, uint32_t* err) {
+  return bounds_ok((int64_t)j < n, err) ? j : 0u;
+}
+
 // Walks the set bits of one particle's candidate mask in candidate order and
 // yields the candidate-table entries, B at a time: the B table loads of a
 // batch are independent and in flight together.  The K mask words are first

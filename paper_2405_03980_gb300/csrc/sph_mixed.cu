@@ -227,7 +227,7 @@ __global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __
 __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t j = cw.perm[k];
+    const uint32_t j = checked_index(cw.perm[k], n, cw.err);
     dst.cell[k] = src.cell[j];
     dst.off[k] = src.off[j];
     dst.vel[k] = src.vel[j];
@@ -288,7 +288,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
       float4 o[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u)
-        if (u < m) o[u] = b.off[e[u] & kNbrIndexMask];
+        if (u < m) o[u] = b.off[checked_index(e[u] & kNbrIndexMask, n, err)];
       float wq[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u) {
@@ -355,7 +355,7 @@ k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   if (!(P.flags & SPH_PFILTER) || b.off[i].w == 3.f) return;  // outer walls keep P
   const float2 own = f.vp[i];
   Kahan num{own.x * own.y, 0.f}, den{own.x, 0.f};  // self term, W(0) / aD = 1
-  const uint32_t cnt = nw.count[i];
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
   const float4* __restrict__ shapes = reinterpret_cast<const float4*>(nw.wsh_f);
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
@@ -368,7 +368,7 @@ k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     float2 vj[8];
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u)
-      if (u < m) vj[u] = f.vp[e[u] & kNbrIndexMask];
+      if (u < m) vj[u] = f.vp[checked_index(e[u] & kNbrIndexMask, n, err)];
     float gn = 0.f, gd = 0.f;
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
@@ -458,7 +458,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
   float gfx = 0.f, gfy = 0.f, gfz = 0.f, gtx = 0.f, gty = 0.f, gtz = 0.f;
   float wx = 0.f, wy = 0.f, wz = 0.f;
-  const uint32_t cnt = nw.count[i];
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
   // The list is read one group of 8 entries (one 32-byte sector) at a time,
   // the next group while the current one is evaluated; the neighbour record
   // of the next entry is loaded one pair ahead.
@@ -469,7 +469,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   if (cnt > 0) {
     ga = groups[2 * i];
     gb = groups[2 * i + 1];
-    const uint32_t j0 = ga.x & kNbrIndexMask;
+    const uint32_t j0 = checked_index(ga.x & kNbrIndexMask, n, err);
     oj_n = b.off[j0];
     vj_n = b.vel[j0];
     wj_n = b.spin[j0];
@@ -488,7 +488,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       const uint32_t ent = e[u];
       const float4 oj = oj_n, vj = vj_n, wj = wj_n;
       if (t0 + u + 1 < cnt) {
-        const uint32_t jn = (u < 7 ? e[u + 1] : ga.x) & kNbrIndexMask;
+        const uint32_t jn = checked_index((u < 7 ? e[u + 1] : ga.x) & kNbrIndexMask, n, err);
         oj_n = b.off[jn];
         vj_n = b.vel[jn];
         wj_n = b.spin[jn];

@@ -351,9 +351,12 @@ k_breakdown_chunks(int32_t n_inst, int64_t n, const InstDev* __restrict__ inst, 
     double fs[5][3];
 #pragma unroll
     for (int q = 0; q < 5; ++q) fs[q][0] = fs[q][1] = fs[q][2] = 0.0;
-    const uint32_t cnt = nw.count[i];
+    // list lengths and entries clamped to their ranges (a diagnostic pass:
+    // a corrupt list gives wrong magnitudes, never an out-of-range access)
+    const uint32_t cnt = min(nw.count[i], (uint32_t)nw.cap);
     for (uint32_t t = 0; t < cnt; ++t) {
-      const uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
+      uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
+      if ((int64_t)j >= n) j = 0;
       double pj[3], vj[3], wj[3];
       V.pos(j, P, pj);
       V.vel(j, vj);

@@ -75,6 +75,7 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
         ((int64_t)(cx - 1 + kc) + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2)) * S;
     rj0 = cw.start[key];
     rlen = cw.start[key + S] - rj0;
+    if (!bounds_ok((int64_t)rj0 + rlen <= n, err)) rlen = 0;
     rcode = ((uint32_t)(2 - kc) | ((uint32_t)(1 - dy) << 2) | ((uint32_t)(1 - dz) << 4))
             << kNbrIndexBits;
   }

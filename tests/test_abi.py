@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for st in range(-9, 1):
+    for st in range(-10, 1):
         assert B.sph_status_string(st) != "unknown status"
 
 
@@ -110,3 +110,15 @@ def test_params_struct_layout_matches_header(tmp_path):
                                           check=True).stdout.split()]
     want = [getattr(B.SphParams, f).offset for f in fields] + [C.sizeof(B.SphParams)]
     assert out == want
+
+
+def test_checked_library_builds_and_exports_the_same_symbols():
+    """The checked variant (-DSPH_CHECKED, device bounds checks) builds for
+    sm_103a from its own objects and exports the same C ABI."""
+    path = Bld.build(checked=True)
+    assert path.endswith("libsph_gb300_checked.so") and os.path.exists(path)
+    L = C.CDLL(path)
+    for n in _declared():
+        assert hasattr(L, n), n
+    L.sph_status_string.restype = C.c_char_p
+    assert b"bounds" in L.sph_status_string(-10)
