@@ -73,17 +73,17 @@ SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (167.2, {"sph_search.cu": "849b66d6f39eb77d",
-                                    "sph_internal.h": "9786ab9e4b2ec723"}),
+    "k_cell_search<true>": (167.2, {"sph_search.cu": "151ee245f9331596",
+                                    "sph_internal.h": "bde2088e17d1f86d"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (554.0, {"sph_mixed.cu": "cd782b84b9c4ffd3",
-                                "sph_internal.h": "9786ab9e4b2ec723"}),
-    "k_forces_mixed": (414.4, {"sph_mixed.cu": "cd782b84b9c4ffd3",
-                               "sph_internal.h": "9786ab9e4b2ec723"}),
-    "k_density_fp64": (640.8, {"sph_fp64.cu": "024b786b7aeb9cb2",
-                               "sph_internal.h": "9786ab9e4b2ec723"}),
-    "k_forces_fp64": (511.8, {"sph_fp64.cu": "024b786b7aeb9cb2",
-                              "sph_internal.h": "9786ab9e4b2ec723"}),
+    "k_density_mixed": (553.9, {"sph_mixed.cu": "a2f6a0d29480f7cb",
+                                "sph_internal.h": "bde2088e17d1f86d"}),
+    "k_forces_mixed": (414.3, {"sph_mixed.cu": "a2f6a0d29480f7cb",
+                               "sph_internal.h": "bde2088e17d1f86d"}),
+    "k_density_fp64": (641.3, {"sph_fp64.cu": "4cdbe2df75722991",
+                               "sph_internal.h": "bde2088e17d1f86d"}),
+    "k_forces_fp64": (511.8, {"sph_fp64.cu": "4cdbe2df75722991",
+                              "sph_internal.h": "bde2088e17d1f86d"}),
 }
 
 
