@@ -42,6 +42,10 @@ struct Fp64View {
     v[2] = p.z;
   }
   __device__ __forceinline__ double rho(int64_t i, const InstDev&) const { return f.rho[i]; }
+  // 1 / rho from the stored volume V = m / rho (one multiply, no division)
+  __device__ __forceinline__ double inv_rho(int64_t i, double, double inv_m) const {
+    return b.vel[i].w * inv_m;
+  }
   __device__ __forceinline__ double pres(int64_t i) const { return f.P[i]; }
   // The wall torque of particle i, if it is not zero (it is zero for every
   // particle without a wall neighbour, walls included); the test looks at
@@ -87,6 +91,10 @@ struct MixView {
   }
   __device__ __forceinline__ double rho(int64_t i, const InstDev& P) const {
     return P.rho0 * (1.0 + (double)f.delta[i]);
+  }
+  // the stored FP32 volume is too coarse for 1/rho - 1/rho0: divide in FP64
+  __device__ __forceinline__ double inv_rho(int64_t, double rho, double) const {
+    return 1.0 / rho;
   }
   __device__ __forceinline__ double pres(int64_t i) const { return (double)f.P[i]; }
   // The wall torque of particle i, if it is not zero (see Fp64View).
@@ -192,20 +200,31 @@ __global__ void k_wall_torque_final(int32_t n_inst, const InstDev* __restrict__ 
   ist[k] = s;
 }
 
+// x^e for an integer e >= 0 by repeated squaring (three multiplies for the
+// e = 6 of the alpha_P = 7 Tait law).
 __device__ __forceinline__ double ipow(double x, int e) {
   double r = 1.0;
-  for (int t = 0; t < e; ++t) r *= x;
+  for (; e > 0; e >>= 1) {
+    if (e & 1) r *= x;
+    x *= x;
+  }
   return r;
 }
 
-// Tait internal energy per unit mass, e(rho) = int_{rho0}^{rho} P(s)/s^2 ds.
-__device__ __forceinline__ double tait_energy(const InstDev& P, double rho) {
+// Tait internal energy per unit mass, e(rho) = int_{rho0}^{rho} P(s)/s^2 ds,
+// from rho and 1/rho; ecoef = p0 / ((alpha_P - 1) rho0).
+__device__ __forceinline__ double tait_energy(const InstDev& P, double rho, double inv_rho,
+                                             double ecoef) {
   const double x = rho * P.inv_rho0;
   double e1;
   if (P.alphaP == 1) e1 = P.p0 * P.inv_rho0 * log(x);
-  else e1 = P.p0 / ((double)(P.alphaP - 1) * P.rho0) * (ipow(x, P.alphaP - 1) - 1.0);
-  return e1 + P.beta_P * (1.0 / rho - P.inv_rho0);
+  else e1 = ecoef * (ipow(x, P.alphaP - 1) - 1.0);
+  return e1 + P.beta_P * (inv_rho - P.inv_rho0);
 }
+
+// The bits of a double >= 0 order like its value: min/max of densities and
+// squared speeds on the integer pipe.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // Fields: 0 M, 1 M_s, 2 M_n, 3-5 momentum, 6-8 L_orb, 9-11 L_spin, 12 E_kin,
 // 13 E_rot, 14 E_int, 15 n_pairs; 16 rho_min, 17 rho_max, 18 v_max.
@@ -222,8 +241,15 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
   double v[kSumFields];
 #pragma unroll
   for (int a = 0; a < kSumFields; ++a) v[a] = 0.0;
-  double rmin = INFINITY, rmax = -INFINITY, vmax2 = 0.0;
-  const double I_s = 1.0 / P.inv_I_s, I_n = 1.0 / P.inv_I_n;  // spin inertia per species
+  // the extrema as bits (all values >= 0), the counts as integers: both on
+  // the integer pipe, leaving the FP64 pipe to the sums
+  long long rmin_b = dbits(INFINITY), rmax_b = 0, vmax2_b = 0;
+  uint32_t n_all = 0, n_s = 0;
+  uint64_t pairs = 0;
+  // per-species constants: mass, 1/mass, spin inertia; Tait energy factor
+  const double I_s = 1.0 / P.inv_I_s, I_n = 1.0 / P.inv_I_n;
+  const double inv_ms = 1.0 / P.m_s, inv_mn = 1.0 / P.m_n;
+  const double ecoef = P.alphaP > 1 ? P.p0 / ((double)(P.alphaP - 1) * P.rho0) : 0.0;
   for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
     const int sp = V.species(i);
     if (sp >= 2) continue;
@@ -235,11 +261,11 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
     V.vel(i, u);
     V.spin(i, w);
     const double rho = V.rho(i, P);
+    const double inv_rho = V.inv_rho(i, rho, inv ? inv_ms : inv_mn);
     // particle counts (exact integers): M_s = m_s N_s and M_n = m_n N_n are
     // formed at the end, so the total mass is conserved bit for bit
-    v[0] += 1.0;
-    v[1] += inv ? 1.0 : 0.0;
-    v[2] += inv ? 0.0 : 1.0;
+    ++n_all;
+    n_s += inv ? 1u : 0u;
     v[3] += m * u[0];
     v[4] += m * u[1];
     v[5] += m * u[2];
@@ -252,13 +278,20 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
     const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     v[12] += 0.5 * m * u2;
     v[13] += 0.5 * I * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-    v[14] += m * tait_energy(P, rho);
-    v[15] += (double)nw.count[i];
-    rmin = fmin(rmin, rho);
-    rmax = fmax(rmax, rho);
-    vmax2 = fmax(vmax2, u2);  // the square root of the largest, once
+    v[14] += m * tait_energy(P, rho, inv_rho, ecoef);
+    pairs += nw.count[i];
+    const long long rb = dbits(rho), ub = dbits(u2);
+    rmin_b = rb < rmin_b ? rb : rmin_b;
+    rmax_b = rb > rmax_b ? rb : rmax_b;
+    vmax2_b = ub > vmax2_b ? ub : vmax2_b;  // the square root of the largest, once
   }
-  const double vmax = sqrt(vmax2);
+  v[0] = (double)n_all;
+  v[1] = (double)n_s;
+  v[2] = (double)(n_all - n_s);
+  v[15] = (double)pairs;
+  const double rmin = n_all ? __longlong_as_double(rmin_b) : INFINITY;
+  const double rmax = n_all ? __longlong_as_double(rmax_b) : -INFINITY;
+  const double vmax = sqrt(__longlong_as_double(vmax2_b));
   block_sum<kSumFields>(v, sh);
   const int t = threadIdx.x;
   mx[0][t] = rmin;
