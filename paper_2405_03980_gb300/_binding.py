@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = True):
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
+                "sph_set_launch_config": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32]),
                 "sph_checkpoint_bytes": (C.c_size_t, [vp]),
                 "sph_save_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
                 "sph_load_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
@@ -127,7 +128,7 @@ def exported_symbols() -> list[str]:
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_force_breakdown", "sph_get_state", "sph_get_neighbors", "sph_check",
             "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
-            "sph_autotune", "sph_get_launch_config",
+            "sph_autotune", "sph_get_launch_config", "sph_set_launch_config",
             "sph_fma_peak", "sph_diag_sums_noalloc", "sph_checkpoint_bytes",
             "sph_save_checkpoint", "sph_load_checkpoint", "sph_destroy", "sph_status_string"]
 
@@ -333,6 +334,11 @@ def _nbytes(a) -> int:
     if isinstance(a, np.ndarray):
         return int(a.nbytes)
     return int(a.numel() * a.element_size())
+
+
+def sph_set_launch_config(ctx, block_density: int, block_forces: int, search_warps: int):
+    _ck(lib().sph_set_launch_config(ctx, int(block_density), int(block_forces),
+                                    int(search_warps)), "sph_set_launch_config")
 
 
 def sph_destroy(ctx):

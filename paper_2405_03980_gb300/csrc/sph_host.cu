@@ -452,8 +452,9 @@ sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
 
 sph_status enqueue_search(sph_ctx* c, cudaStream_t s, int* launches) {
   const float4* rec = mixed(c) ? c->mbuf[c->cur].off : c->nw.posf;
-  CK(launch_cell_search(mixed(c), c->n, rec, c->inst, c->n_inst, c->max_cells, c->cw, c->nw,
-                        c->err, s, c->lc, launches));
+  const uint32_t* inst_of = mixed(c) ? c->mbuf[c->cur].inst : c->buf[c->cur].inst;
+  CK(launch_cell_search(mixed(c), c->n, rec, inst_of, c->inst, c->n_inst, c->max_cells, c->cw,
+                        c->nw, c->err, s, c->lc, launches));
   return SPH_OK;
 }
 
@@ -1099,18 +1100,21 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
   }
   const int cand[3] = {64, 128, 256};   // pair pass
   const int dcand[3] = {32, 64, 128};   // density pass
-  const int wcand[3] = {2, 4, 8};
+  // neighbour search: warp per cell with 2, 4 or 8 cells per block, or
+  // (0) thread per particle; both write the same masks and tables
+  const int wcand[4] = {2, 4, 8, 0};
   float best[3] = {INFINITY, INFINITY, INFINITY};
   LaunchCfg pick = c->lc;
-  // trials 0-2: warps per block of the neighbour search (timed alone);
-  // 3-5: density block size (timed with the search before it, which rebuilds
-  // the lists it compacts); 6-8: pair-pass block size
-  for (int trial = 0; trial < 9 && st == SPH_OK; ++trial) {
-    const int kind = trial / 3;
+  // trials 0-3: mapping and shape of the neighbour search (timed alone);
+  // 4-6: density block size (timed with the search before it, which rebuilds
+  // the lists it compacts); 7-9: pair-pass block size
+  for (int trial = 0; trial < 10 && st == SPH_OK; ++trial) {
+    const int kind = trial < 4 ? 0 : (trial < 7 ? 1 : 2);
+    const int opt = trial < 4 ? trial : (trial < 7 ? trial - 4 : trial - 7);
     LaunchCfg saved = c->lc;
-    if (kind == 0) c->lc.search_warps = wcand[trial % 3];
-    if (kind == 1) c->lc.block_density = dcand[trial % 3];
-    if (kind == 2) c->lc.block_forces = cand[trial % 3];
+    if (kind == 0) c->lc.search_warps = wcand[opt];
+    if (kind == 1) c->lc.block_density = dcand[opt];
+    if (kind == 2) c->lc.block_forces = cand[opt];
     cudaEventRecord(e0, s);
     for (int r = 0; r < reps && st == SPH_OK; ++r) {
       if (kind == 0) st = enqueue_search(c, s, nullptr);
@@ -1130,7 +1134,7 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
     }
     c->lc = saved;
     // the density trials must see the chosen search shape
-    if (kind == 0 && trial == 2) c->lc.search_warps = pick.search_warps;
+    if (kind == 0 && trial == 3) c->lc.search_warps = pick.search_warps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1169,6 +1173,26 @@ const char* sph_stage_name(int32_t stage) {
 }
 
 int32_t sph_launches_per_step(const sph_ctx* c) { return c ? c->launches_per_step : 0; }
+
+sph_status sph_set_launch_config(sph_ctx* c, int32_t block_density, int32_t block_forces,
+                                 int32_t search_warps) {
+  if (!c) return SPH_ERR_ARG;
+  const bool bd = block_density == 32 || block_density == 64 || block_density == 128;
+  const bool bf = block_forces == 64 || block_forces == 128 || block_forces == 256;
+  const bool sw = search_warps == 0 || search_warps == 2 || search_warps == 4 ||
+                  search_warps == 8;
+  if (!bd || !bf || !sw) return SPH_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->lc.block_density = block_density;
+  c->lc.block_forces = block_forces;
+  c->lc.search_warps = search_warps;
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) {
+      cudaGraphExecDestroy(c->graph[g]);
+      c->graph[g] = nullptr;
+    }
+  return SPH_OK;
+}
 
 sph_status sph_destroy(sph_ctx* c) {
   if (!c) return SPH_OK;

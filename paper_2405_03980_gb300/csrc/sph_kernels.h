@@ -12,7 +12,8 @@ struct LaunchCfg {
   int sm_count;          // multiprocessors of the device
   int block_density;     // threads per block of the density pass (32, 64, 128)
   int block_forces;      // threads per block of the pair pass
-  int search_warps;      // warps (cells) per block of the neighbour search
+  int search_warps;      // warps (cells) per block of the neighbour search; 0: one
+                         // thread per particle instead
   bool any_literal;      // some instance uses the literal F_sn (SPH_SN_LITERAL)
   bool any_collision;    // some instance uses the collision model (SPH_COLLISION)
   bool any_filter;       // some instance uses the pressure filter (SPH_PFILTER)
@@ -31,10 +32,13 @@ cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
 // builds the neighbour lists.  rec: the per-particle FP32 records (mixed: cell offset
 // and species, FP64 form: the rounded position and species).  mixed_form:
 // exact FP32 test with cell-displacement codes; otherwise the FP32 prefilter.
-cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec, const InstDev* inst,
-                               int32_t n_inst, int64_t max_cells, const CellWs& cw,
-                               const NbrWs& nw, uint32_t* err, cudaStream_t s,
-                               const LaunchCfg& lc, int* launches);
+// lc.search_warps = 0 selects the thread-per-particle mapping (inst_of: the
+// instance of each sorted particle), which writes the same output.
+cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
+                               const uint32_t* inst_of, const InstDev* inst, int32_t n_inst,
+                               int64_t max_cells, const CellWs& cw, const NbrWs& nw,
+                               uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                               int* launches);
 // Raise the dynamic shared-memory limit of the search kernels (once, before
 // any launch or stream capture).
 cudaError_t prepare_search_kernels();

@@ -43,6 +43,12 @@ __device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
   if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
 }
 
+// r^2 of a pair vector with an explicit rounding sequence, so that both
+// search mappings below classify every candidate with the same bits.
+__device__ __forceinline__ float pair_r2(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
 // rec: per sorted particle (x, y, z, species); mixed: the offset inside the
 // cell, FP64 form: the FP32-rounded absolute position.
 template <bool kMixed>
@@ -158,8 +164,7 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
             dy = ey + dy;
             dz = ez + dz;
           }
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          return valid && r2 < cut2;
+          return valid && pair_r2(dx, dy, dz) < cut2;
         };
         uint32_t* mk = sm.mask + k * kMaskRow;
         uint32_t t = 0;
@@ -195,6 +200,101 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
   }
 }
 
+// The same search with the other mapping: one thread per particle walks the
+// 27 runs of its cell's stencil in candidate order and tests each candidate
+// itself (the same FP32 expression as above, so the same bits), setting bit q
+// of its mask words; the first particle of each cell writes the cell's
+// candidate table and its length.  Lanes of one cell load the same candidate
+// record (a broadcast); lanes of neighbouring cells walk runs of different
+// lengths.  The output is identical to the warp-per-cell kernel's.
+template <bool kMixed>
+__global__ void __launch_bounds__(128)
+k_cell_search_tpp(int64_t n, const float4* __restrict__ rec,
+                  const uint32_t* __restrict__ inst_of, const InstDev* __restrict__ inst,
+                  CellWs cw, NbrWs nw, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const InstDev& P = inst[inst_of[i]];
+  const int S = P.slabs;
+  const int64_t g = (int64_t)cw.skey[i] / S;  // grid cell over all instances
+  const int64_t l = g - P.cell_base / S;      // cell inside the instance
+  const int cx = (int)(l % P.nx);
+  const int cy = (int)((l / P.nx) % P.ny);
+  const int cz = (int)(l / ((int64_t)P.nx * P.ny));
+  const uint32_t i0 = cw.start[g * S];
+  const bool writer = (uint32_t)i == i0;  // writes the cell's candidate table
+  const float4 mine = rec[i];
+  const bool active = mine.w != 3.f;      // outer-wall particles keep no list
+  if (!active && !writer) {
+    nw.count[i] = 0u;
+    return;
+  }
+  uint32_t* __restrict__ table = nw.cand + g * kMaxCand;
+  uint32_t* __restrict__ out = nw.mask + i;
+  const float cut2 = kMixed ? P.cut2_f : P.cut2f_margin;
+  uint32_t q = 0, word = 0, hits = 0, self_q = ~0u;
+  bool over = false;
+  for (int r = 0; r < 27 && !over; ++r) {
+    const int dz = r / 9 - 1, dy = (r / 3) % 3 - 1, kc = r % 3;
+    const int zu = cz + dz;  // unwrapped z cell of the run
+    int z2 = zu;
+    if (P.periodic_z) z2 = z2 < 0 ? z2 + P.nz : (z2 >= P.nz ? z2 - P.nz : z2);
+    const int64_t key =
+        P.cell_base +
+        ((int64_t)(cx - 1 + kc) + (int64_t)P.nx * ((cy + dy) + (int64_t)P.ny * z2)) * S;
+    const uint32_t rj0 = cw.start[key];
+    uint32_t rlen = cw.start[key + S] - rj0;
+    if (!bounds_ok((int64_t)rj0 + rlen <= n, err)) rlen = 0;
+    if (r == 13) self_q = q + ((uint32_t)i - rj0);  // run 13 is the particle's own cell
+    const uint32_t code = ((uint32_t)(2 - kc) | ((uint32_t)(1 - dy) << 2) |
+                           ((uint32_t)(1 - dz) << 4)) << kNbrIndexBits;
+    // (c_i - c_j) L per axis (exact): the run's cell is c_i + (kc - 1, dy, dz),
+    // so the displacement is -(kc - 1, dy, dz), the code minus one per axis
+    const float ex = (float)(1 - kc) * P.cellf[0];
+    const float ey = (float)(-dy) * P.cellf[1];
+    const float ez = (float)(-dz) * P.cellf[2];
+    const float zs = (!kMixed && P.periodic_z) ? (zu < 0 ? -1.f : (zu >= P.nz ? 1.f : 0.f)) : 0.f;
+    for (uint32_t e = 0; e < rlen; ++e, ++q) {
+      if (q >= (uint32_t)kMaxCand) {  // more candidates than the table holds
+        over = true;
+        break;
+      }
+      const uint32_t j = rj0 + e;
+      if (writer) table[q] = j | code;
+      if (active) {
+        float4 c = rec[j];
+        if (!kMixed) {  // image of the candidate across the z period
+          if (zs < 0.f) c.z -= P.Hzf;
+          else if (zs > 0.f) c.z += P.Hzf;
+        }
+        float dx = mine.x - c.x, dyv = mine.y - c.y, dzv = mine.z - c.z;
+        if (kMixed) {
+          dx = ex + dx;
+          dyv = ey + dyv;
+          dzv = ez + dzv;
+        }
+        if (pair_r2(dx, dyv, dzv) < cut2) word |= 1u << (q & 31u);
+        if ((q & 31u) == 31u) {  // a full mask word, without the self bit
+          const uint32_t qs = self_q - (q & ~31u);
+          if (qs < 32u) word &= ~(1u << qs);
+          out[(int64_t)(q >> 5) * n] = word;
+          hits += __popc(word);
+          word = 0u;
+        }
+      }
+    }
+  }
+  if (over) latch(err, ERR_NEIGHBORS);
+  if (active && (q & 31u) != 0u) {  // the last, partial word
+    const uint32_t qs = self_q - (q & ~31u);
+    if (qs < 32u) word &= ~(1u << qs);
+    out[(int64_t)(q >> 5) * n] = word;
+    hits += __popc(word);
+  }
+  if (writer) nw.ncand[g] = q;
+  nw.count[i] = active ? hits : 0u;
+}
+
 size_t search_smem(int warps) { return sizeof(WarpSmem) * (size_t)warps; }
 
 }  // namespace
@@ -210,10 +310,20 @@ cudaError_t prepare_search_kernels() {
                               bytes);
 }
 
-cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec, const InstDev* inst,
-                               int32_t n_inst, int64_t max_cells, const CellWs& cw,
-                               const NbrWs& nw, uint32_t* err, cudaStream_t s,
-                               const LaunchCfg& lc, int* launches) {
+cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
+                               const uint32_t* inst_of, const InstDev* inst, int32_t n_inst,
+                               int64_t max_cells, const CellWs& cw, const NbrWs& nw,
+                               uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
+                               int* launches) {
+  if (lc.search_warps == 0) {  // thread-per-particle mapping
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    if (mixed_form)
+      k_cell_search_tpp<true><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err);
+    else
+      k_cell_search_tpp<false><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  }
   int warps = lc.search_warps;
   if (warps < 1 || warps > kMaxSearchWarps) warps = 4;
   const dim3 grid((unsigned)((max_cells + warps - 1) / warps), (unsigned)n_inst);
