@@ -257,10 +257,11 @@ SPH_API int32_t sph_stage_count(void);
 
 /* Autotune the launch shape of the neighbour search, the density pass and the
  * pair pass: each candidate (the search's mapping, one warp per grid cell
- * with 2, 4 or 8 cells per block or one thread per particle, which produce
- * the same masks and tables; 32, 64 or 128 threads per block of the density
- * pass; 64, 128 or 256 of the pair pass) is timed over reps launches on the
- * current state with CUDA events,
+ * with 2, 4 or 8 cells per block and a segment depth of 256 or 512 staged
+ * candidates, or one thread per particle, which all produce the same masks
+ * and tables; 32, 64 or 128 threads per block of the density pass; 64, 128
+ * or 256 of the pair pass) is timed over reps launches on the current state
+ * with CUDA events,
  * the fastest is kept for later steps, and the step graphs are re-captured on
  * the next sph_step.  The trials recompute the same neighbour lists and
  * densities; the pair-pass outputs (which a step computed from half-step
@@ -271,18 +272,21 @@ SPH_API sph_status sph_autotune(sph_ctx* ctx, int32_t reps, int32_t* block_densi
                                 int32_t* block_forces);
 
 /* The launch shape in use: threads per block of the density and pair passes,
- * and warps per block of the neighbour search (one warp per grid cell), 0 if
- * the search runs one thread per particle.  Any pointer may be NULL. */
+ * warps per block of the neighbour search (one warp per grid cell; 0 if the
+ * search runs one thread per particle) and its segment depth.  Any pointer
+ * may be NULL. */
 SPH_API sph_status sph_get_launch_config(const sph_ctx* ctx, int32_t* block_density,
-                                         int32_t* block_forces, int32_t* search_warps);
+                                         int32_t* block_forces, int32_t* search_warps,
+                                         int32_t* search_depth);
 
 /* Set the launch shape by hand (values as sph_autotune chooses them:
  * block_density 32, 64 or 128; block_forces 64, 128 or 256; search_warps 0
- * (thread per particle), 2, 4 or 8).  Results do not depend on the shape.
- * SPH_ERR_ARG for other values (nothing changed); the step graphs are
- * re-captured on the next sph_step. */
+ * (thread per particle), 2, 4 or 8; search_depth 256 or 512).  Results do
+ * not depend on the shape.  SPH_ERR_ARG for other values (nothing changed);
+ * the step graphs are re-captured on the next sph_step. */
 SPH_API sph_status sph_set_launch_config(sph_ctx* ctx, int32_t block_density,
-                                         int32_t block_forces, int32_t search_warps);
+                                         int32_t block_forces, int32_t search_warps,
+                                         int32_t search_depth);
 SPH_API const char* sph_stage_name(int32_t stage);
 
 /* Number of kernel launches one sph_step(ctx, 1) enqueues. */

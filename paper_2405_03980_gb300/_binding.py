@@ -103,11 +103,13 @@ def lib(build_if_missing: bool = True):
                 "sph_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32),
                                            C.POINTER(C.c_int32)]),
                 "sph_get_launch_config": (C.c_int, [vp, C.POINTER(C.c_int32),
-                                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+                                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                                    C.POINTER(C.c_int32)]),
                 "sph_stage_name": (C.c_char_p, [C.c_int32]),
                 "sph_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
                 "sph_diag_sums_noalloc": (C.c_int, [P, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
-                "sph_set_launch_config": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32]),
+                "sph_set_launch_config": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32,
+                                                    C.c_int32]),
                 "sph_checkpoint_bytes": (C.c_size_t, [vp]),
                 "sph_save_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
                 "sph_load_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
@@ -306,10 +308,11 @@ def sph_autotune(ctx, reps: int = 3) -> tuple[int, int]:
 
 
 def sph_get_launch_config(ctx) -> dict:
-    a, b, w = C.c_int32(), C.c_int32(), C.c_int32()
-    _ck(lib().sph_get_launch_config(ctx, C.byref(a), C.byref(b), C.byref(w)),
+    a, b, w, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _ck(lib().sph_get_launch_config(ctx, C.byref(a), C.byref(b), C.byref(w), C.byref(d)),
         "sph_get_launch_config")
-    return {"block_density": a.value, "block_forces": b.value, "search_warps": w.value}
+    return {"block_density": a.value, "block_forces": b.value, "search_warps": w.value,
+            "search_depth": d.value}
 
 
 def sph_checkpoint_bytes(ctx) -> int:
@@ -336,9 +339,11 @@ def _nbytes(a) -> int:
     return int(a.numel() * a.element_size())
 
 
-def sph_set_launch_config(ctx, block_density: int, block_forces: int, search_warps: int):
+def sph_set_launch_config(ctx, block_density: int, block_forces: int, search_warps: int,
+                          search_depth: int = 512):
     _ck(lib().sph_set_launch_config(ctx, int(block_density), int(block_forces),
-                                    int(search_warps)), "sph_set_launch_config")
+                                    int(search_warps), int(search_depth)),
+        "sph_set_launch_config")
 
 
 def sph_destroy(ctx):

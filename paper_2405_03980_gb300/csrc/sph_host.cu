@@ -691,6 +691,7 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   c->lc.block_density = 128;
   c->lc.block_forces = 128;
   c->lc.search_warps = 4;
+  c->lc.search_depth = 512;
   c->lc.any_literal = false;
   c->lc.any_collision = false;
   c->lc.any_filter = false;
@@ -1100,19 +1101,24 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
   }
   const int cand[3] = {64, 128, 256};   // pair pass
   const int dcand[3] = {32, 64, 128};   // density pass
-  // neighbour search: warp per cell with 2, 4 or 8 cells per block, or
-  // (0) thread per particle; both write the same masks and tables
-  const int wcand[4] = {2, 4, 8, 0};
+  // neighbour search: warp per cell with 2, 4 or 8 cells per block and a
+  // segment depth of 256 or 512 candidates, or (0) thread per particle; all
+  // write the same masks and tables
+  const int wcand[7] = {2, 4, 8, 2, 4, 8, 0};
+  const int scand[7] = {256, 256, 256, 512, 512, 512, 512};
   float best[3] = {INFINITY, INFINITY, INFINITY};
   LaunchCfg pick = c->lc;
-  // trials 0-3: mapping and shape of the neighbour search (timed alone);
-  // 4-6: density block size (timed with the search before it, which rebuilds
-  // the lists it compacts); 7-9: pair-pass block size
-  for (int trial = 0; trial < 10 && st == SPH_OK; ++trial) {
-    const int kind = trial < 4 ? 0 : (trial < 7 ? 1 : 2);
-    const int opt = trial < 4 ? trial : (trial < 7 ? trial - 4 : trial - 7);
+  // trials 0-6: mapping and shape of the neighbour search (timed alone);
+  // 7-9: density block size (timed with the search before it, which rebuilds
+  // the lists it compacts); 10-12: pair-pass block size
+  for (int trial = 0; trial < 13 && st == SPH_OK; ++trial) {
+    const int kind = trial < 7 ? 0 : (trial < 10 ? 1 : 2);
+    const int opt = trial < 7 ? trial : (trial < 10 ? trial - 7 : trial - 10);
     LaunchCfg saved = c->lc;
-    if (kind == 0) c->lc.search_warps = wcand[opt];
+    if (kind == 0) {
+      c->lc.search_warps = wcand[opt];
+      c->lc.search_depth = scand[opt];
+    }
     if (kind == 1) c->lc.block_density = dcand[opt];
     if (kind == 2) c->lc.block_forces = cand[opt];
     cudaEventRecord(e0, s);
@@ -1128,13 +1134,19 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
       st = SPH_ERR_CUDA;
     if (ms < best[kind]) {
       best[kind] = ms;
-      if (kind == 0) pick.search_warps = c->lc.search_warps;
+      if (kind == 0) {
+        pick.search_warps = c->lc.search_warps;
+        pick.search_depth = c->lc.search_depth;
+      }
       if (kind == 1) pick.block_density = c->lc.block_density;
       if (kind == 2) pick.block_forces = c->lc.block_forces;
     }
     c->lc = saved;
     // the density trials must see the chosen search shape
-    if (kind == 0 && trial == 3) c->lc.search_warps = pick.search_warps;
+    if (kind == 0 && trial == 6) {
+      c->lc.search_warps = pick.search_warps;
+      c->lc.search_depth = pick.search_depth;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1158,11 +1170,12 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
 }
 
 sph_status sph_get_launch_config(const sph_ctx* c, int32_t* block_density, int32_t* block_forces,
-                                 int32_t* search_warps) {
+                                 int32_t* search_warps, int32_t* search_depth) {
   if (!c) return SPH_ERR_ARG;
   if (block_density) *block_density = c->lc.block_density;
   if (block_forces) *block_forces = c->lc.block_forces;
   if (search_warps) *search_warps = c->lc.search_warps;
+  if (search_depth) *search_depth = c->lc.search_depth;
   return SPH_OK;
 }
 
@@ -1175,17 +1188,19 @@ const char* sph_stage_name(int32_t stage) {
 int32_t sph_launches_per_step(const sph_ctx* c) { return c ? c->launches_per_step : 0; }
 
 sph_status sph_set_launch_config(sph_ctx* c, int32_t block_density, int32_t block_forces,
-                                 int32_t search_warps) {
+                                 int32_t search_warps, int32_t search_depth) {
   if (!c) return SPH_ERR_ARG;
   const bool bd = block_density == 32 || block_density == 64 || block_density == 128;
   const bool bf = block_forces == 64 || block_forces == 128 || block_forces == 256;
   const bool sw = search_warps == 0 || search_warps == 2 || search_warps == 4 ||
                   search_warps == 8;
-  if (!bd || !bf || !sw) return SPH_ERR_ARG;
+  const bool sd = search_depth == 256 || search_depth == 512;
+  if (!bd || !bf || !sw || !sd) return SPH_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   c->lc.block_density = block_density;
   c->lc.block_forces = block_forces;
   c->lc.search_warps = search_warps;
+  c->lc.search_depth = search_depth;
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {
       cudaGraphExecDestroy(c->graph[g]);

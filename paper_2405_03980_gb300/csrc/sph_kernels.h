@@ -14,6 +14,7 @@ struct LaunchCfg {
   int block_forces;      // threads per block of the pair pass
   int search_warps;      // warps (cells) per block of the neighbour search; 0: one
                          // thread per particle instead
+  int search_depth;      // candidates per staged segment of the warp search (256, 512)
   bool any_literal;      // some instance uses the literal F_sn (SPH_SN_LITERAL)
   bool any_collision;    // some instance uses the collision model (SPH_COLLISION)
   bool any_filter;       // some instance uses the pressure filter (SPH_PFILTER)

@@ -26,14 +26,16 @@
 namespace sphgb {
 namespace {
 
-constexpr int kSeg = 512;                      // candidates staged at a time
-constexpr int kSegChunks = kSeg / 32;
+// kSeg, the segment depth: candidates staged in shared memory at a time (256
+// or 512, chosen by the autotuner; a cell of the 2.6 dx grid has about 470)
 constexpr int kMaskRow = 36;  // mask words of one chunk: 4 targets per 16-byte store, and
                               // lane t reading word t of chunk k hits bank (4k + t) % 32
 constexpr int kMaxSearchWarps = 8;
-static_assert(kMaxCand % kSeg == 0, "segments tile the candidate table");
 
+template <int kSeg>
 struct WarpSmem {
+  static_assert(kMaxCand % kSeg == 0, "segments tile the candidate table");
+  static constexpr int kSegChunks = kSeg / 32;
   uint32_t ent[kSeg];                 // candidate index | cell-displacement code
   float4 tgt[32];                     // records of the current targets
   alignas(16) uint32_t mask[kSegChunks * kMaskRow];  // hit mask of (chunk, target)
@@ -51,13 +53,13 @@ __device__ __forceinline__ float pair_r2(float dx, float dy, float dz) {
 
 // rec: per sorted particle (x, y, z, species); mixed: the offset inside the
 // cell, FP64 form: the FP32-rounded absolute position.
-template <bool kMixed>
+template <bool kMixed, int kSeg>
 __global__ void __launch_bounds__(32 * kMaxSearchWarps, 3)
 k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restrict__ inst,
               CellWs cw, NbrWs nw, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  WarpSmem<kSeg>& sm = reinterpret_cast<WarpSmem<kSeg>*>(smem_raw)[threadIdx.x >> 5];
   const InstDev& P = inst[blockIdx.y];
   const int64_t l = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (l >= (int64_t)P.nx * P.ny * P.nz) return;
@@ -295,19 +297,26 @@ k_cell_search_tpp(int64_t n, const float4* __restrict__ rec,
   nw.count[i] = active ? hits : 0u;
 }
 
-size_t search_smem(int warps) { return sizeof(WarpSmem) * (size_t)warps; }
+size_t search_smem(int warps, int seg) {
+  return (seg == 256 ? sizeof(WarpSmem<256>) : sizeof(WarpSmem<512>)) * (size_t)warps;
+}
 
 }  // namespace
 
 int search_max_warps() { return kMaxSearchWarps; }
 
 cudaError_t prepare_search_kernels() {
-  const int bytes = (int)search_smem(kMaxSearchWarps);
-  cudaError_t e = cudaFuncSetAttribute(k_cell_search<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_cell_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  const void* fns[4] = {(const void*)k_cell_search<true, 256>,
+                        (const void*)k_cell_search<false, 256>,
+                        (const void*)k_cell_search<true, 512>,
+                        (const void*)k_cell_search<false, 512>};
+  for (int k = 0; k < 4; ++k) {
+    const int bytes = (int)search_smem(kMaxSearchWarps, k < 2 ? 256 : 512);
+    const cudaError_t e =
+        cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
@@ -327,11 +336,19 @@ cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
   int warps = lc.search_warps;
   if (warps < 1 || warps > kMaxSearchWarps) warps = 4;
   const dim3 grid((unsigned)((max_cells + warps - 1) / warps), (unsigned)n_inst);
-  const size_t smem = search_smem(warps);
-  if (mixed_form)
-    k_cell_search<true><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
-  else
-    k_cell_search<false><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+  const int seg = lc.search_depth == 256 ? 256 : 512;
+  const size_t smem = search_smem(warps, seg);
+  if (seg == 256) {
+    if (mixed_form)
+      k_cell_search<true, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+    else
+      k_cell_search<false, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+  } else {
+    if (mixed_form)
+      k_cell_search<true, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+    else
+      k_cell_search<false, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -100,8 +100,9 @@ class Simulation:
         return B.sph_get_launch_config(self.ctx)
 
     def set_launch_config(self, block_density: int = 128, block_forces: int = 128,
-                          search_warps: int = 4):
-        B.sph_set_launch_config(self.ctx, block_density, block_forces, search_warps)
+                          search_warps: int = 4, search_depth: int = 512):
+        B.sph_set_launch_config(self.ctx, block_density, block_forces, search_warps,
+                                search_depth)
 
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)

@@ -356,20 +356,27 @@ def test_search_mappings_give_identical_results(precision):
                       box_lo=(rag.params["box_lo"][0], rag.params["box_lo"][1], -3.0),
                       box_hi=(rag.params["box_hi"][0], rag.params["box_hi"][1], 10.0))
     for c in (synth.workload("cyl_8960", seed=7), rag):
-        a = sim_of(c, precision=precision)
-        b = sim_of(c, precision=precision)
-        b.set_launch_config(64, 128, 0)
-        assert b.launch_config()["search_warps"] == 0
+        a = sim_of(c, precision=precision)  # 4 cells per block, depth 512
+        others = [sim_of(c, precision=precision) for _ in range(2)]
+        others[0].set_launch_config(64, 128, 0)         # thread per particle
+        others[1].set_launch_config(32, 256, 2, 256)    # 2 cells per block, depth 256
+        assert others[0].launch_config()["search_warps"] == 0
+        assert others[1].launch_config()["search_depth"] == 256
         for _ in range(2):
             a.step(2)
-            b.step(2)
-            sa, sb = a.state_arrays(), b.state_arrays()
-            for f in sa:
-                assert np.array_equal(sa[f], sb[f]), f
+            sa = a.state_arrays()
+            for b in others:
+                b.step(2)
+                sb = b.state_arrays()
+                for f in sa:
+                    assert np.array_equal(sa[f], sb[f]), f
         oa, na = a.neighbors()
-        ob, nb = b.neighbors()
-        assert np.array_equal(oa, ob) and np.array_equal(na, nb)
+        for b in others:
+            ob, nb = b.neighbors()
+            assert np.array_equal(oa, ob) and np.array_equal(na, nb)
         with pytest.raises(B.SphError):
-            b.set_launch_config(64, 128, 3)
-        a.close()
-        b.close()
+            others[0].set_launch_config(64, 128, 3)
+        with pytest.raises(B.SphError):
+            others[0].set_launch_config(64, 128, 4, 384)
+        for s_ in [a] + others:
+            s_.close()
