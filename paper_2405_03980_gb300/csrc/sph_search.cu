@@ -37,9 +37,45 @@ struct WarpSmem {
   static_assert(kMaxCand % kSeg == 0, "segments tile the candidate table");
   static constexpr int kSegChunks = kSeg / 32;
   uint32_t ent[kSeg];                 // candidate index | cell-displacement code
-  float4 tgt[32];                     // records of the current targets
+  // coordinates of the current targets by axis, so that two consecutive
+  // targets load as one 8-byte pair
+  alignas(16) float tx[32];
+  alignas(16) float ty[32];
+  alignas(16) float tz[32];
   alignas(16) uint32_t mask[kSegChunks * kMaskRow];  // hit mask of (chunk, target)
 };
+
+// Packed FP32 pairs (Blackwell f32x2): one instruction, two independent
+// operations, each rounded as its scalar counterpart.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_splat(float a) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ void f2_split(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 __device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
   if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
@@ -111,7 +147,9 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
     const uint32_t i = tb + lane;
     float4 mine = make_float4(0.f, 0.f, 0.f, 3.f);
     if (lane < nt) mine = rec[i];
-    sm.tgt[lane] = mine;
+    sm.tx[lane] = mine.x;
+    sm.ty[lane] = mine.y;
+    sm.tz[lane] = mine.z;
     const bool active = lane < nt && mine.w != 3.f;  // outer-wall particles keep no list
     if (__ballot_sync(~0u, active) == 0u) {
       if (lane < nt) nw.count[i] = 0u;
@@ -157,10 +195,10 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
           else if (z2 >= P.nz) c.z += P.Hzf;
         }
         // the pair vector e + (o_t - c) of the mixed form is the one every
-        // later use of the entry recomputes; four targets per round keep
-        // four independent chains in flight ahead of their ballots
-        auto hit = [&](const float4& o) {
-          float dx = o.x - c.x, dy = o.y - c.y, dz = o.z - c.z;
+        // later use of the entry recomputes; two targets per packed FP32
+        // instruction, four per round, ahead of their ballots
+        auto hit = [&](uint32_t t) {
+          float dx = sm.tx[t] - c.x, dy = sm.ty[t] - c.y, dz = sm.tz[t] - c.z;
           if (kMixed) {
             dx = ex + dx;
             dy = ey + dy;
@@ -168,11 +206,29 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
           }
           return valid && pair_r2(dx, dy, dz) < cut2;
         };
+        const f2 CX = f2_splat(c.x), CY = f2_splat(c.y), CZ = f2_splat(c.z);
+        const f2 EX = f2_splat(ex), EY = f2_splat(ey), EZ = f2_splat(ez);
+        auto hit2 = [&](uint32_t t, bool& h0, bool& h1) {  // targets t, t + 1 (t even)
+          f2 dx = f2_sub(*reinterpret_cast<const f2*>(sm.tx + t), CX);
+          f2 dy = f2_sub(*reinterpret_cast<const f2*>(sm.ty + t), CY);
+          f2 dz = f2_sub(*reinterpret_cast<const f2*>(sm.tz + t), CZ);
+          if (kMixed) {
+            dx = f2_add(EX, dx);
+            dy = f2_add(EY, dy);
+            dz = f2_add(EZ, dz);
+          }
+          const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+          float r0, r1;
+          f2_split(r2, r0, r1);
+          h0 = valid && r0 < cut2;
+          h1 = valid && r1 < cut2;
+        };
         uint32_t* mk = sm.mask + k * kMaskRow;
         uint32_t t = 0;
         for (; t + 4 <= nt; t += 4) {
-          const bool h0 = hit(sm.tgt[t]), h1 = hit(sm.tgt[t + 1]);
-          const bool h2 = hit(sm.tgt[t + 2]), h3 = hit(sm.tgt[t + 3]);
+          bool h0, h1, h2, h3;
+          hit2(t, h0, h1);
+          hit2(t + 2, h2, h3);
           const uint32_t m0 = __ballot_sync(~0u, h0), m1 = __ballot_sync(~0u, h1);
           const uint32_t m2 = __ballot_sync(~0u, h2), m3 = __ballot_sync(~0u, h3);
           if (lane == 0) {
@@ -180,7 +236,7 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
           }
         }
         for (; t < nt; ++t) {
-          const uint32_t m0 = __ballot_sync(~0u, hit(sm.tgt[t]));
+          const uint32_t m0 = __ballot_sync(~0u, hit(t));
           if (lane == 0) mk[t] = m0;
         }
       }
