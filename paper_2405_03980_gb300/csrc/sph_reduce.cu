@@ -47,19 +47,22 @@ struct Fp64View {
     return b.vel[i].w * inv_m;
   }
   __device__ __forceinline__ double pres(int64_t i) const { return f.P[i]; }
-  // The wall torque of particle i, if it is not zero (it is zero for every
-  // particle without a wall neighbour, walls included); the test looks at
-  // the bits, so that no FP64 instruction is spent on the zeros.
-  __device__ __forceinline__ bool tw_nonzero(int64_t i, double* v) const {
-    const dvec4 p = f.tw[i];
+  // The wall torque record of particle i, whether it is not zero (it is zero
+  // for every particle without a wall neighbour, walls included; the test
+  // looks at the bits, so that no FP64 instruction is spent on the zeros),
+  // and its value.
+  typedef dvec4 TwRec;
+  __device__ __forceinline__ TwRec tw(int64_t i) const { return f.tw[i]; }
+  __device__ __forceinline__ static bool tw_nonzero(const TwRec& p) {
     const unsigned long long any = ((unsigned long long)__double_as_longlong(p.x) |
                                     (unsigned long long)__double_as_longlong(p.y) |
                                     (unsigned long long)__double_as_longlong(p.z)) << 1;
-    if (any == 0ull) return false;  // +0 or -0 in every component
+    return any != 0ull;  // not +0 or -0 in every component
+  }
+  __device__ __forceinline__ static void tw_value(const TwRec& p, double* v) {
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
-    return true;
   }
 };
 
@@ -97,14 +100,16 @@ struct MixView {
     return 1.0 / rho;
   }
   __device__ __forceinline__ double pres(int64_t i) const { return (double)f.P[i]; }
-  // The wall torque of particle i, if it is not zero (see Fp64View).
-  __device__ __forceinline__ bool tw_nonzero(int64_t i, double* v) const {
-    const float4 p = f.tw[i];
-    if (p.x == 0.f && p.y == 0.f && p.z == 0.f) return false;
+  // The wall torque record of particle i (see Fp64View).
+  typedef float4 TwRec;
+  __device__ __forceinline__ TwRec tw(int64_t i) const { return f.tw[i]; }
+  __device__ __forceinline__ static bool tw_nonzero(const TwRec& p) {
+    return ((__float_as_uint(p.x) | __float_as_uint(p.y) | __float_as_uint(p.z)) << 1) != 0u;
+  }
+  __device__ __forceinline__ static void tw_value(const TwRec& p, double* v) {
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
-    return true;
   }
 };
 
@@ -152,22 +157,33 @@ k_wall_torque_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V,
   double v[3] = {0.0, 0.0, 0.0};
   // walls carry a zero wall torque, as does every particle without a wall
   // neighbour: only the others are added (adding a zero changes no sum).
-  // Four records per round are loaded before they are added, in the same
-  // order as one at a time.
+  // Four records per round are all loaded (an index past the chunk reads
+  // its first record and is not added) before any is tested, then added in
+  // the same order as one at a time.
   for (int64_t i0 = r.begin + threadIdx.x; i0 < r.end; i0 += 4 * kRedThreads) {
-    double t[4][3];
-    bool nz[4];
+    typename View::TwRec rec[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t i = i0 + (int64_t)u * kRedThreads;
-      nz[u] = i < r.end && V.tw_nonzero(i, t[u]);
+      rec[u] = V.tw(i < r.end ? i : r.begin);
     }
+    // the tests on the integer pipe give a mask of the records to add; the
+    // conversions and FP64 adds run for those only (a few in a hundred)
+    uint32_t nz = 0u;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!nz[u]) continue;
-      v[0] += t[u][0];
-      v[1] += t[u][1];
-      v[2] += t[u][2];
+      const int64_t i = i0 + (int64_t)u * kRedThreads;
+      if (i < r.end && View::tw_nonzero(rec[u])) nz |= 1u << u;
+    }
+    while (nz != 0u) {
+      const int u = __ffs(nz) - 1;
+      nz &= nz - 1u;
+      const typename View::TwRec p = u == 0 ? rec[0] : (u == 1 ? rec[1] : (u == 2 ? rec[2] : rec[3]));
+      double t[3];
+      View::tw_value(p, t);
+      v[0] += t[0];
+      v[1] += t[1];
+      v[2] += t[2];
     }
   }
   block_sum<3>(v, sh);
