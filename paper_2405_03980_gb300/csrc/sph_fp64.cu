@@ -188,6 +188,34 @@ __device__ __forceinline__ int z_wrap(uint32_t ent, int cz_i, int nz) {
   return (cz_i == 0 && cz == 2u) ? 1 : ((cz_i == nz - 1 && cz == 0u) ? -1 : 0);
 }
 
+// ------------------------------------------------- square roots of distances
+
+// sqrt(x) for the pair distances of the density pass, with few FP64
+// instructions (the FP64 pipe bounds that pass).  The FP32 hardware
+// estimate of 1/sqrt(x) is taken on the top 20 mantissa bits of x;
+// operand and estimate move between the formats by integer operations on
+// their bits, so no conversion instruction is issued.  One step of the
+// third-order iteration y <- y + y e (1/2 + 3e/8), e = 1 - x y^2 (the first
+// terms of the binomial series (1 - e)^(-1/2) = 1 / (y sqrt(x))) takes the
+// estimate's relative error, below 2^-19, to about (5/16) |e|^3 < 2^-55:
+// x times the refined 1/sqrt(x) is within about an ulp of sqrt(x).  An
+// argument whose FP32 form would not be normal (zero, tiny, huge) takes
+// CUDA's sqrt.
+__device__ __forceinline__ bool fp32_range(int hi) {
+  return hi >= 0x38100000 && hi < 0x47F00000;  // 2^-126 <= x < 2^128
+}
+__device__ __forceinline__ double rsqrt_seed_step(double x, int hi) {
+  const float xf = __int_as_float((int)(((unsigned)hi - (896u << 20)) << 3));
+  const unsigned yb = (unsigned)__float_as_int(rsqrtf(xf));
+  const double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+__device__ __forceinline__ double sqrt_dist(double x) {
+  const int hi = __double2hiint(x);
+  return fp32_range(hi) ? x * rsqrt_seed_step(x, hi) : sqrt(x);
+}
+
 // -------------------------------------------------------------------- density
 
 __device__ __forceinline__ double ipow(double x, int e) {
@@ -229,6 +257,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
     const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
     const double mD_s = P.m_s * P.aD, mD_n = P.m_n * P.aD;
+    const long long cut2_bits = __double_as_longlong(P.cut2);
     rho = m_i * P.aD;  // self term W(0)
     uint32_t e[4];
     for (uint32_t m; (m = mk.next(e)) != 0u;) {
@@ -249,11 +278,13 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
           }
           const double r2 =
               __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-          const bool keep = r2 < P.cut2;
+          // r2 < (2h)^2 on the integer pipe: r2 is a sum of squares (+0 or
+          // positive, or NaN), and such doubles order as their bit patterns
+          const bool keep = __double_as_longlong(r2) < cut2_bits;
           out.push(e[u], keep);  // index and cell-displacement code
           if (keep) {
             // m_j W(r) = (m_j aD) t^4 (2q + 1), t = 1 - q/2, q = r / h
-            const double r = sqrt(r2);
+            const double r = sqrt_dist(r2);
             const double t1 = fma(-half_inv_h, r, 1.0);
             const double t2 = t1 * t1;
             const double mD = inviscid(pj[u].w) ? mD_s : mD_n;
