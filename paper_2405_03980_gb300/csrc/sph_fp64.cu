@@ -488,29 +488,34 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       const double al = base + aT;
       const double alz = hproj ? base : al;
       const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
-      double pfx = al * dx + bu * ux;
-      double pfy = al * dy + bu * uy;
-      double pfz = alz * dz + bu * uz;
+      // The pair force al r_ij + bu u_ij (+ bN v_ij) goes into the sums one
+      // fused multiply-add per term, and so does the spin torque
+      // -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij), whose factor
+      // -1/2 (exact) is applied to the sums: the FP64 pipe bounds this loop.
+      const double cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
+      fx = fma(al, dx, fma(bu, ux, fx));
+      fy = fma(al, dy, fma(bu, uy, fy));
+      fz = fma(alz, dz, fma(bu, uz, fz));
       if ((kOpt & kOptLiteral) && literal) {  // coefficient bN of v_ij
-        pfx += bN * vx;
-        pfy += bN * vy;
-        pfz += bN * vz;
+        fx = fma(bN, vx, fx);
+        fy = fma(bN, vy, fy);
+        fz = fma(bN, vz, fz);
       }
-      fx += pfx;
-      fy += pfy;
-      fz += pfz;
-      // spin torque -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij); the
-      // factor -1/2 (exact) is applied to the sums
-      const double qx = bu * (dy * uz - dz * uy);
-      const double qy = bu * (dz * ux - dx * uz);
-      const double qz = bu * (dx * uy - dy * ux);
-      tx += qx;
-      ty += qy;
-      tz += qz;
+      tx = fma(bu, cx, tx);
+      ty = fma(bu, cy, ty);
+      tz = fma(bu, cz, tz);
       if (is_wall(pj.w)) {  // torque exerted by the wall on particle i
-        wx += fma(-0.5, qx, pi.y * pfz - pi.z * pfy);
-        wy += fma(-0.5, qy, pi.z * pfx - pi.x * pfz);
-        wz += fma(-0.5, qz, pi.x * pfy - pi.y * pfx);
+        double pfx = al * dx + bu * ux;
+        double pfy = al * dy + bu * uy;
+        double pfz = alz * dz + bu * uz;
+        if ((kOpt & kOptLiteral) && literal) {
+          pfx += bN * vx;
+          pfy += bN * vy;
+          pfz += bN * vz;
+        }
+        wx += fma(-0.5, bu * cx, pi.y * pfz - pi.z * pfy);
+        wy += fma(-0.5, bu * cy, pi.z * pfx - pi.x * pfz);
+        wz += fma(-0.5, bu * cz, pi.x * pfy - pi.y * pfx);
       }
     }
   }
