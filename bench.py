@@ -80,9 +80,9 @@ DRAM_BYTES_PER_PARTICLE = {
                                 "sph_internal.h": "bde2088e17d1f86d"}),
     "k_forces_mixed": (414.6, {"sph_mixed.cu": "a2f6a0d29480f7cb",
                                "sph_internal.h": "bde2088e17d1f86d"}),
-    "k_density_fp64": (640.2, {"sph_fp64.cu": "fe73034fa3defc15",
+    "k_density_fp64": (640.1, {"sph_fp64.cu": "5710bc8e809895dd",
                                "sph_internal.h": "bde2088e17d1f86d"}),
-    "k_forces_fp64": (511.6, {"sph_fp64.cu": "fe73034fa3defc15",
+    "k_forces_fp64": (511.5, {"sph_fp64.cu": "5710bc8e809895dd",
                               "sph_internal.h": "bde2088e17d1f86d"}),
 }
 
