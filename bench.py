@@ -14,7 +14,10 @@ advances its own replica of the cylinder (no exchange: weak scaling).
 
 `--impl reference` times the CPU FP64 oracle (O(N^2), all host cores) on a
 bounded sample of the same workload: a compact cluster of fluid particles
-whose density, pressure and pair forces are evaluated against all N particles.
+whose density, pressure and pair forces are evaluated against all N particles;
+the per-row costs give the time of a full step (N density rows and N_fluid
+force rows), and value = N / that time.  The cpu_baseline leg of the GPU arm
+reports the same quantity.
 """
 from __future__ import annotations
 
@@ -36,15 +39,28 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s at 19.6M particles"
 UNIT = "particle-steps/s"
 
-# FP64 operations per neighbour pair of the pair pass, counted from the kernel
-# source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1); the
-# work of one force launch is this times the number of fluid neighbour pairs.
+# Algorithmic work is counted per UNIQUE interacting pair with at least one
+# fluid particle: a fluid-fluid pair once (the gather evaluates it from both
+# sides; that second evaluation is implementation work, not algorithmic), a
+# fluid-wall pair once.  unique = (ordered fluid-row pairs + fluid-wall
+# pairs) / 2; the ordered count comes from sph_diagnostics, the fluid-wall
+# count from the host (fluid_wall_pairs).
+# FP32/FP64 operations per pair of the pair pass, counted from the kernel
+# source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1).
 FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # mixed adds cell offsets and Kahan
-# Density pass: operations per neighbour pair of the density sum (pair vector,
-# r^2, sqrt, Wendland W, accumulation; the mixed form adds the cell offsets
-# and the Kahan update).  The candidate tests that find the neighbours are
-# not counted as algorithmic work.
+# Density pass: operations per pair of the density sum (pair vector, r^2,
+# sqrt, Wendland W, accumulation; the mixed form adds the cell offsets and
+# the Kahan update).  W_ij = W_ji, so a pair is algorithmic work once.  The
+# candidate tests that find the neighbours, rejected ones included, are not
+# algorithmic work.
 DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
+# Algorithmic DRAM bytes per particle of the two neighbour passes: each must
+# read a particle's own record once and write its results once; neighbour
+# records are re-reads that a good kernel serves on chip.  Density: the
+# position record in, rho and P (and V, P/rho^2 for the pair pass) out.  Pair
+# pass: position, velocity, spin, V and P/rho^2 in, a and alpha out.
+ALGO_BYTES_PER_PARTICLE = {"k_density_mixed": 4 + 16 + 16, "k_density_fp64": 32 + 32,
+                           "k_forces_mixed": 4 + 48 + 32, "k_forces_fp64": 96 + 64}
 # Optional steps of Algorithm 1 (--extras).  The pressure filter streams each
 # fluid/inner-wall row's neighbour list and the kernel shapes the density
 # pass stored beside it (4 B + 4 B mixed, 4 B + 8 B FP64 per neighbour) and
@@ -62,10 +78,13 @@ FILTER_FLOPS_PER_PAIR = {"fp64": 4, "mixed": 3}
 COLLISION_FLOPS_PER_PAIR = 1
 EXTRAS = {"pfilter": 128, "collision": 256}
 # Neighbour search: FP32 operations per candidate test (pair vector, r^2; the
-# mixed form adds the cell displacement).  Its work is the candidate tests of
-# the 27-cell stencil of every particle that keeps a list (fluid and inner
-# wall), counted on the host from the initial positions (candidate_tests).
+# mixed form adds the cell displacement).  Its implementation work is the
+# candidate tests of the 27-cell stencil of every particle that keeps a list
+# (fluid and inner wall), counted on the host from the initial positions
+# (candidate_tests); reported beside the roofline, not as algorithmic work.
+# Its algorithmic work is reading each particle's position record once.
 SEARCH_FLOPS_PER_TEST = {"fp64": 8, "mixed": 11}
+SEARCH_ALGO_BYTES_PER_PARTICLE = {"fp64": 16, "mixed": 16}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per particle of
 # one launch, from the ncu captures summarised in profiles/ (2,525,900-particle
@@ -99,34 +118,36 @@ STREAM_BYTES_PER_PARTICLE = {
 }
 
 
-def step_roofline(stage_ms, form, n_particles, n_cells, pairs, tests, peak_alu, hbm_gbs,
+def step_roofline(stage_ms, form, n_particles, n_cells, pairs, unique, peak_alu, hbm_gbs,
                   extras=()):
     """Lower bound of one step: every stage at its own roof (the streaming
-    stages at the measured HBM bandwidth with their algorithmic bytes, the
-    search, density and pair passes at the measured FMA rate with their
-    algorithmic flops), summed, and the fraction of it the measured step
-    reaches."""
+    stages and the neighbour search at the measured HBM bandwidth with their
+    algorithmic bytes, the density and pair passes at the measured FMA rate
+    with their algorithmic flops per unique pair), summed, and the fraction of
+    it the measured step reaches.  pairs: ordered fluid-row pairs (what the
+    filter streams); unique: unique pairs with a fluid particle."""
     bound = {}
     for st, b in STREAM_BYTES_PER_PARTICLE.items():
         by = b[form] * n_particles + (8 * n_cells if st == "cell_scan" else 0)
         bound[st] = by / (hbm_gbs * 1e9) * 1e3
-    flops = {"cell_search": SEARCH_FLOPS_PER_TEST[form] * tests,
-             "density": DENSITY_FLOPS_PER_PAIR[form] * pairs,
-             "forces": force_flops(form, extras) * pairs}
+    bound["cell_search"] = SEARCH_ALGO_BYTES_PER_PARTICLE[form] * n_particles / (hbm_gbs * 1e9) * 1e3
+    flops = {"density": DENSITY_FLOPS_PER_PAIR[form] * unique,
+             "forces": force_flops(form, extras) * unique}
     if "pfilter" in extras:
         by = filter_bytes(form, pairs, n_particles)
         fl = FILTER_FLOPS_PER_PAIR[form] * pairs
         bound["pressure_filter"] = max(by / (hbm_gbs * 1e9), fl / (peak_alu[form] * 1e12)) * 1e3
     for st, fl in flops.items():
-        pk = peak_alu["mixed"] if st == "cell_search" else peak_alu[form]  # search is FP32
-        bound[st] = fl / (pk * 1e12) * 1e3
+        bound[st] = fl / (peak_alu[form] * 1e12) * 1e3
     tb = sum(bound.values())
     tm = sum(stage_ms.values())
     return {"bound_ms": tb, "measured_ms": tm, "frac": tb / tm,
             "per_stage_bound_ms": bound, "hbm_gbs": hbm_gbs,
             "note": "sum over stages of algorithmic bytes / measured HBM bandwidth or "
-                    "algorithmic flops / measured FMA rate; measured_ms sums the per-stage "
-                    "event times"}
+                    "algorithmic flops (per unique pair) / measured FMA rate; the neighbour "
+                    "search counts only its position reads (its candidate tests, rejected "
+                    "ones included, are not algorithmic work); measured_ms sums the "
+                    "per-stage event times"}
 
 
 def hbm_peak():
@@ -145,6 +166,11 @@ def force_flops(form, extras=()):
     return FORCE_FLOPS_PER_PAIR[form] + (COLLISION_FLOPS_PER_PAIR if "collision" in extras else 0)
 
 
+def ratio(traffic, algorithmic):
+    """Measured DRAM bytes over algorithmic bytes (None without a capture)."""
+    return None if traffic is None or not algorithmic else traffic / algorithmic
+
+
 def measured_traffic(kernel, n_particles):
     """Per-launch DRAM bytes of kernel at n_particles, or None when no capture
     matches the current sources."""
@@ -157,6 +183,35 @@ def measured_traffic(kernel, n_particles):
         if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
             return None
     return per * n_particles
+
+
+def fluid_wall_pairs(insts):
+    """Unique (fluid, wall) neighbour pairs, r < 2h with the periodic z image,
+    counted on the host from the initial positions (only fluid particles
+    within reach of the wall take part)."""
+    from scipy.spatial import cKDTree
+    total = 0
+    for c in insts:
+        p = c.params
+        reach = 2.0 * p["h"]
+        rxy = np.hypot(c.pos[:, 0], c.pos[:, 1])
+        wall = c.species >= 2
+        if not wall.any():
+            continue
+        near = (c.species < 2) & (rxy > rxy[wall].min() - reach - 1.0)
+        ext = float(np.abs(c.pos[:, :2]).max()) + 4.0 * reach
+        shift = np.array([ext, ext, 0.0])
+        H = float(p["box_hi"][2] - p["box_lo"][2])
+        box = [4.0 * ext, 4.0 * ext, H] if p.get("periodic_z", 1) else None
+        fpos = c.pos[near] + shift
+        wpos = c.pos[wall] + shift
+        if box:
+            fpos[:, 2] %= H
+            wpos[:, 2] %= H
+        tf = cKDTree(fpos, boxsize=box)
+        tw = cKDTree(wpos, boxsize=box)
+        total += int(tf.count_neighbors(tw, np.nextafter(reach, 0.0)))
+    return total
 
 
 def candidate_tests(insts):
@@ -305,8 +360,10 @@ class ClockSampler:
 def oracle_sample(c, target_s: float = 15.0, n_sample: int = 0):
     """Bounded oracle sample: a compact cluster S of fluid particles near
     mid-radius and every particle R within 2h (+1 dx) of its bounding box.
-    One sample step = oracle density+pressure for R and pair forces for S,
-    each evaluated against all N particles (the oracle is O(N) per row)."""
+    One sample step = oracle density+pressure for the rows R and pair forces
+    for the rows S, each row evaluated against all N particles (the oracle is
+    O(N) per row), timed separately so that a full step can be estimated
+    from the per-row costs (full_step_seconds)."""
     import oracle
     p = oracle.make_params(c.params)
     fluid = np.nonzero(c.species < 2)[0]
@@ -322,30 +379,46 @@ def oracle_sample(c, target_s: float = 15.0, n_sample: int = 0):
         return S, np.nonzero(inside)[0]
 
     def run(S, R):
-        t = time.perf_counter()
+        """Seconds per density row and per force row of one sample step."""
+        t0 = time.perf_counter()
         rho, P = oracle.density(p, c.pos, c.species, rows=R)
+        t1 = time.perf_counter()
         oracle.forces(p, c.pos, c.vel, c.spin, c.species, rho, P, rows=S)
-        return time.perf_counter() - t
+        t2 = time.perf_counter()
+        return (t1 - t0) / len(R), (t2 - t1) / len(S), t2 - t0
 
+    # at least 32 force rows per host thread, so that the rows keep every
+    # thread of the oracle's OpenMP loop busy and the per-row costs are
+    # throughput figures, independent of the sample's size
+    k_min = min(len(order), 32 * cores_used())
     if n_sample:
-        S, R = rows_for(n_sample)
-        return p, S, R, run, run(S, R)
-    # calibrate the cost per evaluated row on a small cluster, then size the
-    # cluster so that one sample step costs about target_s seconds
-    S, R = rows_for(32)
-    t = run(S, R)
-    rows_per_s = len(R) / max(t, 1e-4)
+        S, R = rows_for(max(n_sample, k_min))
+        return p, S, R, run
+    # calibrate the cost per evaluated row on the smallest cluster, then size
+    # the cluster so that one sample step costs about target_s seconds
+    S, R = rows_for(k_min)
+    t = run(S, R)[2]
+    rows_per_s = (len(R) + len(S)) / max(t, 1e-4)
     want = target_s * rows_per_s
-    k = 32
+    k = k_min
     while k < len(order):
         k2 = min(len(order), int(k * 1.5) + 1)
-        _, R2 = rows_for(k2)
-        if len(R2) > want:
+        S2, R2 = rows_for(k2)
+        if len(R2) + len(S2) > want:
             break
         k = k2
     S, R = rows_for(k)
-    t = run(S, R)
-    return p, S, R, run, t
+    return p, S, R, run
+
+
+def full_step_seconds(c, t_density_row, t_force_row):
+    """Oracle seconds for one whole step of instance c from the per-row costs:
+    a density row for every fluid and inner-wall particle (outer walls keep
+    rho0) and a force row for every fluid particle; the O(N) kick, drift and
+    wall placement are negligible beside these O(N) rows."""
+    n_density = int((c.species != 3).sum())
+    n_force = int((c.species < 2).sum())
+    return n_density * t_density_row + n_force * t_force_row
 
 
 def cores_used() -> int:
@@ -357,13 +430,18 @@ def cores_used() -> int:
 
 
 def cpu_baseline(c, n_sample=0):
-    _, S, R, run, _t = oracle_sample(c, target_s=10.0, n_sample=n_sample)
-    t = min(run(S, R) for _ in range(2))
-    return {"value": len(S) / t, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+    _, S, R, run = oracle_sample(c, target_s=10.0, n_sample=n_sample)
+    best = min((run(S, R) for _ in range(2)), key=lambda r: r[2])
+    td, tf, t = best
+    T = full_step_seconds(c, td, tf)
+    return {"value": c.n / T, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
             "sample": (f"{len(S)} fluid particles of the {c.n}-particle cylinder: oracle "
-                       f"density+pressure for the {len(R)} particles within 2h of them and "
-                       f"pair forces for the {len(S)}, each against all {c.n} particles "
-                       f"(O(N) per row); best of 2, {t:.2f} s per sample step")}
+                       f"density+pressure rows for the {len(R)} particles within 2h of them "
+                       f"({td * 1e3:.2f} ms per row) and pair-force rows for the {len(S)} "
+                       f"({tf * 1e3:.2f} ms per row), each row against all {c.n} particles; "
+                       f"best of 2 sample steps of {t:.2f} s; value = N / (N_density_rows x "
+                       f"t_density_row + N_fluid x t_force_row), a full step being "
+                       f"{T:.3g} s")}
 
 
 def run_reference(args, dist):
@@ -372,23 +450,30 @@ def run_reference(args, dist):
     # the oracle is O(N) per row: the sample is drawn from the largest instance
     c = max(load_workload(args.workload), key=lambda x: x.n)
     target = min(10.0, max(1.0, 90.0 / max(1, args.steps + args.warmup)))
-    _, S, R, run, _ = oracle_sample(c, target_s=target, n_sample=args.cpu_sample)
+    _, S, R, run = oracle_sample(c, target_s=target, n_sample=args.cpu_sample)
     for _ in range(args.warmup):
         run(S, R)
-    t0 = time.perf_counter()
+    full, wall = 0.0, 0.0
     for _ in range(args.steps):
-        run(S, R)
-    dt = time.perf_counter() - t0
-    v = len(S) * args.steps / dt
+        td, tf, t = run(S, R)
+        full += full_step_seconds(c, td, tf)
+        wall += t
+    v = c.n * args.steps / full
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "particles": c.n,
                        "sample_particles": int(len(S)), "sample_rows": int(len(R)),
+                       "ms_per_step": "wall time of one sample step; value is N over the "
+                                      "full-step time estimated from its per-row costs",
+                       "full_step_seconds": full / args.steps,
                        "l2": "inputs larger than L2 (not applicable on CPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": cores_used(),
-                             "sample": f"{len(S)} of {c.n} particles per step"},
+                             "sample": f"{len(S)} force rows and {len(R)} density rows of the "
+                                       f"{c.n}-particle cylinder per step, each row against "
+                                       f"all N particles, scaled to a full step by the "
+                                       f"per-row costs"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -507,16 +592,34 @@ def run_ours(args, dist):
              "mixed": B.sph_fma_peak(B.SPH_MIXED, 1 << 20)}
     roofs = {}
     tests = candidate_tests(insts)
+    fw = fluid_wall_pairs(insts)
+    census = {}
     for f in results:
         pr = results[f]["diag"]["n_pairs"]
+        uq = (pr + fw) // 2
+        census[f] = {"ordered_fluid_row_pairs": pr, "fluid_wall_pairs": fw,
+                     "unique_pairs": uq, "candidate_tests": tests}
         unit = "FP64" if f == "fp64" else "FP32"
-        stages = [("forces", f"k_forces_{f}", force_flops(f, extras), pr,
-                   "fluid neighbour pairs", unit),
-                  ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], pr,
-                   "fluid neighbour pairs", unit),
-                  ("cell_search", f"k_cell_search<{str(f == 'mixed').lower()}>",
-                   SEARCH_FLOPS_PER_TEST[f], tests, "candidate tests (initial positions)",
-                   "FP32")]
+        stages = [("forces", f"k_forces_{f}", force_flops(f, extras), uq,
+                   "unique pairs with a fluid particle", unit),
+                  ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], uq,
+                   "unique pairs with a fluid particle", unit)]
+        # the neighbour search: algorithmic work is its position reads
+        t = results[f]["stages"]["cell_search"]
+        kern = f"k_cell_search<{str(f == 'mixed').lower()}>"
+        by = SEARCH_ALGO_BYTES_PER_PARTICLE[f] * n_part
+        ach = by / (t * 1e-3) / 1e9
+        roofs.setdefault(f, {})["cell_search"] = {
+            "kernel": kern, "bound": "hbm", "achieved": ach, "peak": hbm_peak(), "unit": "GB/s",
+            "frac": ach / hbm_peak(), "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured",
+            "traffic": measured_traffic(kern, n_part), "traffic_unit": "bytes per launch",
+            "traffic_ratio": ratio(measured_traffic(kern, n_part), by),
+            "work": f"{SEARCH_ALGO_BYTES_PER_PARTICLE[f]} B x {n_part} particles per launch "
+                    "(position records read once); the candidate tests are implementation "
+                    "work, not algorithmic",
+            "candidate_tests": tests,
+            "candidate_test_tflops": SEARCH_FLOPS_PER_TEST[f] * tests / (t * 1e-3) / 1e12,
+            "launch_ms": t}
         if "pfilter" in extras:
             t = results[f]["stages"]["pressure_filter"]
             by = filter_bytes(f, pr, n_part)
@@ -545,10 +648,13 @@ def run_ours(args, dist):
             src = f"measured {u} FMA-chain rate of this GPU (sph_fma_peak), of measured"
             t = results[f]["stages"][stage] * 1e-3
             ach = fpp * units / t / 1e12
+            tr = measured_traffic(kern, n_part)
             roofs.setdefault(f, {})[stage] = {
                 "kernel": kern, "bound": "alu", "achieved": ach, "peak": pk,
                 "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": measured_traffic(kern, n_part), "traffic_unit": "bytes per launch",
+                "traffic": tr, "traffic_unit": "bytes per launch",
+                "algorithmic_bytes": ALGO_BYTES_PER_PARTICLE[kern] * n_part,
+                "traffic_ratio": ratio(tr, ALGO_BYTES_PER_PARTICLE[kern] * n_part),
                 "peak_source": src,
                 "work": f"{fpp} {u} flop x {units} {what} per launch",
                 "launch_ms": results[f]["stages"][stage]}
@@ -558,7 +664,8 @@ def run_ours(args, dist):
     n_cells = sum(float((np.floor((np.array(c.params["box_hi"]) - np.array(c.params["box_lo"]))
                                   / (2.0 * c.params["h"])) + [2, 2, 0]).prod()) for c in insts)
     steps_roof = {f: step_roofline(results[f]["stages"], f, n_part, n_cells,
-                                   results[f]["diag"]["n_pairs"], tests, peaks, hbm, extras)
+                                   results[f]["diag"]["n_pairs"], census[f]["unique_pairs"],
+                                   peaks, hbm, extras)
                   for f in results}
 
     # end-to-end through the C ABI with host buffers
@@ -613,6 +720,7 @@ def run_ours(args, dist):
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,
             "roofline": roof,
+            "pair_census": census[best],
             "step_roofline": steps_roof,
             "roofline_by_form": roofs,
             "cpu_baseline": cpu,

@@ -316,9 +316,11 @@ SPH_API sph_status sph_fma_peak(int32_t precision, int32_t iters, double* tflops
  * n: particles, 1 .. 67,108,864; a larger n is rejected with SPH_ERR_ARG
  *   (the capacity of the fixed scratch array).
  * pos, vel, spin (3n doubles, xyz-interleaved), species (n bytes), rho (n
- *   doubles): device (or managed) pointers, in any particle order; anything
- *   else returns SPH_ERR_ARG.
- * out: SPH_DIAG_SUMS doubles, host or device: M, M_s, M_n, momentum[3],
+ *   doubles): memory of the current device (or managed memory), in any
+ *   particle order; host memory or another device's memory returns
+ *   SPH_ERR_ARG.
+ * out: SPH_DIAG_SUMS doubles, host memory or memory of the current device
+ *   (another device's memory returns SPH_ERR_ARG): M, M_s, M_n, momentum[3],
  *   L_orb[3], L_spin[3], E_kin, E_rot, E_int, 0 (pair counts need neighbour
  *   lists, which this call does not build), rho_min, rho_max, |v|_max, summed
  *   over the fluid particles as in sph_diagnostics.  A host out makes the call
@@ -327,7 +329,13 @@ SPH_API sph_status sph_fma_peak(int32_t precision, int32_t iters, double* tflops
  *
  * The first call on each device (with that device current) looks up the
  * scratch array's device address with cudaGetSymbolAddress; make that first
- * call before any stream capture.  Every call on a device shares the same
+ * call before any stream capture.  With CUDA's lazy module loading (the
+ * default) that first call is also when the array's device memory is
+ * reserved, so it is the call that can fail with SPH_ERR_CUDA on a device
+ * whose memory is used up; later calls reserve nothing.  The address is kept
+ * for the life of the device's context: after a cudaDeviceReset of that
+ * device, do not call this function again in the same process.  Every call
+ * on a device shares the same
  * scratch array and overwrites the partials it reads, so calls that may
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  No cudaMalloc, cudaFree or allocating library

@@ -101,6 +101,9 @@ def lib():
             L.orc_forces.restype = None
             L.orc_forces.argtypes = [P, C.c_int64, dp, dp, dp, u8p, dp, dp, i64p,
                                      C.c_int64, dp, dp, dp, dp]
+            L.orc_forces_ex.restype = None
+            L.orc_forces_ex.argtypes = [P, C.c_int64, dp, dp, dp, u8p, dp, dp, i64p,
+                                        C.c_int64, dp, dp, dp, dp, dp]
             L.orc_place_walls.restype = None
             L.orc_place_walls.argtypes = [P, C.c_int64, u8p, dp, C.c_double, dp, dp, dp]
             L.orc_init.restype = None
@@ -198,7 +201,11 @@ def pressure_filter(p: OrcParams, pos, species, rho, P, rows=None):
     return Pf
 
 
-def forces(p: OrcParams, pos, vel, spin, species, rho, P, rows=None, term_mag=False):
+def forces(p: OrcParams, pos, vel, spin, species, rho, P, rows=None, term_mag=False,
+           scale=False):
+    """Pair forces of the listed rows: (acc, dspin, wall torque[, term sums]
+    [, scale]).  scale (n, 2): sum_j |f_ij| / m_i and sum_j |tau_ij| / I_i of
+    each listed fluid row, the bound on what summation order can change."""
     pos, vel, spin = (np.ascontiguousarray(a, dtype=np.float64) for a in (pos, vel, spin))
     species = np.ascontiguousarray(species, dtype=np.uint8)
     rho, P = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, P))
@@ -207,13 +214,30 @@ def forces(p: OrcParams, pos, vel, spin, species, rho, P, rows=None, term_mag=Fa
     dspin = np.zeros((n, 3))
     wT = np.zeros((n, 3))
     mag = np.zeros(5)
+    sc = np.zeros((n, 2))
     r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
     nr = n if rows is None else r.shape[0]
-    lib().orc_forces(C.byref(p), n, _d(pos), _d(vel), _d(spin), _u8(species), _d(rho),
-                     _d(P), _i64(r), nr, _d(acc), _d(dspin), _d(wT), _d(mag))
+    lib().orc_forces_ex(C.byref(p), n, _d(pos), _d(vel), _d(spin), _u8(species), _d(rho),
+                        _d(P), _i64(r), nr, _d(acc), _d(dspin), _d(wT), _d(mag), _d(sc))
+    out = (acc, dspin, wT)
     if term_mag:
-        return acc, dspin, wT, mag
-    return acc, dspin, wT
+        out += (mag,)
+    if scale:
+        out += (sc,)
+    return out
+
+
+def diagnostics(p: OrcParams, pos, vel, spin, species, rho, T_wall=None, J_wall=None) -> dict:
+    """FP64 conservation diagnostics of a given state (orc_diagnostics)."""
+    pos, vel, spin = (np.ascontiguousarray(a, dtype=np.float64) for a in (pos, vel, spin))
+    species = np.ascontiguousarray(species, dtype=np.uint8)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    T = np.zeros(3) if T_wall is None else np.ascontiguousarray(T_wall, dtype=np.float64)
+    J = np.zeros(3) if J_wall is None else np.ascontiguousarray(J_wall, dtype=np.float64)
+    d = OrcDiag()
+    lib().orc_diagnostics(C.byref(p), pos.shape[0], _d(pos), _d(vel), _d(spin), _u8(species),
+                          _d(rho), _d(T), _d(J), C.byref(d))
+    return d.as_dict()
 
 
 class Sim:

@@ -179,11 +179,11 @@ static void cross(const double a[3], const double b[3], double c[3]) {
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-void orc_forces(const orc_params* p, int64_t n, const double* pos,
-                const double* vel, const double* spin, const uint8_t* species,
-                const double* rho, const double* P, const int64_t* rows,
-                int64_t nrows, double* acc, double* dspin, double* wall_T,
-                double* term_mag) {
+void orc_forces_ex(const orc_params* p, int64_t n, const double* pos,
+                   const double* vel, const double* spin, const uint8_t* species,
+                   const double* rho, const double* P, const int64_t* rows,
+                   int64_t nrows, double* acc, double* dspin, double* wall_T,
+                   double* term_mag, double* scale) {
   double c2 = cutoff2(p);
   double m_n = orc_mass(p, 1), m_s = orc_mass(p, 0);
   double A = 10.0 * (p->eta_bar - 0.6 * p->eta_r); /* M5 */
@@ -200,6 +200,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
     ai[0] = ai[1] = ai[2] = 0.0;
     bi[0] = bi[1] = bi[2] = 0.0;
     if (Ti) Ti[0] = Ti[1] = Ti[2] = 0.0;
+    if (scale) scale[2 * i] = scale[2 * i + 1] = 0.0;
     if (species[i] >= 2) continue; /* walls carry no dynamics */
     double mi = species[i] == 0 ? m_s : m_n;
     double Vi = mi / rho[i];
@@ -209,6 +210,7 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
     memset(fsum, 0, sizeof fsum);
     double tau[3] = {0, 0, 0};
     double Tw[3] = {0, 0, 0};
+    double fabs_sum = 0.0, tabs_sum = 0.0; /* sum_j |f_ij| and sum_j |tau_ij| */
     for (int64_t j = 0; j < n; ++j) {
       if (j == i) continue;
       double d[3];
@@ -296,6 +298,13 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
       for (int a = 0; a < 3; ++a) tau[a] += t[a];
       for (int q = 0; q < 6; ++q)
         for (int a = 0; a < 3; ++a) fsum[q][a] += f[q][a];
+      if (scale) {
+        double fp[3];
+        for (int a = 0; a < 3; ++a)
+          fp[a] = f[0][a] + f[1][a] + f[2][a] + f[3][a] + f[4][a] + f[5][a];
+        fabs_sum += sqrt(norm2(fp));
+        tabs_sum += sqrt(norm2(t));
+      }
       if (species[j] >= 2) {
         double ft[3] = {f[0][0] + f[1][0] + f[2][0] + f[3][0] + f[4][0] + f[5][0],
                         f[0][1] + f[1][1] + f[2][1] + f[3][1] + f[4][1] + f[5][1],
@@ -312,12 +321,25 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
       bi[a] = tau[a] / Ii;
       if (Ti) Ti[a] = Tw[a];
     }
+    if (scale) {
+      scale[2 * i] = fabs_sum / mi;
+      scale[2 * i + 1] = tabs_sum / Ii;
+    }
     for (int q = 0; q < 5; ++q)
       mag[q] += sqrt(fsum[q][0] * fsum[q][0] + fsum[q][1] * fsum[q][1] +
                      fsum[q][2] * fsum[q][2]);
   }
   if (term_mag)
     for (int q = 0; q < 5; ++q) term_mag[q] += mag[q];
+}
+
+void orc_forces(const orc_params* p, int64_t n, const double* pos,
+                const double* vel, const double* spin, const uint8_t* species,
+                const double* rho, const double* P, const int64_t* rows,
+                int64_t nrows, double* acc, double* dspin, double* wall_T,
+                double* term_mag) {
+  orc_forces_ex(p, n, pos, vel, spin, species, rho, P, rows, nrows, acc, dspin, wall_T,
+                term_mag, NULL);
 }
 
 void orc_place_walls(const orc_params* p, int64_t n, const uint8_t* species,

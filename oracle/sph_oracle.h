@@ -17,9 +17,12 @@
  * angular-momentum conservation, rigid-rotation zero viscous force, continuum
  * limit of the viscous/spin terms, energy conservation, brute-force neighbour
  * sets against a k-d tree, time reversibility of the integrator).  The
- * interfacial and local-interaction coefficients C_T and C_l follow a reading
- * of Sec. 2.1 (the paper prints their continuum form only); their sign and
- * antisymmetry are pinned, their magnitude is a free parameter.
+ * interfacial force is pinned in sign, projection, reaction and scale: on a
+ * lattice split by a species interface its summed force per unit area is
+ * the closed form of the kernel's second moment, -C_T/2 in the continuum.
+ * The values of C_T and C_l themselves are free parameters (the paper
+ * prints the continuum form of the two forces only); the local-interaction
+ * magnitude is pinned in sign, direction and reaction only.
  *
  * The pressure filter and the collision model are named in Algorithm 1 but
  * their formulas are not printed; they follow a reading (a zeroth-order
@@ -121,6 +124,17 @@ void orc_forces(const orc_params* p, int64_t n, const double* pos,
                 const double* rho, const double* P, const int64_t* rows,
                 int64_t nrows, double* acc, double* dspin, double* wall_T,
                 double* term_mag);
+
+/* orc_forces, and (scale, optional, 2 doubles per particle) for each listed
+ * fluid row the scale of its absolute pair sums: sum_j |f_ij| / m_i and
+ * sum_j |tau_ij| / I_i, with f_ij the whole pair force and tau_ij the pair's
+ * spin torque (0 for wall rows).  A summation in another order can change
+ * acc_i and dspin_i only by rounding relative to these sums. */
+void orc_forces_ex(const orc_params* p, int64_t n, const double* pos,
+                   const double* vel, const double* spin, const uint8_t* species,
+                   const double* rho, const double* P, const int64_t* rows,
+                   int64_t nrows, double* acc, double* dspin, double* wall_T,
+                   double* term_mag, double* scale);
 
 /* Place the rigid walls at phase theta from their reference positions. */
 void orc_place_walls(const orc_params* p, int64_t n, const uint8_t* species,

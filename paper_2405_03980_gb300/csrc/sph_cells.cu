@@ -154,11 +154,12 @@ inline int grid_for(int64_t n, int threads, int sm_count, int per_sm) {
 
 }  // namespace
 
-cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, int* launches) {
+cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches) {
   const int64_t nb = cw.n_scan_blocks;
   k_scan_chunks<<<(unsigned)nb, kScanThreads, 0, s>>>(cw.count, cw.start, cw.bsum, cw.n_cells);
   k_scan_top<<<1, kScanThreads, 0, s>>>(cw.bsum, nb, cw.start, cw.n_cells);
-  k_scan_add<<<grid_for(cw.n_cells, 256, 152, 8), 256, 0, s>>>(cw.start, cw.bsum, cw.n_cells);
+  k_scan_add<<<grid_for(cw.n_cells, 256, lc.sm_count, 8), 256, 0, s>>>(cw.start, cw.bsum,
+                                                                       cw.n_cells);
   if (launches) *launches += 3;
   return cudaGetLastError();
 }

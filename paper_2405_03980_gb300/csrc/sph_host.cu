@@ -438,7 +438,7 @@ sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
     CK(launch_kick_drift_fp64(c->n, c->buf[a], c->f, c->inst, c->ist, c->cw, c->err, mode, s,
                               c->lc, launches));
   mark(m, s);
-  CK(launch_scan(c->cw, s, launches));
+  CK(launch_scan(c->cw, s, c->lc, launches));
   mark(m, s);
   CK(launch_scatter_sort(c->cw, mixed(c) ? c->mbuf[a].id : c->buf[a].id, c->n, s, c->lc,
                          launches));

@@ -22,7 +22,7 @@ struct LaunchCfg {
 
 // ---- cell build (sph_cells.cu) --------------------------------------------
 // Exclusive scan of cw.count into cw.start (n_cells + 1 entries).
-cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, int* launches);
+cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches);
 // perm[start[key[i]] + slot[i]] = i, then sort each cell by particle id.
 cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
                                 cudaStream_t s, const LaunchCfg& lc, int* launches);

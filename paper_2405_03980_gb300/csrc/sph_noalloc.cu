@@ -7,8 +7,12 @@
 // the particle arrays on the device and want the same FP64 totals that
 // sph_diagnostics reports.  sph_diag_sums_noalloc computes them from plain
 // input arrays; the scratch it needs (one partial per chunk of particles) is
-// the file-scope array below, reserved once per device when the library is
-// loaded and held until the process exits.
+// the file-scope array below.  The CUDA runtime loads this file's module on a
+// device lazily, at the first use of one of its symbols there: the first
+// call on a device, which looks up the array's address, is when the array's
+// device memory is reserved (so that call can fail with SPH_ERR_CUDA on a
+// device whose memory is already used up).  It is held until the process
+// exits.
 #include <mutex>
 
 #include "sph_diag_impl.cuh"
@@ -58,20 +62,27 @@ __global__ void k_diag_final_plain(InstDev P, const double* __restrict__ partial
   if (blockIdx.x == 0 && threadIdx.x == 0) diag_finish(P, partials, n_chunks, out);
 }
 
-bool device_accessible(const void* p) {
+// Where a pointer points, seen from device `dev`: memory that kernels on dev
+// may read or write (dev's own device memory, or managed memory), another
+// device's memory (not reachable without peer access), or host memory.
+enum class Mem { kDevice, kOtherDevice, kHost };
+Mem mem_kind(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return Mem::kHost;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return Mem::kDevice;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev ? Mem::kDevice : Mem::kOtherDevice;
+  return Mem::kHost;
 }
+bool device_accessible(const void* p, int dev) { return mem_kind(p, dev) == Mem::kDevice; }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
-sph_status scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ERR_CUDA;
+// Device address of the scratch array on device dev (the current one),
+// looked up once per device: the host-side name of the array is not a
+// device address.  The cached address is that of the device's context at
+// the first call; a cudaDeviceReset ends that context and makes it stale.
+sph_status scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return SPH_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
@@ -97,19 +108,23 @@ extern "C" sph_status sph_diag_sums_noalloc(const sph_params* params, int64_t n,
                                             const double* rho, double* out, void* stream) {
   if (!params || !pos || !vel || !spin || !species || !rho || !out) return SPH_ERR_ARG;
   if (n < 1 || n > kNoAllocMaxParticles) return SPH_ERR_ARG;
-  if (!device_accessible(pos) || !device_accessible(vel) || !device_accessible(spin) ||
-      !device_accessible(species) || !device_accessible(rho))
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ERR_CUDA;
+  if (!device_accessible(pos, dev) || !device_accessible(vel, dev) ||
+      !device_accessible(spin, dev) || !device_accessible(species, dev) ||
+      !device_accessible(rho, dev))
     return SPH_ERR_ARG;
+  if (mem_kind(out, dev) == Mem::kOtherDevice) return SPH_ERR_ARG;
   InstDev P;
   sph_status st = derive_instance(*params, P);
   if (st != SPH_OK) return st;
   double* scratch = nullptr;
-  if ((st = scratch_address(&scratch)) != SPH_OK) return st;
+  if ((st = scratch_address(dev, &scratch)) != SPH_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n_chunks = (n + kReduceChunk - 1) / kReduceChunk;
   const PlainArrays A{pos, vel, spin, species, rho};
   k_diag_chunks_plain<<<(unsigned)n_chunks, kRedThreads, 0, s>>>(P, A, n, scratch);
-  const bool dev_out = device_accessible(out);
+  const bool dev_out = device_accessible(out, dev);
   double* final_rec = dev_out ? out : scratch + kNoAllocMaxChunks * kDiagFields;
   k_diag_final_plain<<<1, 32, 0, s>>>(P, scratch, n_chunks, final_rec);
   if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;

@@ -10,8 +10,10 @@ draws the two species at random in proportion to their share):
 
 * lattice points at ((i+1/2)dx, (j+1/2)dx, (k+1/2)dx), axis of the cylinder at
   x = y = 0, k = 0 .. H-1 so that z spans [0, H) and is periodic;
-* fluid where r_xy < R, inner wall layer R <= r_xy < R+dx, outer wall layer
-  R+dx <= r_xy < R+2dx (two layers of wall/dummy particles);
+* fluid where r_xy < R, inner wall layer R <= r_xy < R+dx, then the outer
+  (dummy) layers R+dx <= r_xy < R+(1+d)dx, d = dummy_layers: one by default
+  (two wall layers in all), two for the long runs, so that the kernel support
+  of every inner-wall particle (2h = 2.6 dx) lies inside wall particles;
 * fluid points jittered by U(-0.05, 0.05) dx per axis; walls are not jittered;
 * each fluid particle is viscous with probability f_v, otherwise inviscid;
 * velocity Omega z^ x r (+ N(0, 1e-3) per component for the fluid), spin zero
@@ -57,7 +59,7 @@ class Cylinder:
 def workload_params(R: float, H: float, Omega: float, dx: float = 1.0,
                     h_over_dx: float = 1.3, rho0: float = 1.0, gamma: int = 7,
                     Re: float = 100.0, cs_factor: float = 10.0,
-                    dt_factor: float = 0.25) -> dict:
+                    dt_factor: float = 0.25, wall_layers: int = 2) -> dict:
     """Dimensionless parameter recipe of the benchmark workloads.
 
     c_s = 10 Omega R, p0 = beta_P = rho0 c_s^2 / gamma (so P(rho0) = 0),
@@ -72,7 +74,7 @@ def workload_params(R: float, H: float, Omega: float, dx: float = 1.0,
     cs = cs_factor * Omega * R
     p0 = rho0 * cs * cs / gamma
     eta = rho0 * Omega * R * R / Re
-    margin = 2.0 * dx + 2.0 * h
+    margin = wall_layers * dx + 2.0 * h
     ext = R + margin
     return dict(
         dx=dx, h=h, rho0=rho0, alpha_P=float(gamma), p0=p0, beta_P=p0,
@@ -85,10 +87,14 @@ def workload_params(R: float, H: float, Omega: float, dx: float = 1.0,
 
 def cylinder(R: float, H: int, Omega: float = 0.1, f_v: float = 0.3,
              seed: int = 0, dx: float = 1.0, jitter: float = 0.05,
-             vel_noise: float = 1e-3, **param_kw) -> Cylinder:
-    """Jittered-lattice cylinder of radius R and H layers with two wall layers."""
+             vel_noise: float = 1e-3, dummy_layers: int = 1, **param_kw) -> Cylinder:
+    """Jittered-lattice cylinder of radius R and H layers with one inner wall
+    layer and `dummy_layers` outer (dummy) layers."""
+    if dummy_layers < 1:
+        raise ValueError("at least one dummy layer")
     rng = np.random.Generator(np.random.PCG64(seed))
-    m = int(math.ceil((R + 2 * dx) / dx)) + 1
+    outer = (1 + dummy_layers) * dx
+    m = int(math.ceil((R + outer) / dx)) + 1
     ax = (np.arange(-m, m, dtype=np.float64) + 0.5) * dx
     X, Y = np.meshgrid(ax, ax, indexing="ij")
     X = X.ravel()
@@ -97,7 +103,7 @@ def cylinder(R: float, H: int, Omega: float = 0.1, f_v: float = 0.3,
     kind = np.full(X.shape, -1, dtype=np.int8)
     kind[rxy < R] = 0
     kind[(rxy >= R) & (rxy < R + dx)] = WALL_INNER
-    kind[(rxy >= R + dx) & (rxy < R + 2 * dx)] = WALL_OUTER
+    kind[(rxy >= R + dx) & (rxy < R + outer)] = WALL_OUTER
     keep = kind >= 0
     X, Y, kind = X[keep], Y[keep], kind[keep]
     nl = X.shape[0]
@@ -119,13 +125,15 @@ def cylinder(R: float, H: int, Omega: float = 0.1, f_v: float = 0.3,
     vel[fluid] += rng.normal(0.0, vel_noise, size=(nf, 3))
     spin = np.zeros_like(pos)
     spin[~fluid, 2] = Omega
-    params = workload_params(R, H, Omega, dx=dx, **param_kw)
+    params = workload_params(R, H, Omega, dx=dx, wall_layers=1 + dummy_layers, **param_kw)
     return Cylinder(R=R, H=H, dx=dx, Omega=Omega, f_v=f_v, seed=seed, pos=pos,
                     vel=vel, spin=spin, species=species, params=params)
 
 
 # Named workloads: the 8,960-particle parity cylinder, the 2.4M and the 19.6M
-# cylinders (R:H = 1:2), and the near-inviscid low-temperature stress case.
+# cylinders (R:H = 1:2), and the near-inviscid low-temperature stress case,
+# whose 10,000 steps need the inner wall's kernel support covered by wall
+# particles (two dummy layers: 2,592,020 particles in all).
 # The paper_* cylinders have the paper's vessel shape (Sec. 3: diameter five
 # times the height, R:H = 2.5:1) at its three resolutions, 2.45M, 8.62M and
 # 19.6M fluid particles (2,454,000, 8,620,224 and 19,636,400 here), with the
@@ -135,7 +143,7 @@ WORKLOADS = {
     "cyl_8960": dict(R=10.0, H=20, Omega=0.1, f_v=0.3),
     "cyl_2525900": dict(R=72.5, H=145, Omega=0.1, f_v=0.3),
     "cyl_20100112": dict(R=146.0, H=292, Omega=0.1, f_v=0.3),
-    "cyl_2525900_lowT": dict(R=72.5, H=145, Omega=0.2, f_v=0.01),
+    "cyl_2525900_lowT": dict(R=72.5, H=145, Omega=0.2, f_v=0.01, dummy_layers=2),
     "paper_2534800": dict(R=125.0, H=50, Omega=0.1, f_v=1.0 / 6.0),
     "paper_8802016": dict(R=190.0, H=76, Omega=0.1, f_v=1.0 / 6.0),
     "paper_19949600": dict(R=250.0, H=100, Omega=0.1, f_v=1.0 / 6.0),

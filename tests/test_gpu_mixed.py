@@ -4,8 +4,9 @@ oracle and the FP64 GPU form.
 
 Tolerances (stated targets of the mixed form): every field within 2e-5
 relative L2 of the FP64 oracle after one step (rho, P, a, dspin, the
-displacement r1 - r0, v, spin); orbital + spin angular momentum within 1e-6
-relative of the FP64 form over 1000 steps; the mass exactly conserved.
+displacement r1 - r0, v, spin); over 1000 steps the orbital + spin angular
+momentum budget L_z(t) - L_z(0) - J_z(t) within 1e-6 of L_z and the gap to
+the FP64 form's L_z within 1e-6 of L_z; the mass exactly conserved.
 """
 import numpy as np
 import pytest
@@ -131,32 +132,50 @@ def test_mixed_batch_equals_solo_bitwise():
     batch.close()
 
 
+def _lz_run(c, precision, steps):
+    sim = sim_of(c, precision=precision)
+    d0 = sim.diagnostics()
+    sim.step(steps)
+    d = sim.diagnostics()
+    sim.close()
+    Lz0 = d0["L_orb"][2] + d0["L_spin"][2]
+    Lz = d["L_orb"][2] + d["L_spin"][2]
+    return {"Lz0": Lz0, "Lz": Lz, "residual": Lz - Lz0 - d["J_wall"][2],
+            "dmass": d["mass"] - d0["mass"]}
+
+
+def _lz_check(c, steps, gap_tol):
+    r64 = _lz_run(c, B.SPH_FP64, steps)
+    rm = _lz_run(c, B.SPH_MIXED, steps)
+    Lz0 = r64["Lz0"]
+    gap = (rm["Lz"] - r64["Lz"]) / Lz0
+    print("n=%d, %d steps: L_z change %.3e; budget residual fp64 %.3e mixed %.3e; "
+          "mixed - fp64 %.3e (relative to L_z0)"
+          % (c.n, steps, (r64["Lz"] - Lz0) / Lz0, r64["residual"] / Lz0,
+             rm["residual"] / Lz0, gap))
+    assert r64["dmass"] == 0.0 and rm["dmass"] == 0.0
+    assert abs(r64["residual"]) < 1e-10 * abs(Lz0)
+    assert abs(rm["residual"]) < 1e-6 * abs(Lz0)
+    assert abs(gap) < gap_tol
+    return gap
+
+
 def test_mixed_angular_momentum_over_1000_steps():
-    """L_z(t) - L_z(0) must equal the wall torque impulse J_z; the residual of
-    the mixed form and its gap to the FP64 form stay within 1e-6 of L_z.
-    The two-layer wall lets agitated fluid particles diffuse into and through
-    the wall region over long runs, so the cell grid is widened to R + 12 dx
-    here to keep every particle inside it."""
-    c = synth.workload("cyl_8960")
-    ext = c.R + 12.0
-    c.params = dict(c.params, box_lo=(-ext, -ext, 0.0), box_hi=(ext, ext, float(c.H)))
-    res = {}
-    for prec in (B.SPH_FP64, B.SPH_MIXED):
-        sim = sim_of(c, precision=prec)
-        d0 = sim.diagnostics()
-        sim.step(1000)
-        d = sim.diagnostics()
-        Lz0 = d0["L_orb"][2] + d0["L_spin"][2]
-        Lz = d["L_orb"][2] + d["L_spin"][2]
-        res[prec] = (Lz, Lz - Lz0 - d["J_wall"][2], Lz0, d["mass"] - d0["mass"])
-        sim.close()
-    Lz64, r64, Lz0, dm64 = res[B.SPH_FP64]
-    Lzm, rm, _, dmm = res[B.SPH_MIXED]
-    print("budget residual fp64 %.3e mixed %.3e; mixed-fp64 %.3e (relative to L_z0)"
-          % (r64 / Lz0, rm / Lz0, (Lzm - Lz64) / Lz0))
-    assert dm64 == 0.0 and dmm == 0.0
-    assert abs(r64) < 1e-10 * abs(Lz0)
-    assert abs(rm) < 1e-6 * abs(Lz0)
-    # the trajectories themselves separate (the jittered start is acoustically
-    # agitated), so the gap to the FP64 run is a sanity bound, not the target
-    assert abs(Lzm - Lz64) < 1e-4 * abs(Lz0)
+    """L_z(t) - L_z(0) must equal the wall torque impulse J_z: the budget
+    residual over 1000 steps stays within 1e-6 of L_z in the mixed form
+    (1e-10 in FP64), on the 8,960 cylinder with two dummy layers behind the
+    inner wall (its own cell grid, no widening: with a single dummy layer the
+    inner wall's summed density is 2 % low, its pressure negative, and fluid
+    leaks through the wall within a few hundred steps).  The gap between the
+    two forms' L_z is held to 1e-6 of L_z as well."""
+    c = synth.cylinder(R=10.0, H=20, Omega=0.1, f_v=0.3, seed=0, dummy_layers=2)
+    _lz_check(c, 1000, 1e-6)
+
+
+def test_mixed_vs_fp64_angular_momentum_2_4m_1000_steps():
+    """The 2.4M-particle cylinder (2,525,900 particles, R:H = 1:2, Omega =
+    0.1, viscous fraction 0.3) over 1000 steps in both forms, on the
+    workload's own box: exact mass in both, the angular-momentum budget
+    residual within 1e-6 of L_z (mixed) and 1e-10 (FP64), and the mixed
+    form's L_z within 1e-6 of the FP64 form's."""
+    _lz_check(synth.workload("cyl_2525900"), 1000, 1e-6)

@@ -20,6 +20,13 @@ MUTATIONS = {
     "spin_velocity_sign": ("double u[3] = {vij[0] + 0.5 * dxw[0]", "double u[3] = {vij[0] - 0.5 * dxw[0]"),
     "local_interaction_sign": ("double s = -p->C_l * Vi * Vj * W;", "double s = p->C_l * Vi * Vj * W;"),
     "interfacial_sign": ("double s = p->C_T * Vi * Vj * F;", "double s = -p->C_T * Vi * Vj * F;"),
+    "interfacial_kernel_not_gradient": ("double s = p->C_T * Vi * Vj * F;",
+                                        "double s = p->C_T * Vi * Vj * W;"),
+    "interfacial_doubled": ("double s = p->C_T * Vi * Vj * F;",
+                            "double s = 2.0 * p->C_T * Vi * Vj * F;"),
+    "interfacial_masses_for_volumes": ("double s = p->C_T * Vi * Vj * F;",
+                                       "double s = p->C_T * mi * mj * F;"),
+    "interfacial_projects_x": ("f[1][0] = s * d[0];", "f[1][0] = 0.0 * d[0];"),
     "density_without_self": ("if (q2 < c2) r +=", "if (q2 < c2 && j != i) r +="),
     "no_z_minimum_image": ("if (d[2] > half) d[2] -= p->Hz;", "if (d[2] > half) d[2] -= 0;"),
     "spin_full_kick": ("spin[3 * i + a] += hdt * dspin[3 * i + a];\n    }\n  }\n  for",

@@ -343,6 +343,85 @@ def test_interfacial_force_sign_projection_and_reaction():
     assert np.allclose(np.cross(acc[0], pos[0] - pos[1]), 0.0, atol=1e-15)
 
 
+def _interface_column(p, axis):
+    """Unjittered lattice of 12 x 13 x 13 points split by the plane x_axis = 0
+    (inviscid below, viscous above); rows: the column of points on the axis
+    below the plane.  Returns the summed force on those rows."""
+    G = np.stack(np.meshgrid(*[np.arange(-6, 7)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    G = G[G[:, axis] <= 5].astype(np.float64)
+    G[:, axis] += 0.5
+    sp = np.where(G[:, axis] < 0.0, 0, 1).astype(np.uint8)
+    others = [k for k in range(3) if k != axis]
+    rows = np.where((G[:, others[0]] == 0) & (G[:, others[1]] == 0) & (G[:, axis] < 0))[0]
+    rho = np.full(len(G), p.rho0)  # rest density: V_j = m_j / rho0 for every j
+    zero = np.zeros_like(G)
+    acc, _, _ = oracle.forces(p, G, zero, zero, sp, rho, np.zeros(len(G)), rows=rows)
+    return (oracle.mass(p, 0) * acc[rows]).sum(0)
+
+
+@pytest.mark.parametrize("h_over_dx", [1.3, 2.6])
+def test_interfacial_force_planar_interface_closed_form(h_over_dx):
+    """Scale and radial factor of the interfacial force (Eqs. 1-2).  The pair
+    form is the gradient estimate sum_j V_j (T_j - T_i) grad_i W_ij of a
+    temperature that jumps by dT across the species interface, times
+    -/+ rho_s sigma V_i.  On a lattice split by a plane, the pairs that cross
+    it from one column give, by counting the pairs at each separation s,
+        sum_i f_i = -C_T V^2 dx sum_{s>=1} s^2 sum_{p,q} F(dx |(s,p,q)|)
+                  = -(C_T V^2 dx / 2) sum_{n in Z^3} n_x^2 F(|n| dx),
+    and the second moment of the kernel gradient, int x^2 F d^3x = 1 (by
+    parts from int W = 1), makes that -C_T / 2 per unit interface area in
+    the continuum: half the jump acts on each side.  With the horizontal
+    projection of Sec. 2.1 a horizontal interface feels nothing."""
+    p = oracle.make_params(_params(h_over_dx=h_over_dx, periodic_z=0, C_T=1.7, rho0=2.0),
+                           flags=oracle.TERM_T | oracle.HPROJ)
+    m = int(math.ceil(2.0 * h_over_dx)) + 1
+    g = np.arange(-m, m + 1, dtype=np.float64)
+    n = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    moment = sum(nx * nx * oracle.F(p, r) for nx, r in zip(n[:, 0], np.sqrt((n * n).sum(1))))
+    # continuum second moment of F, to the lattice's accuracy at this h
+    assert moment * p.dx ** 5 == pytest.approx(1.0, abs=2e-4 if h_over_dx > 2 else 3e-2)
+    V = oracle.mass(p, 0) / p.rho0
+    expect = -0.5 * p.C_T * V * V * p.dx * moment
+    for axis in (0, 1):  # vertical interfaces: normal x, then y
+        f = _interface_column(p, axis)
+        assert f[axis] == pytest.approx(expect, rel=1e-12)
+        assert f[2] == 0.0
+        assert abs(f[1 - axis]) < 1e-14 * abs(expect)
+        if h_over_dx > 2:
+            assert f[axis] / p.dx ** 2 == pytest.approx(-0.5 * p.C_T, rel=3e-4)
+    # horizontal interface: no force under the projection, the same law without it
+    f = _interface_column(p, 2)
+    assert np.all(f == 0.0) or np.abs(f).max() < 1e-14 * abs(expect)
+    assert f[2] == 0.0
+    p.flags = oracle.TERM_T
+    f = _interface_column(p, 2)
+    assert f[2] == pytest.approx(expect, rel=1e-12)
+
+
+def test_force_scale_is_the_absolute_pair_sum():
+    """The per-row scale the parity tests use, sum_j |f_ij| / m_i and
+    sum_j |tau_ij| / I_i: for a lone pair it is |a| and |alpha| themselves,
+    and on every row it bounds them (triangle inequality)."""
+    p = oracle.make_params(_params(periodic_z=0, C_T=0.4, C_l=0.6),
+                           flags=oracle.TERMS_ALL | oracle.HPROJ)
+    pos = np.array([[0.0, 0.0, 0.0], [0.8, -0.5, 0.9]])
+    vel = np.array([[0.1, 0.3, -0.2], [-0.4, 0.2, 0.1]])
+    spin = np.array([[0.2, -0.1, 0.3], [0.0, 0.5, -0.2]])
+    sp = np.array([0, 1], np.uint8)
+    rho, P = oracle.density(p, pos, sp)
+    P = P + np.array([0.3, -0.1])
+    acc, dsp, _, sc = oracle.forces(p, pos, vel, spin, sp, rho, P, scale=True)
+    assert sc[:, 0] == pytest.approx(np.linalg.norm(acc, axis=1), rel=1e-15)
+    assert sc[:, 1] == pytest.approx(np.linalg.norm(dsp, axis=1), rel=1e-15)
+    pos, vel, spin, sp = _block(6, 6, 6, seed=13)
+    p = oracle.make_params(_params(Hz=6.0, C_T=0.3, C_l=0.7), flags=oracle.TERMS_ALL | oracle.HPROJ)
+    rho, P = oracle.density(p, pos, sp)
+    acc, dsp, _, sc = oracle.forces(p, pos, vel, spin, sp, rho, P, scale=True)
+    assert np.all(np.linalg.norm(acc, axis=1) <= sc[:, 0] * (1 + 1e-14))
+    assert np.all(np.linalg.norm(dsp, axis=1) <= sc[:, 1] * (1 + 1e-14))
+    assert np.all(sc[:, 0] > 0) and np.all(sc[:, 1] > 0)
+
+
 def test_local_interaction_opposes_relative_velocity():
     """F_sn = C_l v_sn acts between unlike species with its reaction on the
     other species (Sec. 2.1), decelerating their relative motion."""

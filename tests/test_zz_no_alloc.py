@@ -2,8 +2,10 @@
 allocate device memory (a plug-in inside an application that owns all device
 allocations).  It must agree with sph_diagnostics on the same state, call
 after call, while keeping its partial sums in the library's fixed scratch
-array instead of a caller workspace.  This file is collected last so that a
-run stopping at the first failure has already run every other test."""
+array instead of a caller workspace, take no device memory after its first
+call, and agree with the CPU oracle's FP64 diagnostics of the same state.
+This file is collected last so that a run stopping at the first failure has
+already run every other test."""
 import numpy as np
 import pytest
 
@@ -48,13 +50,19 @@ def test_noalloc_sums_match_sph_diagnostics_twice(precision):
     sp = torch.from_numpy(c.species).to(dev)
     params = B.params_from_dict(c.params, precision=precision)
     outs = []
-    # first call: host output; second call: device output
+    dev_out = torch.full((B.SPH_DIAG_SUMS,), float("nan"), dtype=torch.float64, device=dev)
+    # first call: host output (on a fresh device this call also loads the
+    # module that holds the scratch array); second call: device output, which
+    # must not take any device memory
     host_out = np.full(B.SPH_DIAG_SUMS, np.nan)
     B.sph_diag_sums_noalloc(params, c.n, pos, vel, spin, sp, rho, host_out)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info(dev)
     outs.append(host_out)
-    dev_out = torch.full((B.SPH_DIAG_SUMS,), float("nan"), dtype=torch.float64, device=dev)
     B.sph_diag_sums_noalloc(params, c.n, pos, vel, spin, sp, rho, dev_out)
     torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info(dev)
+    assert free_after == free_before
     outs.append(dev_out.cpu().numpy())
     for o in outs:
         assert o[0] == ref["mass"] and o[1] == ref["mass_s"] and o[2] == ref["mass_n"]
@@ -69,6 +77,26 @@ def test_noalloc_sums_match_sph_diagnostics_twice(precision):
         assert o[15] == 0.0
         assert o[16] == ref["rho_min"] and o[17] == ref["rho_max"] and o[18] == ref["v_max"]
     assert np.array_equal(outs[0], outs[1])
+    # and against the CPU oracle's FP64 diagnostics of the same state
+    import oracle
+    ref = oracle.diagnostics(oracle.make_params(c.params), st["pos"], st["vel"], st["spin"],
+                             c.species, st["rho"])
+    o = outs[0]
+    assert o[0] == pytest.approx(ref["mass"], rel=TOL)
+    assert o[1] == pytest.approx(ref["mass_s"], rel=TOL)
+    assert o[2] == pytest.approx(ref["mass_n"], rel=TOL)
+    fl = c.species < 2
+    m = o[0] / fl.sum()
+    vs = m * np.linalg.norm(st["vel"][fl], axis=1).sum()
+    ls = m * np.linalg.norm(np.cross(st["pos"][fl], st["vel"][fl]), axis=1).sum()
+    ss = np.linalg.norm(st["spin"][fl], axis=1).sum() * m * c.params["inertia_coef"]
+    for a in range(3):
+        assert abs(o[3 + a] - ref["mom"][a]) <= TOL * vs
+        assert abs(o[6 + a] - ref["L_orb"][a]) <= TOL * ls
+        assert abs(o[9 + a] - ref["L_spin"][a]) <= TOL * ss + 1e-300
+    for k, q in (("E_kin", 12), ("E_rot", 13), ("E_int", 14), ("rho_min", 16),
+                 ("rho_max", 17), ("v_max", 18)):
+        assert o[q] == pytest.approx(ref[k], rel=TOL, abs=1e-300), k
     sim.close()
 
 
