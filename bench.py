@@ -42,12 +42,22 @@ UNIT = "particle-steps/s"
 # Algorithmic work is counted per UNIQUE interacting pair with at least one
 # fluid particle: a fluid-fluid pair once (the gather evaluates it from both
 # sides; that second evaluation is implementation work, not algorithmic), a
-# fluid-wall pair once.  unique = (ordered fluid-row pairs + fluid-wall
-# pairs) / 2; the ordered count comes from sph_diagnostics, the fluid-wall
-# count from the host (fluid_wall_pairs).
-# FP32/FP64 operations per pair of the pair pass, counted from the kernel
-# source (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1).
-FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # mixed adds cell offsets and Kahan
+# fluid-wall pair once.  The counts come from sph_pair_census, which sorts
+# the ordered (fluid row, neighbour) pairs of the lists into species classes:
+# unique = fluid-fluid / 2 + fluid-wall.
+# Operations per pair of the pair pass, counted from the kernel source
+# (add/sub/mul = 1, fused multiply-add = 2, sqrt/rsqrt/div = 1), by the terms
+# a pair carries (Eqs. 1-2 as the model reads them): two inviscid particles
+# the pressure term alone; unlike species (walls count as viscous) pressure,
+# interfacial and local interaction with its torque; two viscous particles
+# pressure, shear and rotational with its torque.  The FP64 form's pair pass
+# runs one specialised loop per class and these are its counts; the mixed
+# form adds the cell offsets of the pair vector (3) and its compensated
+# sums (3 per pair), and its single loop evaluates every term for every pair
+# (96 operations), the difference being implementation work.
+FORCE_FLOPS_BY_CLASS = {"fp64": {"II": 23, "IX": 76, "VV": 79},
+                        "mixed": {"II": 29, "IX": 82, "VV": 85}}
+FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # every term for every pair
 # Density pass: operations per pair of the density sum (pair vector, r^2,
 # sqrt, Wendland W, accumulation; the mixed form adds the cell offsets and
 # the Kahan update).  W_ij = W_ji, so a pair is algorithmic work once.  The
@@ -119,7 +129,7 @@ STREAM_BYTES_PER_PARTICLE = {
 
 
 def step_roofline(stage_ms, form, n_particles, n_cells, pairs, unique, peak_alu, hbm_gbs,
-                  extras=()):
+                  extras=(), force_flops=None):
     """Lower bound of one step: every stage at its own roof (the streaming
     stages and the neighbour search at the measured HBM bandwidth with their
     algorithmic bytes, the density and pair passes at the measured FMA rate
@@ -132,7 +142,7 @@ def step_roofline(stage_ms, form, n_particles, n_cells, pairs, unique, peak_alu,
         bound[st] = by / (hbm_gbs * 1e9) * 1e3
     bound["cell_search"] = SEARCH_ALGO_BYTES_PER_PARTICLE[form] * n_particles / (hbm_gbs * 1e9) * 1e3
     flops = {"density": DENSITY_FLOPS_PER_PAIR[form] * unique,
-             "forces": force_flops(form, extras) * unique}
+             "forces": force_flops}
     if "pfilter" in extras:
         by = filter_bytes(form, pairs, n_particles)
         fl = FILTER_FLOPS_PER_PAIR[form] * pairs
@@ -162,10 +172,6 @@ def filter_bytes(form, pairs, n_particles):
     return FILTER_BYTES_PER_PAIR[form] * pairs + FILTER_BYTES_PER_PARTICLE[form] * n_particles
 
 
-def force_flops(form, extras=()):
-    return FORCE_FLOPS_PER_PAIR[form] + (COLLISION_FLOPS_PER_PAIR if "collision" in extras else 0)
-
-
 def ratio(traffic, algorithmic):
     """Measured DRAM bytes over algorithmic bytes (None without a capture)."""
     return None if traffic is None or not algorithmic else traffic / algorithmic
@@ -185,33 +191,12 @@ def measured_traffic(kernel, n_particles):
     return per * n_particles
 
 
-def fluid_wall_pairs(insts):
-    """Unique (fluid, wall) neighbour pairs, r < 2h with the periodic z image,
-    counted on the host from the initial positions (only fluid particles
-    within reach of the wall take part)."""
-    from scipy.spatial import cKDTree
-    total = 0
-    for c in insts:
-        p = c.params
-        reach = 2.0 * p["h"]
-        rxy = np.hypot(c.pos[:, 0], c.pos[:, 1])
-        wall = c.species >= 2
-        if not wall.any():
-            continue
-        near = (c.species < 2) & (rxy > rxy[wall].min() - reach - 1.0)
-        ext = float(np.abs(c.pos[:, :2]).max()) + 4.0 * reach
-        shift = np.array([ext, ext, 0.0])
-        H = float(p["box_hi"][2] - p["box_lo"][2])
-        box = [4.0 * ext, 4.0 * ext, H] if p.get("periodic_z", 1) else None
-        fpos = c.pos[near] + shift
-        wpos = c.pos[wall] + shift
-        if box:
-            fpos[:, 2] %= H
-            wpos[:, 2] %= H
-        tf = cKDTree(fpos, boxsize=box)
-        tw = cKDTree(wpos, boxsize=box)
-        total += int(tf.count_neighbors(tw, np.nextafter(reach, 0.0)))
-    return total
+def pair_classes(census):
+    """Unique pairs by class from the ordered census [II, unlike fluid,
+    VV, inviscid-wall, viscous-wall]: fluid-fluid pairs halved, fluid-wall
+    pairs once (walls count as viscous)."""
+    c = [int(x) for x in census]
+    return {"II": c[0] // 2, "IX": c[1] // 2 + c[3], "VV": c[2] // 2 + c[4]}
 
 
 def candidate_tests(insts):
@@ -246,7 +231,7 @@ def candidate_tests(insts):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cyl_20100112")
@@ -258,6 +243,9 @@ def parse():
     ap.add_argument("--extras", default="",
                     help="optional steps of Algorithm 1 to switch on: pfilter, collision "
                          "(comma list; the default step has neither)")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="skin of the mixed form's reused neighbour lists in dx (0: the "
+                         "library default; < 0: rebuild every step)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="fluid particles in the oracle sample (0 = size for ~15 s)")
     return ap.parse_args()
@@ -511,10 +499,19 @@ def time_form(insts, precision, args, dist, dev):
     ms = dist.max(ms)
     diag = sim.diagnostics()
     diag["n_pairs"] = sum(sim.diagnostics(k)["n_pairs"] for k in range(len(insts)))
-    stages = sim.profile(args.profile_steps)
+    # the mixed form rebuilds its lists only every few steps: the per-stage
+    # times are means over a window of steps, and the list-build stages are
+    # also reported per build
+    census = np.sum([sim.pair_census(k) for k in range(len(insts))], axis=0)
+    b0 = sum(sim.list_builds(k) for k in range(len(insts)))
+    nprof = args.profile_steps if precision == B.SPH_FP64 else max(args.profile_steps, 16)
+    stages = sim.profile(nprof)
+    builds = (sum(sim.list_builds(k) for k in range(len(insts))) - b0) / len(insts)
     launches = sim.launches_per_step()
     out = {"ms_per_step": ms, "diag": diag, "stages": stages, "clocks": ck,
-           "launches_per_step": launches, "sim": sim, "blocks": blocks}
+           "launches_per_step": launches, "sim": sim, "blocks": blocks,
+           "profile_steps": nprof, "list_builds_per_step": builds / nprof,
+           "census": [int(x) for x in census]}
     return out
 
 
@@ -572,6 +569,9 @@ def run_ours(args, dist):
     B.lib(build_if_missing=True)
     extras = parse_extras(args.extras)
     insts = load_workload(args.workload, extras)
+    if args.skin:
+        for c in insts:
+            c.params = dict(c.params, skin=args.skin)
     n_part = sum(c.n for c in insts)
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     prec = {"fp64": B.SPH_FP64, "mixed": B.SPH_MIXED}
@@ -592,20 +592,28 @@ def run_ours(args, dist):
              "mixed": B.sph_fma_peak(B.SPH_MIXED, 1 << 20)}
     roofs = {}
     tests = candidate_tests(insts)
-    fw = fluid_wall_pairs(insts)
     census = {}
     for f in results:
         pr = results[f]["diag"]["n_pairs"]
-        uq = (pr + fw) // 2
-        census[f] = {"ordered_fluid_row_pairs": pr, "fluid_wall_pairs": fw,
-                     "unique_pairs": uq, "candidate_tests": tests}
+        cls = pair_classes(results[f]["census"])
+        uq = sum(cls.values())
+        census[f] = {"ordered_fluid_row_pairs": pr, "ordered_by_class": results[f]["census"],
+                     "unique_by_class": cls, "unique_pairs": uq, "candidate_tests": tests}
         unit = "FP64" if f == "fp64" else "FP32"
-        stages = [("forces", f"k_forces_{f}", force_flops(f, extras), uq,
-                   "unique pairs with a fluid particle", unit),
+        byc = FORCE_FLOPS_BY_CLASS[f]
+        fl_forces = sum(byc[k] * cls[k] for k in cls) + (
+            COLLISION_FLOPS_PER_PAIR * uq if "collision" in extras else 0)
+        stages = [("forces", f"k_forces_{f}", fl_forces / max(uq, 1), uq,
+                   "unique pairs with a fluid particle (" +
+                   ", ".join(f"{cls[k]} {k} at {byc[k]}" for k in cls) + " flop)", unit),
                   ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], uq,
                    "unique pairs with a fluid particle", unit)]
-        # the neighbour search: algorithmic work is its position reads
-        t = results[f]["stages"]["cell_search"]
+        # the neighbour search: algorithmic work is its position reads; in the
+        # mixed form it runs in the steps that rebuild the lists, so its
+        # launch time is the stage's mean over the profiled steps divided by
+        # the builds per step
+        bps = results[f]["list_builds_per_step"]
+        t = results[f]["stages"]["cell_search"] / (bps if bps > 0 else 1.0)
         kern = f"k_cell_search<{str(f == 'mixed').lower()}>"
         by = SEARCH_ALGO_BYTES_PER_PARTICLE[f] * n_part
         ach = by / (t * 1e-3) / 1e9
@@ -619,7 +627,7 @@ def run_ours(args, dist):
                     "work, not algorithmic",
             "candidate_tests": tests,
             "candidate_test_tflops": SEARCH_FLOPS_PER_TEST[f] * tests / (t * 1e-3) / 1e12,
-            "launch_ms": t}
+            "launch_ms": t, "list_builds_per_step": bps}
         if "pfilter" in extras:
             t = results[f]["stages"]["pressure_filter"]
             by = filter_bytes(f, pr, n_part)
@@ -656,7 +664,7 @@ def run_ours(args, dist):
                 "algorithmic_bytes": ALGO_BYTES_PER_PARTICLE[kern] * n_part,
                 "traffic_ratio": ratio(tr, ALGO_BYTES_PER_PARTICLE[kern] * n_part),
                 "peak_source": src,
-                "work": f"{fpp} {u} flop x {units} {what} per launch",
+                "work": f"{fpp:.2f} {u} flop x {units} {what} per launch",
                 "launch_ms": results[f]["stages"][stage]}
     dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
     roof = roofs[best][dom_stage]
@@ -665,7 +673,9 @@ def run_ours(args, dist):
                                   / (2.0 * c.params["h"])) + [2, 2, 0]).prod()) for c in insts)
     steps_roof = {f: step_roofline(results[f]["stages"], f, n_part, n_cells,
                                    results[f]["diag"]["n_pairs"], census[f]["unique_pairs"],
-                                   peaks, hbm, extras)
+                                   peaks, hbm, extras,
+                                   force_flops=roofs[f]["forces"]["achieved"] * 1e12 *
+                                   roofs[f]["forces"]["launch_ms"] * 1e-3)
                   for f in results}
 
     # end-to-end through the C ABI with host buffers
@@ -703,6 +713,10 @@ def run_ours(args, dist):
                              results[f]["diag"]["n_pairs"] * dist.world /
                              (results[f]["ms_per_step"] * 1e-3),
                          "stage_ms": results[f]["stages"],
+                         "stage_ms_note": f"mean per step over {results[f]['profile_steps']} "
+                                          "eager steps (the list-build stages run only in "
+                                          "the steps that rebuild)",
+                         "list_builds_per_step": results[f]["list_builds_per_step"],
                          "launch_config": results[f]["blocks"]} for f in results}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
@@ -715,7 +729,7 @@ def run_ours(args, dist):
                        "R": insts[0].R if len(insts) == 1 else None,
                        "H": insts[0].H if len(insts) == 1 else None,
                        "form": best, "parallelism": "replicas",
-                       "extras": list(extras),
+                       "extras": list(extras), "skin": args.skin or "default",
                        "l2": "inputs larger than L2 (state of GBs), no flush"},
             "pair_interactions_per_s": pairs * dist.world / (r["ms_per_step"] * 1e-3),
             "forms": forms_out,

@@ -119,6 +119,21 @@ typedef struct sph_params {
   double col_dist;      /* collision model: pairs closer than this (and less
                            than 2h) whose distance shrinks collide            */
   double col_e;         /* collision model: restitution coefficient in [0, 1] */
+  double skin;          /* mixed form: skin width s of its reused neighbour
+                           lists (lengths as dx).  The lists hold the pairs
+                           closer than 2h + s at their build and are rebuilt
+                           (keys, sort, reorder, search) only once a particle
+                           of the instance has departed s/2 from where the
+                           vessel's rigid rotation since the build has carried
+                           its build position (the rotation keeps every pair
+                           distance), or has left its cell by a cell side;
+                           every step re-tests r < 2h, so the neighbour sets
+                           are those of the current positions.  0 = 0.3 dx;
+                           < 0 = rebuild every step; at most 2h, and narrowed
+                           where a short axis would otherwise get cells more
+                           than 5 % deeper than 2h + s (a periodic z needs 3
+                           cells).  The FP64 form rebuilds every step and
+                           ignores it. */
 } sph_params;
 
 /* FP64 conservation diagnostics of one instance (sums over fluid particles). */
@@ -213,6 +228,16 @@ SPH_API sph_status sph_diagnostics(sph_ctx* ctx, int32_t inst, sph_diag* out);
  * since the last reorder (SPH_ERR_STATE otherwise); synchronises. */
 SPH_API sph_status sph_force_breakdown(sph_ctx* ctx, int32_t inst, double out[5]);
 
+/* Neighbour-pair census of instance inst (synchronises): the ordered pairs
+ * (fluid particle, listed neighbour) of the last density pass by species
+ * class, out[0] both inviscid, out[1] one inviscid and one viscous fluid
+ * particle, out[2] both viscous, out[3] inviscid and wall, out[4] viscous
+ * and wall.  The pair terms of Eqs. 1-2 a pair carries depend on its class
+ * (the pressure term alone between two inviscid particles), so this is the
+ * measure of the pair pass's algorithmic work.  Needs a density pass since
+ * the last reorder (SPH_ERR_STATE otherwise). */
+SPH_API sph_status sph_pair_census(sph_ctx* ctx, int32_t inst, int64_t out[5]);
+
 /* Checkpoint and resume (a production run of the paper's size takes days).
  * A checkpoint is a small header plus a verbatim copy of the context's state
  * buffer: the sorted particle state in its stored precision (the mixed form's
@@ -289,8 +314,15 @@ SPH_API sph_status sph_set_launch_config(sph_ctx* ctx, int32_t block_density,
                                          int32_t search_depth);
 SPH_API const char* sph_stage_name(int32_t stage);
 
-/* Number of kernel launches one sph_step(ctx, 1) enqueues. */
+/* Number of kernel launches one sph_step(ctx, 1) enqueues (the mixed form's
+ * list-build kernels are enqueued every step and return at once in the
+ * steps that reuse the lists). */
 SPH_API int32_t sph_launches_per_step(const sph_ctx* ctx);
+
+/* Neighbour-list builds of instance inst so far (synchronises): in the mixed
+ * form the initial build, standalone cell builds and the steps whose drift
+ * exhausted the skin; in the FP64 form every step plus the initial one. */
+SPH_API sph_status sph_list_builds(sph_ctx* ctx, int32_t inst, int64_t* builds);
 
 /* Measure the device's FP64 (SPH_FP64) or FP32 (SPH_MIXED) FMA throughput in
  * TFLOP/s with independent dependent-FMA chains (iters FMAs per chain, >= 64):

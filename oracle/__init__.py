@@ -227,6 +227,16 @@ def forces(p: OrcParams, pos, vel, spin, species, rho, P, rows=None, term_mag=Fa
     return out
 
 
+def place_walls(p: OrcParams, species, wall_ref, theta: float, pos, vel, spin):
+    """Walls at phase theta from their reference positions, in place."""
+    for a in (pos, vel, spin):
+        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float64
+    species = np.ascontiguousarray(species, dtype=np.uint8)
+    wall_ref = np.ascontiguousarray(wall_ref, dtype=np.float64)
+    lib().orc_place_walls(C.byref(p), pos.shape[0], _u8(species), _d(wall_ref), float(theta),
+                          _d(pos), _d(vel), _d(spin))
+
+
 def diagnostics(p: OrcParams, pos, vel, spin, species, rho, T_wall=None, J_wall=None) -> dict:
     """FP64 conservation diagnostics of a given state (orc_diagnostics)."""
     pos, vel, spin = (np.ascontiguousarray(a, dtype=np.float64) for a in (pos, vel, spin))

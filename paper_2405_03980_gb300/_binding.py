@@ -41,7 +41,8 @@ class SphParams(C.Structure):
         "C_l", "C_T", "C_omega", "mass_ratio", "inertia_coef", "Omega", "dt")] + [
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("periodic_z", C.c_int32), ("precision", C.c_int32), ("flags", C.c_uint32),
-        ("nbr_cap", C.c_int32), ("col_dist", C.c_double), ("col_e", C.c_double)]
+        ("nbr_cap", C.c_int32), ("col_dist", C.c_double), ("col_e", C.c_double),
+        ("skin", C.c_double)]
 
 
 class SphDiag(C.Structure):
@@ -98,6 +99,8 @@ def lib(build_if_missing: bool = True):
                 "sph_get_neighbors": (C.c_int, [vp, i64p, i64p, C.c_int64]),
                 "sph_check": (C.c_int, [vp]),
                 "sph_launches_per_step": (C.c_int32, [vp]),
+                "sph_list_builds": (C.c_int, [vp, C.c_int32, i64p]),
+                "sph_pair_census": (C.c_int, [vp, C.c_int32, i64p]),
                 "sph_profile_steps": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.c_int32]),
                 "sph_stage_count": (C.c_int32, []),
                 "sph_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32),
@@ -129,7 +132,8 @@ def exported_symbols() -> list[str]:
     return ["sph_params_default", "sph_state_bytes", "sph_workspace_bytes", "sph_init",
             "sph_init_batch", "sph_build_cells", "sph_density", "sph_forces", "sph_step",
             "sph_diagnostics", "sph_force_breakdown", "sph_get_state", "sph_get_neighbors", "sph_check",
-            "sph_launches_per_step", "sph_profile_steps", "sph_stage_count", "sph_stage_name",
+            "sph_launches_per_step", "sph_list_builds", "sph_pair_census",
+            "sph_profile_steps", "sph_stage_count", "sph_stage_name",
             "sph_autotune", "sph_get_launch_config", "sph_set_launch_config",
             "sph_fma_peak", "sph_diag_sums_noalloc", "sph_checkpoint_bytes",
             "sph_save_checkpoint", "sph_load_checkpoint", "sph_destroy", "sph_status_string"]
@@ -172,6 +176,7 @@ def params_from_dict(p: dict, precision: int = SPH_FP64, flags: int = SPH_FLAGS_
     s.nbr_cap = int(p.get("nbr_cap", nbr_cap))
     s.col_dist = float(p.get("col_dist", 0.8 * float(p["dx"])))
     s.col_e = float(p.get("col_e", 0.2))
+    s.skin = float(p.get("skin", 0.0))
     return s
 
 
@@ -275,6 +280,19 @@ def sph_check(ctx):
 
 def sph_launches_per_step(ctx) -> int:
     return int(lib().sph_launches_per_step(ctx))
+
+
+def sph_pair_census(ctx, inst: int = 0) -> np.ndarray:
+    out = np.zeros(5, dtype=np.int64)
+    _ck(lib().sph_pair_census(ctx, inst, out.ctypes.data_as(C.POINTER(C.c_int64))),
+        "sph_pair_census")
+    return out
+
+
+def sph_list_builds(ctx, inst: int = 0) -> int:
+    n = C.c_int64(0)
+    _ck(lib().sph_list_builds(ctx, inst, C.byref(n)), "sph_list_builds")
+    return int(n.value)
 
 
 def sph_profile_steps(ctx, nsteps: int) -> dict:

@@ -15,6 +15,12 @@ constexpr int kScanThreads = 1024;
 constexpr int kPerThread = kScanChunk / kScanThreads;  // 4
 static_assert(kPerThread == 4, "scan layout assumes 4 elements per thread");
 
+// The kernels of the cell build do nothing while a gate word is zero (the
+// mixed form's steps that reuse their lists); a null gate always runs.
+__device__ __forceinline__ bool closed(const uint32_t* gate) {
+  return gate != nullptr && *(const volatile uint32_t*)gate == 0u;
+}
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -26,14 +32,18 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_chunks(const uint32_t* __restrict__ count, uint32_t* __restrict__ start,
-              uint32_t* __restrict__ bsum, int64_t n) {
+k_scan_chunks(uint32_t* __restrict__ count, uint32_t* __restrict__ start,
+              uint32_t* __restrict__ bsum, int64_t n, const uint32_t* gate) {
   __shared__ uint32_t warp_ex[32];
   __shared__ uint32_t block_total;
+  if (closed(gate)) return;
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kPerThread;
   uint32_t v[kPerThread];
 #pragma unroll
-  for (int k = 0; k < kPerThread; ++k) v[k] = (base + k < n) ? count[base + k] : 0u;
+  for (int k = 0; k < kPerThread; ++k) {
+    v[k] = (base + k < n) ? count[base + k] : 0u;
+    if (base + k < n) count[base + k] = 0u;  // zero for the next build
+  }
   uint32_t s = v[0] + v[1] + v[2] + v[3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = warp_incl_scan(s);
@@ -57,9 +67,11 @@ k_scan_chunks(const uint32_t* __restrict__ count, uint32_t* __restrict__ start,
 
 // One block: exclusive scan of the chunk sums in place, total to start[n].
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* __restrict__ start, int64_t n) {
+k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* __restrict__ start, int64_t n,
+           const uint32_t* gate) {
   __shared__ uint32_t warp_ex[32];
   __shared__ uint32_t tile_total;
+  if (closed(gate)) return;
   uint32_t carry = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t t0 = 0; t0 < nb; t0 += kScanThreads) {
@@ -83,7 +95,8 @@ k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* __restrict__ start
 }
 
 __global__ void k_scan_add(uint32_t* __restrict__ start, const uint32_t* __restrict__ bsum,
-                           int64_t n) {
+                           int64_t n, const uint32_t* gate) {
+  if (closed(gate)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     start[i] += bsum[i / kScanChunk];
@@ -91,7 +104,8 @@ __global__ void k_scan_add(uint32_t* __restrict__ start, const uint32_t* __restr
 
 __global__ void k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
                           const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
-                          int64_t n, int64_t n_cells, uint32_t* err) {
+                          int64_t n, int64_t n_cells, uint32_t* err, const uint32_t* gate) {
+  if (closed(gate)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t k = key[i];
@@ -106,7 +120,8 @@ __global__ void k_scatter(const uint32_t* __restrict__ key, const uint32_t* __re
 // about 18 particles at a cell side of 2h = 2.6 dx).
 __global__ void k_cell_sort(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
                             const uint32_t* __restrict__ id, int64_t n_cells, int64_t n,
-                            uint32_t* err) {
+                            uint32_t* err, const uint32_t* gate) {
+  if (closed(gate)) return;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = start[c], e = start[c + 1];
@@ -154,22 +169,26 @@ inline int grid_for(int64_t n, int threads, int sm_count, int per_sm) {
 
 }  // namespace
 
-cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches) {
+cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches,
+                        const uint32_t* gate) {
   const int64_t nb = cw.n_scan_blocks;
-  k_scan_chunks<<<(unsigned)nb, kScanThreads, 0, s>>>(cw.count, cw.start, cw.bsum, cw.n_cells);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(cw.bsum, nb, cw.start, cw.n_cells);
+  k_scan_chunks<<<(unsigned)nb, kScanThreads, 0, s>>>(cw.count, cw.start, cw.bsum, cw.n_cells,
+                                                      gate);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(cw.bsum, nb, cw.start, cw.n_cells, gate);
   k_scan_add<<<grid_for(cw.n_cells, 256, lc.sm_count, 8), 256, 0, s>>>(cw.start, cw.bsum,
-                                                                       cw.n_cells);
+                                                                       cw.n_cells, gate);
   if (launches) *launches += 3;
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
-                                cudaStream_t s, const LaunchCfg& lc, int* launches) {
+                                cudaStream_t s, const LaunchCfg& lc, int* launches,
+                                const uint32_t* gate) {
   k_scatter<<<grid_for(n, 256, lc.sm_count, 16), 256, 0, s>>>(cw.key, cw.slot, cw.start,
-                                                                cw.perm, n, cw.n_cells, cw.err);
+                                                                cw.perm, n, cw.n_cells, cw.err,
+                                                                gate);
   k_cell_sort<<<grid_for(cw.n_cells, 128, lc.sm_count, 16), 128, 0, s>>>(
-      cw.start, cw.perm, id, cw.n_cells, n, cw.err);
+      cw.start, cw.perm, id, cw.n_cells, n, cw.err, gate);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }

@@ -227,10 +227,12 @@ __device__ __forceinline__ double ipow(double x, int e) {
 // Density and Tait pressure (Eq. 4), one thread per particle, from the hit
 // bits of the FP32 prefilter of the neighbour search (sph_search.cu): every
 // candidate whose bit is set is re-tested exactly in FP64 (no fused
-// multiply-add in r^2, strict <); the neighbours are summed and written, in
-// candidate order, as i's neighbour list for the pair pass.  The walk takes
-// 4 candidates at a time: their table entries, then their position records,
-// are loaded together before they are tested.
+// multiply-add in r^2, strict <); the neighbours are summed and written as
+// i's neighbour list for the pair pass, a fluid particle's inviscid
+// neighbours first (in candidate order, count_a of them) and then the others
+// (in candidate order, from a second walk over the bits set aside for them).
+// The walk takes 4 candidates at a time: their table entries, then their
+// position records, are loaded together before they are tested.
 // kFilter: some instance uses the pressure filter; the kernel shape of every
 // list entry is then stored beside the list (nw.wsh_d) for the filter.
 template <int BLOCK, bool kFilter>
@@ -246,7 +248,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
   const int sp = (int)pi.w;
   const double m_i = sp == 0 ? P.m_s : P.m_n;
   double rho;
-  uint32_t cnt = 0;
+  uint32_t cnt = 0, count_a = kUnsplit;
   if (sp == 3) {
     rho = P.rho0;
   } else {
@@ -255,12 +257,17 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     const bool per = P.periodic_z != 0;
     MaskWalk mk(nw, n, i, g, smask + threadIdx.x, BLOCK);
     ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
+    // fluid rows without the filter: the inviscid neighbours are listed
+    // first; the others are set aside as mask bits and listed after them by a
+    // second walk (the pair pass then runs one specialised loop per part)
+    const bool split = !kFilter && sp < 2;
+    MaskKeep keep_b(mk);
     const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
     const double mD_s = P.m_s * P.aD, mD_n = P.m_n * P.aD;
     const long long cut2_bits = __double_as_longlong(P.cut2);
     rho = m_i * P.aD;  // self term W(0)
-    uint32_t e[4];
-    for (uint32_t m; (m = mk.next(e)) != 0u;) {
+    uint32_t e[4], q[4];
+    for (uint32_t m; (m = mk.next(e, q)) != 0u;) {
       dvec4 pj[4];
 #pragma unroll
       for (uint32_t u = 0; u < 4; ++u)
@@ -281,13 +288,15 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
           // r2 < (2h)^2 on the integer pipe: r2 is a sum of squares (+0 or
           // positive, or NaN), and such doubles order as their bit patterns
           const bool keep = __double_as_longlong(r2) < cut2_bits;
-          out.push(e[u], keep);  // index and cell-displacement code
+          const bool inv_j = inviscid(pj[u].w);
+          if (split && keep && !inv_j) keep_b.set(q[u]);
+          out.push(e[u], keep && (inv_j || !split));  // index and cell-displacement code
           if (keep) {
             // m_j W(r) = (m_j aD) t^4 (2q + 1), t = 1 - q/2, q = r / h
             const double r = sqrt_dist(r2);
             const double t1 = fma(-half_inv_h, r, 1.0);
             const double t2 = t1 * t1;
-            const double mD = inviscid(pj[u].w) ? mD_s : mD_n;
+            const double mD = inv_j ? mD_s : mD_n;
             const double Wt = t2 * t2 * fma(two_inv_h, r, 1.0);
             rho += mD * Wt;
             if (kFilter) {  // the shape of this list entry, in the list's layout
@@ -299,10 +308,22 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
       }
       if (out.pend >= (uint32_t)kDrainAt) out.drain();
     }
+    if (split) {
+      count_a = out.total();
+      keep_b.finish();  // the set-aside bits now stand in the staged mask words
+      MaskWalk mk2 = mk;
+      mk2.k = 0;
+      mk2.w = mk2.sw[0];
+      for (uint32_t m; (m = mk2.next(e)) != 0u;) {
+        for (uint32_t u = 0; u < m; ++u) out.push(e[u], true);
+        if (out.pend >= (uint32_t)kDrainAt) out.drain();
+      }
+    }
     cnt = out.finish();
     if (out.overflow()) latch(err, ERR_NEIGHBORS);
   }
   nw.count[i] = cnt;
+  nw.count_a[i] = count_a;
   const double Pres = P.p0 * ipow(rho * P.inv_rho0, P.alphaP) - P.beta_P;
   f.rho[i] = rho;
   f.P[i] = Pres;
@@ -365,86 +386,65 @@ k_pfilter_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
 
 // ------------------------------------------------------------------ pair pass
 
-// kOpt: kOptLiteral if some instance uses the literal F_sn (coefficient of
-// v_ij), kOptCollision if some instance uses the collision model; the
-// default form (0) has neither and drops both at compile time.
-template <int BLOCK, int kOpt>
-__global__ void __launch_bounds__(BLOCK, kOpt ? 512 / BLOCK : 0)
-k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst,
-              CellWs cw, NbrWs nw, uint32_t* err) {
-  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  if (i >= n) return;
-  const dvec4 pi = b.pos[i];
-  const int sp_i = (int)pi.w;
-  if (sp_i >= 2) {
-    const dvec4 z = {0.0, 0.0, 0.0, 0.0};
-    f.acc[i] = z;
-    f.dspin[i] = z;
-    f.tw[i] = z;
-    return;
-  }
-  const InstDev& P = inst[b.inst[i]];
-  const dvec4 vi = b.vel[i];   // w = V_i
-  const dvec4 wi = b.spin[i];  // w = P_i / rho_i^2
-  const double m_i = sp_i == 0 ? P.m_s : P.m_n;
-  const double inv_I = sp_i == 0 ? P.inv_I_s : P.inv_I_n;
-  const uint32_t fl = P.flags;
-  // per-particle coefficients with the term switches and V_i folded in
-  const double cP = (fl & SPH_TERM_P) ? m_i : 0.0;
-  const double cT = (fl & SPH_TERM_T) ? P.C_T * vi.w : 0.0;
-  const double cA = (fl & SPH_TERM_SH) ? P.A * vi.w : 0.0;
-  const double cB = (fl & SPH_TERM_ROT) ? P.B * vi.w : 0.0;
-  const double cN = (fl & SPH_TERM_SN) ? P.C_l * vi.w : 0.0;
-  const double hz = (fl & SPH_HPROJ) ? 0.0 : 1.0;
-  const bool literal = (kOpt & kOptLiteral) && (fl & SPH_SN_LITERAL) != 0;
-  const bool inv_i = sp_i == 0;
-  // collision model: the bits of col_dist^2 (0 when off; r^2 > 0 orders like
-  // its bits); its coefficient -(1 + e) mu_ij / dt is read, for the rare
-  // colliding pair only, from the table indexed by the species sum, so both
-  // sides of a pair read one value
-  const long long col2b = (kOpt & kOptCollision) ? __double_as_longlong(P.col2) : 0ll;
-  const int si = inv_i ? 0 : 1;
-  // The species factors of the pair terms depend on j only through whether
-  // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
-  // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
-  // rotational); walls count as viscous.
-  const double mX0 = inv_i ? 0.0 : 1.0, mX1 = inv_i ? 1.0 : 0.0;
-  const double mV1 = inv_i ? 0.0 : 1.0;
-  // The kernel constants cF (in F) and aD (in W) are folded in here, so
-  // that the pair loop forms only the shapes t^3 and t^4 (2q + 1).
-  const double cP0 = cP * P.m_s * P.cF, cP1 = cP * P.m_n * P.cF;
-  const double cT0 = cT * mX0 * P.cF, cT1 = cT * mX1 * P.cF;
-  const double cBA1 = mV1 != 0.0 ? (cB - cA) * P.cF : 0.0;
-  const double cB1 = -cB * mV1 * P.cF;
-  const double cN0 = -cN * mX0 * P.aD, cN1 = -cN * mX1 * P.aD;
-  const bool hproj = hz == 0.0;
-  const double half_inv_h = 0.5 * P.inv_h, two_inv_h = 2.0 * P.inv_h;
-  const double hwx = 0.5 * wi.x, hwy = 0.5 * wi.y, hwz = 0.5 * wi.z;
-  const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
-  const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
-  const bool per = P.periodic_z != 0;
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  double tx = 0.0, ty = 0.0, tz = 0.0;
-  double wx = 0.0, wy = 0.0, wz = 0.0;
-  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
+// The pair terms a neighbour brings depend on the species of the pair
+// (walls count as viscous): two inviscid particles exchange the pressure
+// term alone; unlike species the pressure, interfacial and local-interaction
+// terms (and the latter's spin torque); two viscous particles the pressure,
+// shear and rotational terms and the rotational torque.  The density pass
+// lists a fluid particle's inviscid neighbours first (count_a of them), and
+// the pair pass runs over the fluid particles in species order (all inviscid
+// ones, then all viscous ones), so that each warp walks the two parts of its
+// lists with one specialised loop each: kPathII, kPathIX, kPathVV.  kPathAll
+// is the unspecialised loop for unsplit lists (the pressure filter's runs).
+enum { kPathAll = 0, kPathII = 1, kPathIX = 2, kPathVV = 3 };
+
+// Per-particle constants of the pair pass, with the term switches, V_i and
+// the kernel constants folded in.
+struct PairCtx {
+  dvec4 pi, vi, wi;          // own records: position+species, velocity+V, spin+P/rho^2
+  double cP0, cP1;           // pressure coefficient for an inviscid / other j
+  double cT0, cT1;           // interfacial, j inviscid / other (zero for like species)
+  double cBA1, cB1;          // shear - rotational along r, rotational along u (j other)
+  double cN0, cN1;           // local interaction (zero for like species)
+  double half_inv_h, two_inv_h;
+  double hwx, hwy, hwz;      // half the own spin
+  long long col2b;           // collision distance^2 bits (0: off)
+  int si, cz_i;
+  bool hproj, literal, per;
+};
+
+struct PairSums {
+  double fx = 0.0, fy = 0.0, fz = 0.0;  // force
+  double tx = 0.0, ty = 0.0, tz = 0.0;  // spin torque (times -2)
+  double wx = 0.0, wy = 0.0, wz = 0.0;  // torque of the walls on the particle
+};
+
+// Entries t_begin .. t_end of particle i's list, one 32-byte group at a time.
+template <int kPath, int kOpt>
+__device__ __forceinline__ void pair_loop(const PairCtx& C, const InstDev& P, const Fp64Buf& b,
+                                          const NbrWs& nw, int64_t n, int64_t i,
+                                          uint32_t t_begin, uint32_t t_end, uint32_t* err,
+                                          PairSums& S) {
   const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
-  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
-    // one group of 8 entries (a 32-byte sector) per read
-    const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
-    const uint4 ga = groups[g], gb = groups[g + 1];
+  const dvec4 pi = C.pi, vi = C.vi, wi = C.wi;
+  for (uint32_t t = t_begin; t < t_end;) {
+    const uint32_t g0 = t >> 3;
+    const int64_t gi = 2 * ((int64_t)g0 * n + i);
+    const uint4 ga = groups[gi], gb = groups[gi + 1];
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
-    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+    const uint32_t u0 = t & 7u;
+    const uint32_t u1 = t_end - (g0 << 3) < 8u ? t_end - (g0 << 3) : 8u;
+    t = (g0 + 1) << 3;
 #pragma unroll
     for (uint32_t u = 0; u < 8; ++u) {
-      if (u >= m) break;
+      if (u < u0) continue;
+      if (u >= u1) break;
       const uint32_t j = checked_index(e[u] & kNbrIndexMask, n, err);
       const dvec4 pj = b.pos[j];
-      const dvec4 vj = b.vel[j];
-      const dvec4 wj = b.spin[j];
       const double dx = pi.x - pj.x, dy = pi.y - pj.y;
       double dz = pi.z - pj.z;
-      if (per) {  // minimum image across the z period
-        const int wz = z_wrap(e[u], cz_i, P.nz);
+      if (C.per) {  // minimum image across the z period
+        const int wz = z_wrap(e[u], C.cz_i, P.nz);
         if (wz > 0) dz += P.Hz;
         else if (wz < 0) dz -= P.Hz;
       }
@@ -455,78 +455,331 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
       if (!(r2b > 0 && r2b <= 0x7ff0000000000000LL)) continue;
       const double inv_r = rsqrt(r2);
       const double r = r2 * inv_r;
-      const double inv_r2 = inv_r * inv_r;
-      const double t1 = fma(-half_inv_h, r, 1.0);          // 1 - q/2
+      const double t1 = fma(-C.half_inv_h, r, 1.0);  // 1 - q/2
       const double t2 = t1 * t1;
-      const double F = t2 * t1;                             // F / cF
-      const double W = t2 * t2 * fma(two_inv_h, r, 1.0);    // W / aD
-      const bool vis_j = !inviscid(pj.w);
+      const double F = t2 * t1;                      // F / cF
+      if (kPath == kPathII) {
+        // two inviscid particles: the pressure term alone (and a collision);
+        // j is fluid, so no wall torque
+        const double Prj = b.spin[j].w;
+        double al = C.cP0 * (wi.w + Prj) * F;
+        if (kOpt & kOptCollision) {
+          const dvec4 vj = b.vel[j];
+          const double dv = dx * (vi.x - vj.x) + dy * (vi.y - vj.y) + dz * (vi.z - vj.z);
+          if (r2b < C.col2b && __double2hiint(dv) < 0) al += P.cC[0] * dv * (inv_r * inv_r);
+        }
+        S.fx = fma(al, dx, S.fx);
+        S.fy = fma(al, dy, S.fy);
+        S.fz = fma(al, dz, S.fz);
+        continue;
+      }
+      const dvec4 vj = b.vel[j];
+      const dvec4 wj = b.spin[j];
+      // whether j is viscous (or a wall): fixed by the list part except in
+      // the unspecialised loop (unlike species: j is viscous iff i is not)
+      const bool vis_j = kPath == kPathVV ? true
+                       : kPath == kPathIX ? C.si == 0
+                                          : !inviscid(pj.w);
       // relative velocity v_ij and spin-corrected u_ij = v_ij + 1/2 r_ij x (w_i + w_j),
       // with s = (w_i + w_j) / 2
       const double vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-      const double sx = fma(0.5, wj.x, hwx), sy = fma(0.5, wj.y, hwy), sz = fma(0.5, wj.z, hwz);
+      const double sx = fma(0.5, wj.x, C.hwx), sy = fma(0.5, wj.y, C.hwy),
+                   sz = fma(0.5, wj.z, C.hwz);
       const double ux = fma(dy, sz, fma(-dz, sy, vx));
       const double uy = fma(dz, sx, fma(-dx, sz, vy));
       const double uz = fma(dx, sy, fma(-dy, sx, vz));
-      const double dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
       // The five pair terms collected along r_ij and u_ij (and v_ij for the
       // literal F_sn): shear -A V_iV_j F (e.v) e = -A V_iV_j F dv/r^2 r_ij,
       // rotational -B V_iV_j F (u - (e.u) e) = -B V_iV_j F u + B V_iV_j F dv/r^2 r_ij
       // (r_ij . u_ij = r_ij . v_ij: the spin part of u_ij is normal to r_ij).
       const double VF = vj.w * F;
-      const double aP = (vis_j ? cP1 : cP0) * (wi.w + wj.w) * F;
-      const double aT = (vis_j ? cT1 : cT0) * VF;
-      const double aV = vis_j ? VF * inv_r2 * (cBA1 * dv) : 0.0;
-      const double bR = vis_j ? cB1 * VF : 0.0;
-      const double bN = (vis_j ? cN1 : cN0) * vj.w * W;
+      double aP, aT = 0.0, aV = 0.0, bR = 0.0, bN = 0.0, dv = 0.0;
+      const bool need_dv = kPath != kPathIX || (kOpt & kOptCollision);
+      if (need_dv) dv = dx * vx + dy * vy + dz * vz;  // r_ij . v_ij
+      if (kPath == kPathIX) {  // unlike species: pressure, interfacial, F_sn
+        const double W = t2 * t2 * fma(C.two_inv_h, r, 1.0);  // W / aD
+        aP = (vis_j ? C.cP1 : C.cP0) * (wi.w + wj.w) * F;
+        aT = (vis_j ? C.cT1 : C.cT0) * VF;
+        bN = (vis_j ? C.cN1 : C.cN0) * vj.w * W;
+      } else if (kPath == kPathVV) {  // like viscous species: pressure, shear, rotational
+        aP = C.cP1 * (wi.w + wj.w) * F;
+        aV = VF * (inv_r * inv_r) * (C.cBA1 * dv);
+        bR = C.cB1 * VF;
+      } else {  // any pair
+        const double W = t2 * t2 * fma(C.two_inv_h, r, 1.0);
+        aP = (vis_j ? C.cP1 : C.cP0) * (wi.w + wj.w) * F;
+        aT = (vis_j ? C.cT1 : C.cT0) * VF;
+        aV = vis_j ? VF * (inv_r * inv_r) * (C.cBA1 * dv) : 0.0;
+        bR = vis_j ? C.cB1 * VF : 0.0;
+        bN = (vis_j ? C.cN1 : C.cN0) * vj.w * W;
+      }
       double base = aP + aV;  // the z component drops aT under the projection
       // collision of an approaching pair closer than col_dist: the central
       // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij;
       // both tests on the bits (dv < 0: its sign bit; -0 adds nothing)
-      if ((kOpt & kOptCollision) && r2b < col2b && __double2hiint(dv) < 0)
-        base += P.cC[si + (vis_j ? 1 : 0)] * dv * inv_r2;
+      if ((kOpt & kOptCollision) && r2b < C.col2b && __double2hiint(dv) < 0)
+        base += P.cC[C.si + (vis_j ? 1 : 0)] * dv * (inv_r * inv_r);
       const double al = base + aT;
-      const double alz = hproj ? base : al;
-      const double bu = literal ? bR : bR + bN;  // coefficient of u_ij
+      const double alz = C.hproj ? base : al;
+      const double bu = C.literal ? bR : bR + bN;  // coefficient of u_ij
       // The pair force al r_ij + bu u_ij (+ bN v_ij) goes into the sums one
       // fused multiply-add per term, and so does the spin torque
       // -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij), whose factor
       // -1/2 (exact) is applied to the sums: the FP64 pipe bounds this loop.
       const double cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
-      fx = fma(al, dx, fma(bu, ux, fx));
-      fy = fma(al, dy, fma(bu, uy, fy));
-      fz = fma(alz, dz, fma(bu, uz, fz));
-      if ((kOpt & kOptLiteral) && literal) {  // coefficient bN of v_ij
-        fx = fma(bN, vx, fx);
-        fy = fma(bN, vy, fy);
-        fz = fma(bN, vz, fz);
+      S.fx = fma(al, dx, fma(bu, ux, S.fx));
+      S.fy = fma(al, dy, fma(bu, uy, S.fy));
+      S.fz = fma(alz, dz, fma(bu, uz, S.fz));
+      if ((kOpt & kOptLiteral) && C.literal) {  // coefficient bN of v_ij
+        S.fx = fma(bN, vx, S.fx);
+        S.fy = fma(bN, vy, S.fy);
+        S.fz = fma(bN, vz, S.fz);
       }
-      tx = fma(bu, cx, tx);
-      ty = fma(bu, cy, ty);
-      tz = fma(bu, cz, tz);
+      S.tx = fma(bu, cx, S.tx);
+      S.ty = fma(bu, cy, S.ty);
+      S.tz = fma(bu, cz, S.tz);
       if (is_wall(pj.w)) {  // torque exerted by the wall on particle i
         double pfx = al * dx + bu * ux;
         double pfy = al * dy + bu * uy;
         double pfz = alz * dz + bu * uz;
-        if ((kOpt & kOptLiteral) && literal) {
+        if ((kOpt & kOptLiteral) && C.literal) {
           pfx += bN * vx;
           pfy += bN * vy;
           pfz += bN * vz;
         }
-        wx += fma(-0.5, bu * cx, pi.y * pfz - pi.z * pfy);
-        wy += fma(-0.5, bu * cy, pi.z * pfx - pi.x * pfz);
-        wz += fma(-0.5, bu * cz, pi.x * pfy - pi.y * pfx);
+        S.wx += fma(-0.5, bu * cx, pi.y * pfz - pi.z * pfy);
+        S.wy += fma(-0.5, bu * cy, pi.z * pfx - pi.x * pfz);
+        S.wz += fma(-0.5, bu * cz, pi.x * pfy - pi.y * pfx);
       }
     }
   }
+}
+
+// kOpt: kOptLiteral if some instance uses the literal F_sn (coefficient of
+// v_ij), kOptCollision if some instance uses the collision model; the
+// default form (0) has neither and drops both at compile time.  Thread t
+// takes the fluid particle order[t]: t < n_inv are the inviscid ones, and
+// the threads from the fluid count on (the grid covers all n) return.
+template <int BLOCK, int kOpt>
+__global__ void __launch_bounds__(BLOCK, kOpt ? 512 / BLOCK : 0)
+k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
+              NbrWs nw, uint32_t* err, int64_t part_totals) {
+  const int64_t t = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (t >= (int64_t)nw.part[part_totals + 1]) return;
+  const int64_t n_inv = nw.part[part_totals];
+  const int64_t i = checked_index(nw.order[t], n, err);
+  PairCtx C;
+  C.pi = b.pos[i];
+  const int sp_i = (int)C.pi.w;
+  const InstDev& P = inst[b.inst[i]];
+  C.vi = b.vel[i];   // w = V_i
+  C.wi = b.spin[i];  // w = P_i / rho_i^2
+  const double m_i = sp_i == 0 ? P.m_s : P.m_n;
+  const double inv_I = sp_i == 0 ? P.inv_I_s : P.inv_I_n;
+  const uint32_t fl = P.flags;
+  const double cP = (fl & SPH_TERM_P) ? m_i : 0.0;
+  const double cT = (fl & SPH_TERM_T) ? P.C_T * C.vi.w : 0.0;
+  const double cA = (fl & SPH_TERM_SH) ? P.A * C.vi.w : 0.0;
+  const double cB = (fl & SPH_TERM_ROT) ? P.B * C.vi.w : 0.0;
+  const double cN = (fl & SPH_TERM_SN) ? P.C_l * C.vi.w : 0.0;
+  C.literal = (kOpt & kOptLiteral) && (fl & SPH_SN_LITERAL) != 0;
+  const bool inv_i = sp_i == 0;
+  // collision model: the bits of col_dist^2 (0 when off; r^2 > 0 orders like
+  // its bits); its coefficient -(1 + e) mu_ij / dt is read, for the rare
+  // colliding pair only, from the table indexed by the species sum, so both
+  // sides of a pair read one value
+  C.col2b = (kOpt & kOptCollision) ? __double_as_longlong(P.col2) : 0ll;
+  C.si = inv_i ? 0 : 1;
+  // The species factors of the pair terms depend on j only through whether
+  // j is inviscid (suffix 0) or not (suffix 1): mX = 1 for unlike species
+  // (interfacial force, F_sn), mV = 1 for two viscous particles (shear,
+  // rotational); walls count as viscous.
+  const double mX0 = inv_i ? 0.0 : 1.0, mX1 = inv_i ? 1.0 : 0.0;
+  const double mV1 = inv_i ? 0.0 : 1.0;
+  // The kernel constants cF (in F) and aD (in W) are folded in here, so
+  // that the pair loop forms only the shapes t^3 and t^4 (2q + 1).
+  C.cP0 = cP * P.m_s * P.cF;
+  C.cP1 = cP * P.m_n * P.cF;
+  C.cT0 = cT * mX0 * P.cF;
+  C.cT1 = cT * mX1 * P.cF;
+  C.cBA1 = mV1 != 0.0 ? (cB - cA) * P.cF : 0.0;
+  C.cB1 = -cB * mV1 * P.cF;
+  C.cN0 = -cN * mX0 * P.aD;
+  C.cN1 = -cN * mX1 * P.aD;
+  C.hproj = (fl & SPH_HPROJ) != 0;
+  C.half_inv_h = 0.5 * P.inv_h;
+  C.two_inv_h = 2.0 * P.inv_h;
+  C.hwx = 0.5 * C.wi.x;
+  C.hwy = 0.5 * C.wi.y;
+  C.hwz = 0.5 * C.wi.z;
+  const int64_t g = (int64_t)cw.skey[i] / P.slabs;  // grid cell
+  C.cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
+  C.per = P.periodic_z != 0;
+  PairSums S;
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
+  const uint32_t ca = nw.count_a[i];
+  if (ca == kUnsplit) {
+    pair_loop<kPathAll, kOpt>(C, P, b, nw, n, i, 0u, cnt, err, S);
+  } else {
+    const uint32_t na = ca < cnt ? ca : cnt;
+    // the inviscid neighbours, then the others: the warp's particles are of
+    // one species except at the boundary of the two parts of the order
+    if (t < n_inv) {
+      pair_loop<kPathII, kOpt>(C, P, b, nw, n, i, 0u, na, err, S);
+      pair_loop<kPathIX, kOpt>(C, P, b, nw, n, i, na, cnt, err, S);
+    } else {
+      pair_loop<kPathIX, kOpt>(C, P, b, nw, n, i, 0u, na, err, S);
+      pair_loop<kPathVV, kOpt>(C, P, b, nw, n, i, na, cnt, err, S);
+    }
+  }
   const double inv_m = 1.0 / m_i;
-  f.acc[i] = dvec4{fx * inv_m, fy * inv_m, fz * inv_m, 0.0};
-  tx *= -0.5;
-  ty *= -0.5;
-  tz *= -0.5;
+  f.acc[i] = dvec4{S.fx * inv_m, S.fy * inv_m, S.fz * inv_m, 0.0};
+  const double tx = -0.5 * S.tx, ty = -0.5 * S.ty, tz = -0.5 * S.tz;
   f.dspin[i] = dvec4{tx * inv_I, ty * inv_I, tz * inv_I, 0.0};
-  f.tw[i] = dvec4{wx, wy, wz, 0.0};
-  if (!finite3(fx, fy, fz) || !finite3(tx, ty, tz)) latch(err, ERR_NONFINITE);
+  f.tw[i] = dvec4{S.wx, S.wy, S.wz, 0.0};
+  if (!finite3(S.fx, S.fy, S.fz) || !finite3(tx, ty, tz)) latch(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------ species partition
+
+// Stable partition of the fluid particles by species for the pair pass,
+// deterministic (no atomics): per tile of kPartTile sorted particles, the
+// counts of inviscid and viscous fluid; their exclusive scans over the tiles
+// (inviscid first); then each tile writes its particles' indices in order.
+// Wall rows, which the pair pass does not visit, get zero accelerations and
+// wall torque here.
+constexpr int kPartThreads = 256;
+constexpr int kPartPer = kPartTile / kPartThreads;  // 16 consecutive particles per thread
+
+__device__ __forceinline__ int fluid_class(double w) {  // 0 inviscid, 1 viscous, 2 wall
+  return inviscid(w) ? 0 : (is_wall(w) ? 2 : 1);
+}
+
+// Exclusive block scan of two counts at once (kPartThreads threads).
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t v, uint32_t& ea, uint32_t& ev,
+                                            uint32_t& ta, uint32_t& tv) {
+  __shared__ uint32_t wa[32], wv[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t ia = a, iv = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t xa = __shfl_up_sync(~0u, ia, o), xv = __shfl_up_sync(~0u, iv, o);
+    if (lane >= o) {
+      ia += xa;
+      iv += xv;
+    }
+  }
+  if (lane == 31) {
+    wa[warp] = ia;
+    wv[warp] = iv;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = kPartThreads / 32;
+    uint32_t sa = lane < nw ? wa[lane] : 0u, sv = lane < nw ? wv[lane] : 0u;
+    uint32_t ja = sa, jv = sv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t xa = __shfl_up_sync(~0u, ja, o), xv = __shfl_up_sync(~0u, jv, o);
+      if (lane >= o) {
+        ja += xa;
+        jv += xv;
+      }
+    }
+    if (lane < nw) {
+      wa[lane] = ja - sa;
+      wv[lane] = jv - sv;
+    }
+    if (lane == nw - 1) {
+      wa[31] = ja;
+      wv[31] = jv;
+    }
+  }
+  __syncthreads();
+  ea = wa[warp] + ia - a;
+  ev = wv[warp] + iv - v;
+  ta = wa[31];
+  tv = wv[31];
+}
+
+__global__ void __launch_bounds__(kPartThreads)
+k_part_count(int64_t n, Fp64Buf b, uint32_t* __restrict__ part) {
+  const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartPer;
+  uint32_t a = 0, v = 0;
+  for (int k = 0; k < kPartPer; ++k)
+    if (base + k < n) {
+      const int c = fluid_class(b.pos[base + k].w);
+      a += c == 0;
+      v += c == 1;
+    }
+  uint32_t ea, ev, ta, tv;
+  block_scan2(a, v, ea, ev, ta, tv);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ta;
+    part[2 * blockIdx.x + 1] = tv;
+  }
+}
+
+// One block: the tile offsets (inviscid from 0, viscous after all inviscid)
+// in place, and the totals part[2 nt] = inviscid, part[2 nt + 1] = fluid.
+__global__ void __launch_bounds__(kPartThreads)
+k_part_scan(int64_t nt, uint32_t* __restrict__ part) {
+  __shared__ uint32_t carry[2];
+  if (threadIdx.x == 0) carry[0] = carry[1] = 0u;
+  __syncthreads();
+  for (int64_t t0 = 0; t0 < nt; t0 += kPartThreads) {
+    const int64_t t = t0 + threadIdx.x;
+    const uint32_t a = t < nt ? part[2 * t] : 0u, v = t < nt ? part[2 * t + 1] : 0u;
+    uint32_t ea, ev, ta, tv;
+    block_scan2(a, v, ea, ev, ta, tv);
+    const uint32_t ca = carry[0], cv = carry[1];
+    if (t < nt) {
+      part[2 * t] = ca + ea;
+      part[2 * t + 1] = cv + ev;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry[0] = ca + ta;
+      carry[1] = cv + tv;
+    }
+    __syncthreads();
+  }
+  // the viscous offsets start after every inviscid particle
+  const uint32_t n_inv = carry[0];
+  for (int64_t t = threadIdx.x; t < nt; t += kPartThreads) part[2 * t + 1] += n_inv;
+  if (threadIdx.x == 0) {
+    part[2 * nt] = n_inv;
+    part[2 * nt + 1] = n_inv + carry[1];
+  }
+}
+
+__global__ void __launch_bounds__(kPartThreads)
+k_part_scatter(int64_t n, Fp64Buf b, Fp64Fields f, const uint32_t* __restrict__ part,
+               uint32_t* __restrict__ order) {
+  const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartPer;
+  int cls[kPartPer];
+  uint32_t a = 0, v = 0;
+#pragma unroll
+  for (int k = 0; k < kPartPer; ++k) {
+    cls[k] = base + k < n ? fluid_class(b.pos[base + k].w) : 3;
+    a += cls[k] == 0;
+    v += cls[k] == 1;
+  }
+  uint32_t ea, ev, ta, tv;
+  block_scan2(a, v, ea, ev, ta, tv);
+  uint32_t oa = part[2 * blockIdx.x] + ea, ov = part[2 * blockIdx.x + 1] + ev;
+  const dvec4 z = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < kPartPer; ++k) {
+    const int64_t i = base + k;
+    if (cls[k] == 0) order[oa++] = (uint32_t)i;
+    else if (cls[k] == 1) order[ov++] = (uint32_t)i;
+    else if (cls[k] == 2) {
+      f.acc[i] = z;
+      f.dspin[i] = z;
+      f.tw[i] = z;
+    }
+  }
 }
 
 // ----------------------------------------------------------- load / unload
@@ -636,6 +889,12 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                const InstDev* inst, const CellWs& cw, const NbrWs& nw,
                                uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
                                int* launches) {
+  // the species partition of the fluid particles, then the pair pass over it
+  const int64_t nt = (n + kPartTile - 1) / kPartTile;
+  k_part_count<<<(unsigned)nt, kPartThreads, 0, s>>>(n, b, nw.part);
+  k_part_scan<<<1, kPartThreads, 0, s>>>(nt, nw.part);
+  k_part_scatter<<<(unsigned)nt, kPartThreads, 0, s>>>(n, b, f, nw.part, nw.order);
+  if (launches) *launches += 3;
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
   // the pair pass carries only the options some instance uses
@@ -643,11 +902,11 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
   auto go = [&](auto kopt) {
     constexpr int O = decltype(kopt)::value;
     if (lc.block_forces == 256)
-      k_forces_fp64<256, O><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_forces_fp64<256, O><<<g256, 256, 0, s>>>(n, b, f, inst, cw, nw, err, 2 * nt);
     else if (lc.block_forces == 64)
-      k_forces_fp64<64, O><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_forces_fp64<64, O><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err, 2 * nt);
     else
-      k_forces_fp64<128, O><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_forces_fp64<128, O><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err, 2 * nt);
   };
   if (opt == 0)
     go(std::integral_constant<int, 0>());

@@ -114,7 +114,35 @@ sph_status derive(const sph_params& p, InstDev& d) {
   }
   d.periodic_z = p.periodic_z ? 1 : 0;
   d.slabs = kSlabs;
-  const double side = 2.0 * h;
+  // mixed form: neighbour lists kept across steps with a skin (0 = 0.5 dx,
+  // negative = none); the cells must hold the 2h + skin stencil
+  if (!isfinite(p.skin)) return SPH_ERR_ARG;
+  d.skin = 0.0;
+  if (p.precision == SPH_MIXED) d.skin = p.skin == 0.0 ? 0.3 * p.dx : (p.skin > 0.0 ? p.skin : 0.0);
+  if (!(d.skin <= 2.0 * h)) return SPH_ERR_ARG;
+  // The cells split each axis evenly with a side >= 2h + skin.  A periodic z
+  // needs 3 cells; and where the even split would make the cells more than
+  // 5 % deeper than 2h + skin (a short axis), one more cell with a narrower
+  // skin keeps the 27-cell stencil's candidates within the table.
+  for (int pass = 0; pass < 8 && d.skin > 0.0; ++pass) {
+    double s2 = d.skin;
+    for (int a = 0; a < 3; ++a) {
+      const double L = p.box_hi[a] - p.box_lo[a];
+      if (!(L > 0) || !isfinite(L)) return SPH_ERR_ARG;
+      const double want = 2.0 * h + s2;
+      const double nc = floor(L / want);
+      double cells = -1.0;  // the cell count to fit, if any
+      if (a == 2 && d.periodic_z && nc < 3) cells = 3.0;
+      else if (nc >= 1 && L / nc > 1.05 * want) cells = nc + 1.0;
+      if (cells > 0) {
+        const double s3 = L / cells * (1.0 - 1e-12) - 2.0 * h;
+        s2 = s3 > 0.0 ? s3 : 0.0;
+      }
+    }
+    if (s2 == d.skin) break;
+    d.skin = s2;
+  }
+  const double side = 2.0 * h + d.skin;
   double xmax = 0.0;
   int32_t n[3];
   for (int a = 0; a < 3; ++a) {
@@ -194,6 +222,22 @@ sph_status derive(const sph_params& p, InstDev& d) {
   d.Omega_f = (float)p.Omega;
   d.col2_f = (float)d.col2;
   for (int k = 0; k < 3; ++k) d.cC_f[k] = (float)d.cC[k];
+  // the list-build test keeps every pair within 2h + skin (rounded up, so
+  // that no pair the exact test can accept later is lost to rounding); a
+  // rebuild is due once a particle moved 0.495 skin (both ends of a pair
+  // together less than the skin)
+  if (d.skin > 0.0) {
+    d.skin_cut2_f = nextafterf((float)((2.0 * h + d.skin) * (2.0 * h + d.skin)), INFINITY);
+    // the departure is formed from FP32 positions of up to |x| ~ 2^11 dx:
+    // 1e-3 dx of the half skin covers their rounding
+    d.skin_disp2_f = (float)((0.5 * d.skin - 1e-3 * p.dx) * (0.5 * d.skin - 1e-3 * p.dx));
+  } else {
+    d.skin_cut2_f = d.cut2_f;
+    d.skin_disp2_f = -1.0f;
+  }
+  // between builds the offsets may leave the cell by one cell side: their
+  // FP32 resolution stays that of [0, 2L)
+  d.skin_omax_f = d.cellf[0] < d.cellf[2] ? d.cellf[0] : d.cellf[2];
   return SPH_OK;
 }
 
@@ -231,6 +275,8 @@ struct sph_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool forces_valid = false;
   bool lists_valid = false;      // neighbour lists of the current sorted order
+  bool skin_valid = false;       // mixed form: the reused lists of the workspace
+                                 // belong to the state (not after a checkpoint load)
   int launches_per_step = 0;
   int64_t max_cells = 0;         // largest cell grid of an instance
   LaunchCfg lc;
@@ -265,7 +311,8 @@ int64_t backup_bytes(int32_t precision, int64_t n, int32_t n_inst) {
 }
 
 void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
-           int64_t total_chunks, int32_t cap, int32_t precision, bool filter, Carved& c) {
+           int64_t total_chunks, int32_t cap, int32_t skin_cap, int32_t precision, bool filter,
+           Carved& c) {
   memset(&c, 0, sizeof c);
   Carver s(state);
   c.inst = s.take<InstDev>(n_inst);
@@ -300,6 +347,7 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
     c.mf.tw = s.take<float4>(n);
     c.mf.delta = s.take<float>(n);
     c.mf.P = s.take<float>(n);
+    c.mf.oref = s.take<float4>(n);
   }
   c.state_bytes = s.off + kAlign;
 
@@ -321,10 +369,20 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
   c.nw.ncand = w.take<uint32_t>(n_cells / kSlabs);
   c.nw.cand = w.take<uint32_t>(n_cells / kSlabs * kMaxCand);
   c.nw.cap = cap;
-  if (precision == SPH_FP64)
+  if (precision == SPH_MIXED) {  // the reused candidate lists of the mixed form
+    c.nw.skin = w.take<uint32_t>((int64_t)skin_cap * n);
+    c.nw.skin_count = w.take<uint32_t>(n);
+    c.nw.skin_cap = skin_cap;
+  }
+  if (precision == SPH_FP64) {
     c.f.vp = w.take<dvec2>(n);
-  else
+    // the split lists and the species order of the FP64 pair pass
+    c.nw.count_a = w.take<uint32_t>(n);
+    c.nw.order = w.take<uint32_t>(n);
+    c.nw.part = w.take<uint32_t>(2 * ((n + kPartTile - 1) / kPartTile) + 2);
+  } else {
     c.mf.vp = w.take<float2>(n);
+  }
   if (filter) {  // kernel shapes of the list entries, for the pressure filter
     if (precision == SPH_FP64)
       c.nw.wsh_d = w.take<double>((int64_t)cap * n);
@@ -346,6 +404,7 @@ struct Plan {
   std::vector<InstDev> inst;
   int64_t n = 0, n_cells = 0, total_chunks = 0;
   int32_t cap = 160;
+  int32_t skin_cap = 0;          // slots of the mixed form's reused lists
   int32_t precision = SPH_FP64;
   bool any_filter = false;       // some instance uses the pressure filter
 };
@@ -375,6 +434,16 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
     kb += d.n_chunks;
   }
   if (pb > kMaxParticles || cb >= (int64_t)0xFFFFFFF0ll) return SPH_ERR_GRID_OVERFLOW;
+  // the reused lists hold the pairs within 2h + skin: the capacity of the
+  // exact lists scaled by the volume ratio of the two spheres, in groups of 8
+  if (pl.precision == SPH_MIXED) {
+    double ratio = 1.0;
+    for (const InstDev& d : pl.inst) {
+      const double q = (2.0 * d.h + d.skin) / (2.0 * d.h);
+      ratio = std::max(ratio, q * q * q);
+    }
+    pl.skin_cap = (int32_t)(ceil(pl.cap * ratio / kNbrGroup) * kNbrGroup);
+  }
   pl.n = pb;
   pl.n_cells = cb;
   pl.total_chunks = kb;
@@ -426,42 +495,91 @@ const char* const kStageNames[kStages] = {
 
 bool mixed(const sph_ctx* c) { return c->precision == SPH_MIXED; }
 
+// FP64 form: kick + drift (mode 1) or wall placement (mode 0) with the cell
+// keys, scan, scatter and cell sort, and the reorder into the other buffer.
 sph_status enqueue_cells(sph_ctx* c, cudaStream_t s, int mode, int* launches,
                          Marks* m = nullptr) {
   const int a = c->cur, b = 1 - c->cur;
   mark(m, s);
   CK(cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s));
-  if (mixed(c))
-    CK(launch_kick_drift_mixed(c->n, c->mbuf[a], c->mf, c->inst, c->ist, c->cw, c->err, mode, s,
-                               c->lc, launches));
-  else
-    CK(launch_kick_drift_fp64(c->n, c->buf[a], c->f, c->inst, c->ist, c->cw, c->err, mode, s,
-                              c->lc, launches));
+  CK(launch_kick_drift_fp64(c->n, c->buf[a], c->f, c->inst, c->ist, c->cw, c->err, mode, s,
+                            c->lc, launches));
   mark(m, s);
   CK(launch_scan(c->cw, s, c->lc, launches));
   mark(m, s);
-  CK(launch_scatter_sort(c->cw, mixed(c) ? c->mbuf[a].id : c->buf[a].id, c->n, s, c->lc,
-                         launches));
+  CK(launch_scatter_sort(c->cw, c->buf[a].id, c->n, s, c->lc, launches));
   mark(m, s);
-  if (mixed(c))
-    CK(launch_reorder_mixed(c->n, c->mbuf[a], c->mbuf[b], c->cw, s, c->lc, launches));
-  else
-    CK(launch_reorder_fp64(c->n, c->buf[a], c->buf[b], c->cw, c->nw, s, c->lc, launches));
+  CK(launch_reorder_fp64(c->n, c->buf[a], c->buf[b], c->cw, c->nw, s, c->lc, launches));
   return SPH_OK;
 }
 
-sph_status enqueue_search(sph_ctx* c, cudaStream_t s, int* launches) {
-  const float4* rec = mixed(c) ? c->mbuf[c->cur].off : c->nw.posf;
+// Neighbour search: the FP64 form's prefilter on the rounded positions; the
+// mixed form's list-build test on the offsets of the last build (gate: only
+// the instances that rebuild in this step; null: all).
+sph_status enqueue_search(sph_ctx* c, cudaStream_t s, int* launches,
+                          const InstState* gate = nullptr) {
+  const float4* rec = mixed(c) ? c->mf.oref : c->nw.posf;
   const uint32_t* inst_of = mixed(c) ? c->mbuf[c->cur].inst : c->buf[c->cur].inst;
   CK(launch_cell_search(mixed(c), c->n, rec, inst_of, c->inst, c->n_inst, c->max_cells, c->cw,
-                        c->nw, c->err, s, c->lc, launches));
+                        c->nw, c->err, s, c->lc, launches, gate));
+  return SPH_OK;
+}
+
+// Mixed form: the gated list build of a step after the drift (keys, scan,
+// scatter and cell sort, reorder and copy-back, then per instance the search
+// and the compaction into the reused lists), and the gate closed.
+sph_status enqueue_build_mixed(sph_ctx* c, cudaStream_t s, int mode, int* launches,
+                               Marks* m = nullptr) {
+  const uint32_t* gate = c->err + kErrRebuild;
+  CK(launch_keys_mixed(c->n, c->mbuf[0], c->inst, c->ist, c->cw, c->err, mode, s, c->lc,
+                       launches));
+  mark(m, s);
+  CK(launch_scan(c->cw, s, c->lc, launches, gate));
+  mark(m, s);
+  CK(launch_scatter_sort(c->cw, c->mbuf[0].id, c->n, s, c->lc, launches, gate));
+  mark(m, s);
+  CK(launch_reorder_mixed(c->n, c->mbuf[0], c->mbuf[1], c->cw, gate, s, c->lc, launches));
+  CK(launch_copyback_mixed(c->n, c->mbuf[1], c->mbuf[0], c->mf, c->ist, gate, s, c->lc,
+                           launches));
+  mark(m, s);
+  sph_status st = enqueue_search(c, s, launches, c->ist);
+  if (st != SPH_OK) return st;
+  CK(launch_skin_list_mixed(c->n, c->mbuf[0], c->inst, c->ist, c->cw, c->nw, c->err, 1, s,
+                            launches));
+  CK(launch_gate(false, c->n_inst, c->inst, c->ist, c->err, mode, s, launches));
+  c->skin_valid = true;
+  return SPH_OK;
+}
+
+// Mixed form: a build of every instance's lists at the current positions
+// (initial evaluation, a standalone cell build): walls placed at the current
+// phase, no kick or drift.
+sph_status enqueue_forced_build_mixed(sph_ctx* c, cudaStream_t s, int* launches) {
+  CK(launch_gate(true, c->n_inst, c->inst, c->ist, c->err, 0, s, launches));
+  CK(launch_drift_mixed(c->n, c->mbuf[0], c->mf, c->inst, c->ist, c->err, 0, s, c->lc,
+                        launches));
+  return enqueue_build_mixed(c, s, 0, launches);
+}
+
+// Mixed form: the reused lists again from the cells and the offsets of the
+// last build, in the stored order (after a checkpoint load, whose workspace
+// holds none): the same masks and so the same lists as at that build.
+sph_status enqueue_relist_mixed(sph_ctx* c, cudaStream_t s) {
+  CK(cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s));
+  CK(launch_relist_keys_mixed(c->n, c->mbuf[0], c->mf, c->inst, c->cw, s, c->lc));
+  CK(launch_scan(c->cw, s, c->lc, nullptr));
+  sph_status st = enqueue_search(c, s, nullptr);
+  if (st != SPH_OK) return st;
+  CK(launch_skin_list_mixed(c->n, c->mbuf[0], c->inst, c->ist, c->cw, c->nw, c->err, 0, s,
+                            nullptr));
+  c->skin_valid = true;
   return SPH_OK;
 }
 
 sph_status enqueue_density_only(sph_ctx* c, cudaStream_t s, int* launches) {
   if (mixed(c))
-    CK(launch_density_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->cw, c->nw, c->err, s,
-                            c->lc, launches));
+    CK(launch_density_mixed(c->n, c->mbuf[c->cur], c->mf, c->inst, c->nw, c->err, s, c->lc,
+                            launches));
   else
     CK(launch_density_fp64(c->n, c->buf[c->cur], c->f, c->inst, c->cw, c->nw, c->err, s,
                            c->lc, launches));
@@ -478,10 +596,17 @@ sph_status enqueue_pfilter(sph_ctx* c, cudaStream_t s, int* launches) {
   return SPH_OK;
 }
 
-// Neighbour search, then density and pressure, then the pressure filter.
+// Neighbour search (FP64 form; the mixed form searches in its list builds
+// and reuses the lists, rebuilt first if a checkpoint load dropped them),
+// then density and pressure, then the pressure filter.
 sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
-  mark(m, s);
-  sph_status st = enqueue_search(c, s, launches);
+  sph_status st = SPH_OK;
+  if (!mixed(c)) {
+    mark(m, s);
+    st = enqueue_search(c, s, launches);
+  } else if (!c->skin_valid) {
+    st = enqueue_relist_mixed(c, s);
+  }
   if (st != SPH_OK) return st;
   mark(m, s);
   st = enqueue_density_only(c, s, launches);
@@ -521,11 +646,21 @@ sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches
   return SPH_OK;
 }
 
-// One kick-drift-kick step; flips c->cur (the reorder target becomes current).
+// One kick-drift-kick step.  FP64 form: flips c->cur (the reorder target
+// becomes current).  Mixed form: the drift, the gated list build, then the
+// passes over the reused lists; c->cur stays 0.
 sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
-  sph_status st = enqueue_cells(c, s, 1, launches, m);
+  sph_status st;
+  if (mixed(c)) {
+    mark(m, s);
+    CK(launch_drift_mixed(c->n, c->mbuf[0], c->mf, c->inst, c->ist, c->err, 1, s, c->lc,
+                          launches));
+    st = enqueue_build_mixed(c, s, 1, launches, m);
+  } else {
+    st = enqueue_cells(c, s, 1, launches, m);
+    c->cur = 1 - c->cur;
+  }
   if (st != SPH_OK) return st;
-  c->cur = 1 - c->cur;
   st = enqueue_density(c, s, launches, m);
   if (st != SPH_OK) return st;
   return enqueue_forces(c, s, 1, launches, m);
@@ -533,7 +668,7 @@ sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nu
 
 sph_status capture_graphs(sph_ctx* c) {
   const int saved = c->cur;
-  for (int g = 0; g < 2; ++g) {
+  for (int g = 0; g < (mixed(c) ? 1 : 2); ++g) {
     c->cur = (saved + g) & 1;
     const int start_cur = c->cur;
     cudaGraph_t graph = nullptr;
@@ -619,8 +754,8 @@ size_t sph_state_bytes(int32_t n_inst, const sph_params* params, const int64_t* 
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
-        pl.any_filter, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.skin_cap,
+        pl.precision, pl.any_filter, c);
   return c.state_bytes;
 }
 
@@ -628,8 +763,8 @@ size_t sph_workspace_bytes(int32_t n_inst, const sph_params* params, const int64
   Plan pl;
   if (plan(n_inst, params, counts, pl) != SPH_OK) return 0;
   Carved c;
-  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
-        pl.any_filter, c);
+  carve(nullptr, nullptr, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.skin_cap,
+        pl.precision, pl.any_filter, c);
   return c.ws_bytes;
 }
 
@@ -648,8 +783,8 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   if (((uintptr_t)dev_state % kAlign) || ((uintptr_t)dev_workspace % kAlign))
     return SPH_ERR_WORKSPACE;
   Carved cv;
-  carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap, pl.precision,
-        pl.any_filter, cv);
+  carve(dev_state, dev_workspace, n_inst, pl.n, pl.n_cells, pl.total_chunks, pl.cap,
+        pl.skin_cap, pl.precision, pl.any_filter, cv);
   if (state_bytes < cv.state_bytes || workspace_bytes < cv.ws_bytes) return SPH_ERR_WORKSPACE;
 
   sph_ctx* c = new (std::nothrow) sph_ctx();
@@ -756,8 +891,16 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
   if (le != cudaSuccess) return fail(SPH_ERR_CUDA);
   c->cur = 0;
   // initial evaluation: walls at phase 0, cells, density, forces (a_0, alpha_0)
-  if ((st = enqueue_cells(c, s, 0, nullptr)) != SPH_OK) return fail(st);
-  c->cur = 1;
+  if (mixed(c)) {
+    if (cudaMemsetAsync(c->mf.oref, 0, sizeof(float4) * (size_t)n, s) != cudaSuccess ||
+        cudaMemsetAsync(c->cw.count, 0, sizeof(uint32_t) * (size_t)c->cw.n_cells, s) !=
+            cudaSuccess)
+      return fail(SPH_ERR_CUDA);
+    if ((st = enqueue_forced_build_mixed(c, s, nullptr)) != SPH_OK) return fail(st);
+  } else {
+    if ((st = enqueue_cells(c, s, 0, nullptr)) != SPH_OK) return fail(st);
+    c->cur = 1;
+  }
   if ((st = enqueue_density(c, s, nullptr)) != SPH_OK) return fail(st);
   if ((st = enqueue_forces(c, s, 0, nullptr)) != SPH_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SPH_ERR_CUDA);
@@ -781,9 +924,14 @@ sph_status sph_init(sph_ctx** ctx, const sph_params* params, int64_t n, const do
 sph_status sph_build_cells(sph_ctx* c) {
   NvtxRange range("sph_build_cells");
   if (!c) return SPH_ERR_ARG;
-  sph_status st = enqueue_cells(c, c->stream, 0, nullptr);
+  sph_status st;
+  if (mixed(c)) {  // the mixed form builds its reused lists with the cells
+    st = enqueue_forced_build_mixed(c, c->stream, nullptr);
+  } else {
+    st = enqueue_cells(c, c->stream, 0, nullptr);
+    c->cur = 1 - c->cur;
+  }
   if (st != SPH_OK) return st;
-  c->cur = 1 - c->cur;
   c->forces_valid = false;
   c->lists_valid = false;
   return SPH_OK;
@@ -815,13 +963,17 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps) {
     if (st != SPH_OK) return st;
     c->forces_valid = true;
   }
+  if (mixed(c) && !c->skin_valid) {  // a checkpoint load dropped the reused lists
+    sph_status st = enqueue_relist_mixed(c, c->stream);
+    if (st != SPH_OK) return st;
+  }
   if (!c->graph[0]) {
     sph_status st = capture_graphs(c);
     if (st != SPH_OK) return st;
   }
   for (int32_t t = 0; t < nsteps; ++t) {
     CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-    c->cur = 1 - c->cur;
+    if (!mixed(c)) c->cur = 1 - c->cur;  // the mixed form keeps one state buffer
   }
   return SPH_OK;
 }
@@ -846,6 +998,23 @@ sph_status sph_force_breakdown(sph_ctx* c, int32_t inst, double out[5]) {
   CK(cudaMemcpyAsync(out, c->diag_out + (int64_t)inst * kDiagFields, sizeof(double) * 5,
                      cudaMemcpyDeviceToHost, c->stream));
   return sph_check(c);
+}
+
+sph_status sph_pair_census(sph_ctx* c, int32_t inst, int64_t out[5]) {
+  if (!c || !out || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
+  if (!c->lists_valid) return SPH_ERR_STATE;  // needs the lists of a density pass
+  if (mixed(c))
+    CK(launch_census_mixed(c->n_inst, c->n, c->total_chunks, c->inst, c->mbuf[c->cur], c->mf,
+                           c->nw, c->part_diag, c->diag_out, c->stream));
+  else
+    CK(launch_census_fp64(c->n_inst, c->n, c->total_chunks, c->inst, c->buf[c->cur], c->f, c->nw,
+                          c->part_diag, c->diag_out, c->stream));
+  double d[5];
+  CK(cudaMemcpyAsync(d, c->diag_out + (int64_t)inst * kDiagFields, sizeof d,
+                     cudaMemcpyDeviceToHost, c->stream));
+  const sph_status st = sph_check(c);
+  for (int q = 0; q < 5; ++q) out[q] = (int64_t)d[q];
+  return st;
 }
 
 sph_status sph_diagnostics(sph_ctx* c, int32_t inst, sph_diag* out) {
@@ -959,6 +1128,7 @@ sph_status sph_load_checkpoint(sph_ctx* c, const void* buf, size_t bytes) {
   c->cur = h.cur;
   c->forces_valid = h.forces_valid != 0;  // the accelerations came with the state
   c->lists_valid = false;                 // neighbour lists live in the workspace
+  c->skin_valid = false;                  // so do the mixed form's reused lists
   return sph_check(c);
 }
 
@@ -1127,6 +1297,9 @@ sph_status sph_autotune(sph_ctx* c, int32_t reps, int32_t* block_density, int32_
       else if (kind == 1) st = enqueue_density(c, s, nullptr);
       else st = enqueue_forces(c, s, 0, nullptr);
     }
+    // (mixed form: the search trials write only the masks and tables of a
+    // build, which its lists do not read; its density trials re-test the
+    // reused lists, so the trials leave the lists as they were)
     cudaEventRecord(e1, s);
     float ms = 0.f;
     if (st == SPH_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1186,6 +1359,16 @@ const char* sph_stage_name(int32_t stage) {
 }
 
 int32_t sph_launches_per_step(const sph_ctx* c) { return c ? c->launches_per_step : 0; }
+
+sph_status sph_list_builds(sph_ctx* c, int32_t inst, int64_t* builds) {
+  if (!c || !builds || inst < 0 || inst >= c->n_inst) return SPH_ERR_ARG;
+  InstState st;
+  CK(cudaMemcpyAsync(&st, c->ist + inst, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  const sph_status e = sph_check(c);
+  // the FP64 form builds its lists at the start and in every step
+  *builds = mixed(c) ? (int64_t)st.rebuilds : st.step + 1;
+  return e;
+}
 
 sph_status sph_set_launch_config(sph_ctx* c, int32_t block_density, int32_t block_forces,
                                  int32_t search_warps, int32_t search_depth) {

@@ -73,6 +73,16 @@ struct InstDev {
   float rho0_f, A_f, B_f, C_l_f, C_T_f;
   float dt_f, hdt_f, Omega_f;
   float col2_f, cC_f[3];
+  // Reused neighbour lists of the mixed form: the lists are built with the
+  // radius 2h + skin (cell side >= 2h + skin) and kept while every particle
+  // of the instance stays within skin/2 of where the vessel's rigid rotation
+  // since the build has carried its build position (rotation keeps every
+  // pair distance, so only the departure from it can bring a new pair inside
+  // 2h); every step re-tests r < 2h.  skin 0: rebuilt every step.
+  double skin;
+  float skin_cut2_f;              // (2h + skin)^2: the list-build test
+  float skin_disp2_f;             // rebuild when |departure|^2 exceeds this (< 0: always)
+  float skin_omax_f;              // rebuild when an offset leaves [-omax, L + omax]
 };
 
 // Mutable per-instance scalars that live on the device.
@@ -81,7 +91,10 @@ struct InstState {
   double T_wall[3];               // wall torque of the last force evaluation
   double J_wall[3];               // trapezoidal impulse of T_wall
   int64_t step;
-  int64_t pad;
+  int32_t rebuild;                // mixed form: the lists are rebuilt in this step
+  int32_t rebuilds;               // mixed form: list builds so far
+  double theta_ref;               // mixed form: wall phase at the last list build
+  double pad;
 };
 
 // One copy of the sorted FP64 particle state (double-buffered for the reorder).
@@ -128,6 +141,8 @@ struct MixFields {
   float* delta;         // rho / rho0 - 1
   float* P;
   float2* vp;           // pressure filter input (V, P); (0, 0) for outer walls
+  float4* oref;         // offsets (and species) at the last list build; the
+                        // cells stay fixed until the next build
 };
 
 constexpr uint32_t kCellBitsX = 11, kCellBitsY = 11, kCellBitsZ = 10;
@@ -167,6 +182,8 @@ constexpr int kMaxCandWords = kMaxCand / 32;
 // writes whole sectors and reads 1 KB contiguous per group.  An entry is a
 // candidate-table entry (index | displacement code).
 constexpr int kNbrGroup = 8;
+constexpr uint32_t kUnsplit = 0xFFFFFFFFu;
+constexpr int kPartTile = 4096;  // particles per tile of the species partition
 
 // Compile-time options of the pair pass (template argument kOpt).
 constexpr int kOptLiteral = 1;    // literal F_sn on v_ij (SPH_SN_LITERAL)
@@ -179,6 +196,14 @@ __host__ __device__ __forceinline__ int64_t nbr_slot(int64_t n, int64_t i, uint3
 struct NbrWs {
   uint32_t* list;       // neighbour entries, layout above
   uint32_t* count;      // neighbours per particle (list length)
+  // FP64 form: the list of a fluid particle holds its inviscid neighbours
+  // first; count_a is their number (kUnsplit: not ordered, when the
+  // pressure filter is on).  Species partition of the fluid particles for
+  // the pair pass: order[0 .. n_inv) inviscid, then the viscous ones, each in
+  // sorted order.
+  uint32_t* count_a;
+  uint32_t* order;
+  uint32_t* part;       // per-tile counts of the partition, then its totals
   float4* posf;         // FP32 copy of sorted positions (FP64-form prefilter)
   uint32_t* mask;       // [kMaxCandWords][n] candidate hit bits
   uint32_t* cand;       // [grid cells][kMaxCand] candidate table of each cell
@@ -189,9 +214,30 @@ struct NbrWs {
   double* wsh_d;        // FP64 form
   float* wsh_f;         // mixed form
   int32_t cap;          // list slots per particle (multiple of 8)
+  // Mixed form: the reused candidate lists (entries within 2h + skin at the
+  // last build, candidate-table entries in the layout of nbr_slot with
+  // skin_cap slots) and their lengths; the density pass re-tests them.
+  uint32_t* skin;
+  uint32_t* skin_count;
+  int32_t skin_cap;
 };
 
+// Error-word slots: err[0] latched error bits; err[1] (mixed form) non-zero
+// while some instance rebuilds its lists in the current step.
+constexpr int kErrRebuild = 1;
+
 #ifdef __CUDACC__
+// z of an absolute position folded into the period [lo, lo + Hz) when z is
+// periodic (mixed form: between list builds an offset may carry a particle
+// past the period's end; it is folded when positions are formed).
+__device__ __forceinline__ double fold_z(const InstDev& P, double z) {
+  if (P.periodic_z) {
+    if (z >= P.lo[2] + P.Hz) z -= P.Hz;
+    else if (z < P.lo[2]) z += P.Hz;
+  }
+  return z;
+}
+
 // Checked build (compiled with -DSPH_CHECKED): the indices the kernels take
 // from data (cell keys, sorted positions, candidate runs, neighbour entries,
 // list lengths) are bounds-checked before use; a failed check latches
@@ -256,6 +302,49 @@ struct MaskWalk {
       }
     }
     return m;
+  }
+  // The same, also giving each entry's candidate position q = 32 word + bit.
+  template <int B>
+  __device__ __forceinline__ uint32_t next(uint32_t (&e)[B], uint32_t (&q)[B]) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      while (w == 0u && k + 1 < K) w = sw[++k * stride];
+      if (w != 0u) {
+        const uint32_t bit = (uint32_t)__ffs(w) - 1u;
+        w &= w - 1u;
+        q[u] = (k << 5) + bit;
+        e[u] = tab[q[u]];
+        m = (uint32_t)u + 1u;
+      }
+    }
+    return m;
+  }
+};
+
+// Candidate positions set aside during a mask walk, as bits, written back
+// over the walk's own staged mask words once the walk has passed them (a
+// word is staged before any of its bits is returned), so that a second walk
+// over the same words yields the set-aside entries in candidate order.
+struct MaskKeep {
+  uint32_t* sw;
+  uint32_t stride, K;
+  uint32_t k = 0, acc = 0;
+  __device__ __forceinline__ MaskKeep(const MaskWalk& mk) : sw(mk.sw), stride(mk.stride), K(mk.K) {}
+  __device__ __forceinline__ void set(uint32_t q) {  // q ascending over the calls
+    const uint32_t kq = q >> 5;
+    while (k < kq) {
+      sw[k * stride] = acc;
+      acc = 0u;
+      ++k;
+    }
+    acc |= 1u << (q & 31u);
+  }
+  __device__ __forceinline__ void finish() {  // the remaining words: set-aside bits or none
+    for (; k < K; ++k) {
+      sw[k * stride] = acc;
+      acc = 0u;
+    }
   }
 };
 

@@ -21,11 +21,15 @@ struct LaunchCfg {
 };
 
 // ---- cell build (sph_cells.cu) --------------------------------------------
-// Exclusive scan of cw.count into cw.start (n_cells + 1 entries).
-cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches);
+// Exclusive scan of cw.count into cw.start (n_cells + 1 entries); the counts
+// are left at zero for the next build.  gate: the kernels do nothing while
+// *gate is zero (null: always run).
+cudaError_t launch_scan(const CellWs& cw, cudaStream_t s, const LaunchCfg& lc, int* launches,
+                        const uint32_t* gate = nullptr);
 // perm[start[key[i]] + slot[i]] = i, then sort each cell by particle id.
 cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
-                                cudaStream_t s, const LaunchCfg& lc, int* launches);
+                                cudaStream_t s, const LaunchCfg& lc, int* launches,
+                                const uint32_t* gate = nullptr);
 
 // ---- neighbour search (sph_search.cu) ---------------------------------------
 // One warp per cell of every instance (grid.y = instance); writes the
@@ -35,11 +39,13 @@ cudaError_t launch_scatter_sort(const CellWs& cw, const uint32_t* id, int64_t n,
 // exact FP32 test with cell-displacement codes; otherwise the FP32 prefilter.
 // lc.search_warps = 0 selects the thread-per-particle mapping (inst_of: the
 // instance of each sorted particle), which writes the same output.
+// gate (mixed form): only the instances whose InstState::rebuild is set are
+// searched (null: all).  The mixed form's test is r^2 < (2h + skin)^2.
 cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
                                const uint32_t* inst_of, const InstDev* inst, int32_t n_inst,
                                int64_t max_cells, const CellWs& cw, const NbrWs& nw,
                                uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
-                               int* launches);
+                               int* launches, const InstState* gate = nullptr);
 // Raise the dynamic shared-memory limit of the search kernels (once, before
 // any launch or stream capture).
 cudaError_t prepare_search_kernels();
@@ -81,17 +87,43 @@ cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
                              const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc);
 
 // ---- mixed-precision path (sph_mixed.cu) -------------------------------------
-cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
-                                    const InstDev* inst, const InstState* ist, const CellWs& cw,
-                                    uint32_t* err, int mode, cudaStream_t s, const LaunchCfg& lc,
-                                    int* launches);
+// The mixed form keeps its neighbour lists across steps (a skin, InstDev::skin)
+// and advances one state buffer (mbuf[0]; mbuf[1] is the reorder's scratch).
+// A step: drift (cells fixed; sets the rebuild gate err[kErrRebuild] and
+// InstState::rebuild of the instances that moved too far), then, gated, keys,
+// scan, scatter/sort, reorder, copy-back and (per instance) search and list
+// compaction, then density over the reused lists, pressure filter, pair pass,
+// kick, wall torque, and the gate closed.
+// mode 0: walls placed at the current phase, no kick/drift; mode 1: half kick
+// + drift + walls at the next phase.
+cudaError_t launch_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                               const InstDev* inst, InstState* ist, uint32_t* err, int mode,
+                               cudaStream_t s, const LaunchCfg& lc, int* launches);
+cudaError_t launch_keys_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
+                              const InstState* ist, const CellWs& cw, uint32_t* err, int mode,
+                              cudaStream_t s, const LaunchCfg& lc, int* launches);
+// Sorted keys and cell counts of the current order from the cells and the
+// offsets of the last build (relist after a checkpoint load; counts zero).
+cudaError_t launch_relist_keys_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                     const InstDev* inst, const CellWs& cw, cudaStream_t s,
+                                     const LaunchCfg& lc);
+// open: every instance rebuilds (the gate opened); otherwise close the gate,
+// recording the wall phase of the step's builds (mode as for the drift).
+cudaError_t launch_gate(bool open, int32_t n_inst, const InstDev* inst, InstState* ist,
+                        uint32_t* err, int mode, cudaStream_t s, int* launches);
 cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
-                                 const CellWs& cw, cudaStream_t s, const LaunchCfg& lc,
-                                 int* launches);
+                                 const CellWs& cw, const uint32_t* gate, cudaStream_t s,
+                                 const LaunchCfg& lc, int* launches);
+cudaError_t launch_copyback_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
+                                  const MixFields& f, const InstState* ist, const uint32_t* gate,
+                                  cudaStream_t s, const LaunchCfg& lc, int* launches);
+// gated: only the instances that rebuild (InstState::rebuild); 0: all.
+cudaError_t launch_skin_list_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
+                                   const InstState* ist, const CellWs& cw, const NbrWs& nw,
+                                   uint32_t* err, int gated, cudaStream_t s, int* launches);
 cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
-                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
-                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
-                                 int* launches);
+                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                 cudaStream_t s, const LaunchCfg& lc, int* launches);
 cudaError_t launch_pfilter_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                  cudaStream_t s, int* launches);
@@ -142,5 +174,16 @@ cudaError_t launch_breakdown_mixed(int32_t n_inst, int64_t n, int64_t total_chun
                                    const InstDev* inst, const MixBuf& b, const MixFields& f,
                                    const NbrWs& nw, double* partials, double* out,
                                    cudaStream_t s);
+
+// Per-instance neighbour-pair census of the current lists: ordered (fluid
+// row, neighbour) pairs by species class into out[k * kDiagFields + q],
+// q = 0 inviscid-inviscid, 1 unlike fluid, 2 viscous-viscous, 3 inviscid-wall,
+// 4 viscous-wall.
+cudaError_t launch_census_fp64(int32_t n_inst, int64_t n, int64_t total_chunks,
+                               const InstDev* inst, const Fp64Buf& b, const Fp64Fields& f,
+                               const NbrWs& nw, double* partials, double* out, cudaStream_t s);
+cudaError_t launch_census_mixed(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                const InstDev* inst, const MixBuf& b, const MixFields& f,
+                                const NbrWs& nw, double* partials, double* out, cudaStream_t s);
 
 }  // namespace sphgb

@@ -134,23 +134,40 @@ __device__ __forceinline__ bool finite3f(float a, float b, float c) {
 
 // ---------------------------------------------------------------- integrator
 
-__global__ void k_kick_drift_mixed(int64_t n, MixBuf b, MixFields f,
-                                   const InstDev* __restrict__ inst,
-                                   const InstState* __restrict__ ist, CellWs cw, uint32_t* err,
-                                   int mode) {
+// A gate word: kernels of the list build run only while it is non-zero
+// (null: always).
+__device__ __forceinline__ bool gate_closed(const uint32_t* gate) {
+  return gate != nullptr && *(const volatile uint32_t*)gate == 0u;
+}
+
+// Wall placement at the step's phase: the rigid rotation of the reference
+// position, in FP64.
+__device__ __forceinline__ void wall_xy(const InstDev& P, const InstState& S, const dvec2& r0,
+                                        int mode, double& x, double& y) {
+  double th = S.theta;
+  if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
+  double s, cs;
+  sincos(th, &s, &cs);
+  x = __dsub_rn(__dmul_rn(cs, r0.x), __dmul_rn(s, r0.y));
+  y = __dadd_rn(__dmul_rn(s, r0.x), __dmul_rn(cs, r0.y));
+}
+
+// Half kick and drift (mode 1), or the walls' placement alone (mode 0), with
+// every particle's cell held fixed: between list builds the offsets may leave
+// [0, L), which keeps the cell-displacement codes of the lists valid.  A
+// particle that departed more than half the skin from its build position
+// carried along by the vessel's rigid rotation since the build (rotation
+// keeps every pair distance), or whose offset left [-L, 2L), marks its
+// instance for a rebuild in this step (and opens the step's rebuild gate).
+__global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst,
+                              InstState* __restrict__ ist, uint32_t* err, int mode) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t k = b.inst[i];
     const InstDev& P = inst[k];
     float4 o = b.off[i];
     const int sp = (int)o.w;
-    int c[3];
-    bool ok = true;
     if (sp < 2) {
-      const uint32_t cc = b.cell[i];
-      c[0] = cell_x(cc);
-      c[1] = cell_y(cc);
-      c[2] = cell_z(cc);
       if (mode == 1) {
         float4 v = b.vel[i];
         float4 w = b.spin[i];
@@ -165,43 +182,128 @@ __global__ void k_kick_drift_mixed(int64_t n, MixBuf b, MixFields f,
         o.x += P.dt_f * v.x;
         o.y += P.dt_f * v.y;
         o.z += P.dt_f * v.z;
-        ok &= normalize(o.x, c[0], P.cellf[0], P.clo[0], P.chi[0], false, P.nx);
-        ok &= normalize(o.y, c[1], P.cellf[1], P.clo[1], P.chi[1], false, P.ny);
-        ok &= normalize(o.z, c[2], P.cellf[2], P.clo[2], P.chi[2], P.periodic_z != 0, P.nz);
         b.vel[i] = v;
         b.spin[i] = w;
         b.off[i] = o;
-        b.cell[i] = pack_cell(c[0], c[1], c[2]);
         if (!finite3f(v.x, v.y, v.z) || !finite3f(w.x, w.y, w.z)) latch(err, ERR_NONFINITE);
       }
     } else {
-      double th = ist[k].theta;
-      if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
-      double s, cs;
-      sincos(th, &s, &cs);
-      const dvec2 r0 = b.ref[i];
-      const double x = __dsub_rn(__dmul_rn(cs, r0.x), __dmul_rn(s, r0.y));
-      const double y = __dadd_rn(__dmul_rn(s, r0.x), __dmul_rn(cs, r0.y));
-      // a wall keeps its z cell and offset; x, y follow the rigid rotation
+      double x, y;
+      wall_xy(P, ist[k], b.ref[i], mode, x, y);
       const uint32_t cc = b.cell[i];
-      ok &= to_cell(P, 0, x, c[0], o.x);
-      ok &= to_cell(P, 1, y, c[1], o.y);
-      c[2] = cell_z(cc);
+      o.x = (float)((x - P.lo[0]) - (double)cell_x(cc) * P.cell[0]);
+      o.y = (float)((y - P.lo[1]) - (double)cell_y(cc) * P.cell[1]);
       b.off[i] = o;
-      b.cell[i] = pack_cell(c[0], c[1], c[2]);
       b.vel[i] = make_float4((float)(-P.Omega * y), (float)(P.Omega * x), 0.f, b.vel[i].w);
       b.spin[i] = make_float4(0.f, 0.f, P.Omega_f, b.spin[i].w);
     }
-    if (!ok) latch(err, ERR_ESCAPED);
-    int slab = (int)(o.x * ((float)P.slabs / P.cellf[0]));
-    slab = slab < 0 ? 0 : (slab >= P.slabs ? P.slabs - 1 : slab);
-    const uint32_t key = (uint32_t)(P.cell_base +
-                                    ((int64_t)c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2])) *
-                                        P.slabs +
-                                    slab);
+    const float4 r = f.oref[i];
+    const uint32_t cc = b.cell[i];
+    const float cx = (float)(P.lo[0] + (double)cell_x(cc) * P.cell[0]);
+    const float cy = (float)(P.lo[1] + (double)cell_y(cc) * P.cell[1]);
+    double th = ist[k].theta;
+    if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
+    float sn, cs;
+    sincosf((float)(th - ist[k].theta_ref), &sn, &cs);
+    const float xr = cx + r.x, yr = cy + r.y;
+    const float dx = (cx + o.x) - (cs * xr - sn * yr);
+    const float dy = (cy + o.y) - (sn * xr + cs * yr);
+    const float dz = o.z - r.z;
+    const float om = P.skin_omax_f;
+    const bool inside = o.x >= -om && o.x <= P.cellf[0] + om && o.y >= -om &&
+                        o.y <= P.cellf[1] + om && o.z >= -om && o.z <= P.cellf[2] + om;
+    if (!(dx * dx + dy * dy + dz * dz <= P.skin_disp2_f && inside) && ist[k].rebuild == 0) {
+      ist[k].rebuild = 1;
+      err[kErrRebuild] = 1u;
+    }
+  }
+}
+
+// Sort keys of a list build (the rebuild gate open): particles of the
+// instances that rebuild get their offsets back into [0, L) (moving whole
+// cells; walls are placed exactly at the step's phase) and the key of their
+// new cell; the other instances keep the keys of their last sort, so that
+// the sort leaves their order, and with it their lists, unchanged.  Every
+// particle takes an arrival slot in its key's count.
+__global__ void k_keys_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
+                             const InstState* __restrict__ ist, CellWs cw, uint32_t* err,
+                             int mode) {
+  if (gate_closed(err + kErrRebuild)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = b.inst[i];
+    uint32_t key;
+    if (ist[k].rebuild) {
+      const InstDev& P = inst[k];
+      float4 o = b.off[i];
+      const uint32_t cc = b.cell[i];
+      int c[3] = {cell_x(cc), cell_y(cc), cell_z(cc)};
+      bool ok = true;
+      if ((int)o.w < 2) {
+        ok &= normalize(o.x, c[0], P.cellf[0], P.clo[0], P.chi[0], false, P.nx);
+        ok &= normalize(o.y, c[1], P.cellf[1], P.clo[1], P.chi[1], false, P.ny);
+        ok &= normalize(o.z, c[2], P.cellf[2], P.clo[2], P.chi[2], P.periodic_z != 0, P.nz);
+      } else {  // a wall keeps its z cell and offset; x, y follow the rotation
+        double x, y;
+        wall_xy(P, ist[k], b.ref[i], mode, x, y);
+        ok &= to_cell(P, 0, x, c[0], o.x);
+        ok &= to_cell(P, 1, y, c[1], o.y);
+      }
+      if (!ok) latch(err, ERR_ESCAPED);
+      b.off[i] = o;
+      b.cell[i] = pack_cell(c[0], c[1], c[2]);
+      int slab = (int)(o.x * ((float)P.slabs / P.cellf[0]));
+      slab = slab < 0 ? 0 : (slab >= P.slabs ? P.slabs - 1 : slab);
+      key = (uint32_t)(P.cell_base +
+                       ((int64_t)c[0] + (int64_t)P.nx * (c[1] + (int64_t)P.ny * c[2])) * P.slabs +
+                       slab);
+    } else {
+      key = cw.skey[i];
+    }
     cw.key[i] = key;
     cw.slot[i] = atomicAdd(&cw.count[key], 1u);
   }
+}
+
+// Keys of the current order recomputed from the cells and the offsets of the
+// last build (after a checkpoint load, whose workspace holds no lists): the
+// order is already sorted by them, so the counts, their scan and the sorted
+// keys are all a relist needs.
+__global__ void k_relist_keys_mixed(int64_t n, MixBuf b, MixFields f,
+                                    const InstDev* __restrict__ inst, CellWs cw) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const InstDev& P = inst[b.inst[i]];
+    const uint32_t cc = b.cell[i];
+    int slab = (int)(f.oref[i].x * ((float)P.slabs / P.cellf[0]));
+    slab = slab < 0 ? 0 : (slab >= P.slabs ? P.slabs - 1 : slab);
+    const uint32_t key = (uint32_t)(
+        P.cell_base +
+        ((int64_t)cell_x(cc) + (int64_t)P.nx * (cell_y(cc) + (int64_t)P.ny * cell_z(cc))) *
+            P.slabs +
+        slab);
+    cw.skey[i] = key;
+    atomicAdd(&cw.count[key], 1u);
+  }
+}
+
+// Open the rebuild gate of every instance (initial evaluation, a standalone
+// cell build) / close it at the end of a step, counting the builds.
+__global__ void k_gate_force(int32_t n_inst, InstState* ist, uint32_t* err) {
+  for (int32_t k = threadIdx.x; k < n_inst; k += blockDim.x) ist[k].rebuild = 1;
+  if (threadIdx.x == 0) err[kErrRebuild] = 1u;
+}
+__global__ void k_gate_close(int32_t n_inst, const InstDev* __restrict__ inst, InstState* ist,
+                             uint32_t* err, int mode) {
+  for (int32_t k = threadIdx.x; k < n_inst; k += blockDim.x)
+    if (ist[k].rebuild) {  // the wall phase the new lists were built at
+      double th = ist[k].theta;
+      if (mode == 1) th = __dadd_rn(th, __dmul_rn(inst[k].Omega, inst[k].dt));
+      ist[k].theta_ref = th;
+      ist[k].rebuild = 0;
+      ist[k].rebuilds += 1;
+    }
+  if (threadIdx.x == 0) err[kErrRebuild] = 0u;
 }
 
 __global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst) {
@@ -224,7 +326,9 @@ __global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __
   }
 }
 
-__global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
+__global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw,
+                                const uint32_t* gate) {
+  if (gate_closed(gate)) return;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t j = checked_index(cw.perm[k], n, cw.err);
@@ -239,22 +343,84 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw) {
   }
 }
 
+// The sorted state back into the main buffer (the step's kernels all read
+// one buffer); the instances that rebuilt record their offsets as the
+// reference of the new lists.
+__global__ void k_copyback_mixed(int64_t n, MixBuf src, MixBuf dst, MixFields f,
+                                 const InstState* __restrict__ ist, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float4 o = src.off[k];
+    const uint32_t q = src.inst[k];
+    dst.cell[k] = src.cell[k];
+    dst.off[k] = o;
+    dst.vel[k] = src.vel[k];
+    dst.spin[k] = src.spin[k];
+    dst.ref[k] = src.ref[k];
+    dst.id[k] = src.id[k];
+    dst.inst[k] = q;
+    if (ist[q].rebuild) f.oref[k] = o;
+  }
+}
+
+// The reused candidate list of every particle of the instances that rebuild
+// (all instances without a gate): the set bits of its candidate mask, in
+// order, as candidate-table entries, 8 per 32-byte group.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_skin_list_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
+                  const InstState* __restrict__ ist, CellWs cw, NbrWs nw, uint32_t* err,
+                  int gated) {
+  __shared__ uint32_t smask[BLOCK * kMaxCandWords];
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = b.inst[i];
+  if (gated && !ist[k].rebuild) return;
+  const InstDev& P = inst[k];
+  uint32_t cnt = 0;
+  if (b.off[i].w != 3.f) {  // outer-wall particles keep no list
+    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
+    const uint32_t groups = (uint32_t)nw.skin_cap >> 3;
+    uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
+      if (g < groups) {
+        uint4* dst = reinterpret_cast<uint4*>(nw.skin + nbr_slot(n, i, g << 3));
+        dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
+        dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
+      }
+      cnt += m;
+    }
+    if (cnt > (groups << 3)) {
+      latch(err, ERR_NEIGHBORS);
+      cnt = groups << 3;
+    }
+  }
+  nw.skin_count[i] = cnt;
+}
+
 // -------------------------------------------------------------------- density
 
+// r^2 of a pair vector with an explicit rounding sequence: the same bits as
+// the neighbour search's test, so that a list rebuilt every step (skin 0)
+// keeps exactly the search's neighbours.
+__device__ __forceinline__ float pair_r2f(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
 // Density deviation and Tait pressure, one thread per particle, summed over
-// the set bits of the particle's candidate mask (sph_search.cu; the search's
-// test is exact in this form, so every set bit is a neighbour), which are
-// also written, in order, as the particle's neighbour list for the pair pass.
-// The walk takes 8 neighbours at a time: their table entries, then their
-// offset records, are loaded together before the 8 pairs are summed, and the
-// 8 entries are stored as one 32-byte list group.
+// the entries of its reused list that lie within 2h now (r^2 < (2h)^2 on the
+// current offsets and the entry's cell-displacement code), which are also
+// written, in order, as the particle's neighbour list for the pair pass.
+// The list is read one 32-byte group of 8 entries at a time, and the 8
+// offset records are loaded together before the 8 pairs are tested.
 // kFilter: some instance uses the pressure filter; the kernel shape of every
 // list entry is then stored beside the list (nw.wsh_f) for the filter.
 template <int BLOCK, bool kFilter>
 __global__ void __launch_bounds__(BLOCK)
-k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, CellWs cw,
-                NbrWs nw, uint32_t* err) {
-  __shared__ uint32_t smask[BLOCK * kMaxCandWords];
+k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
+                uint32_t* err) {
+  __shared__ uint32_t stage[BLOCK * kStageStride];
   __shared__ float4 dtab[64];
   fill_disp_table(dtab);
   __syncthreads();
@@ -269,54 +435,51 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   if (sp == 3) {
     delta = 0.f;
   } else {
-    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
-    const uint32_t groups = (uint32_t)nw.cap >> 3;
+    ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
     const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
     const float mrD0 = P.mr_f[0] * P.aD_f, mrD1 = P.mr_f[1] * P.aD_f;
-    uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
-      // every batch but the last holds 8 neighbours: it is list group g
-      if (g < groups) {
-        uint4* dst = reinterpret_cast<uint4*>(nw.list + nbr_slot(n, i, g << 3));
-        dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
-        dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
-      }
-      cnt += m;
+    const float cut2 = P.cut2_f;
+    const uint32_t scnt = checked_count(nw.skin_count[i], nw.skin_cap, err);
+    const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.skin);
+    for (uint32_t t0 = 0; t0 < scnt; t0 += 8) {
+      const int64_t g = 2 * ((int64_t)(t0 >> 3) * n + i);
+      const uint4 ga = groups[g], gb = groups[g + 1];
+      const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+      const uint32_t m = scnt - t0 < 8u ? scnt - t0 : 8u;
       float4 o[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u)
         if (u < m) o[u] = b.off[checked_index(e[u] & kNbrIndexMask, n, err)];
-      float wq[8];
 #pragma unroll
       for (uint32_t u = 0; u < 8; ++u) {
-        wq[u] = 0.f;
         if (u < m) {
-          float dx, dy2, dz2;
-          entry_vec(P, dtab, e[u], oi, o[u], dx, dy2, dz2);
-          const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          // r = r2 / sqrt(r2) from the approximate reciprocal square root
-          const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-          // (m_j / rho0) W(r) = (m_j aD / rho0) t^4 (2q + 1), t = 1 - q/2
-          const float t1 = fmaf(-half_inv_h, r, 1.f);
-          const float t2 = t1 * t1;
-          const float Wt = t2 * t2 * fmaf(two_inv_h, r, 1.f);
-          wq[u] = Wt;
-          acc.add((o[u].w == 0.f ? mrD0 : mrD1) * Wt);
+          float dx, dy, dz;
+          entry_vec(P, dtab, e[u], oi, o[u], dx, dy, dz);
+          const float r2 = pair_r2f(dx, dy, dz);
+          const bool keep = r2 < cut2;
+          out.push(e[u], keep);
+          if (keep) {
+            // r = r2 / sqrt(r2) from the approximate reciprocal square root
+            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+            // (m_j / rho0) W(r) = (m_j aD / rho0) t^4 (2q + 1), t = 1 - q/2
+            const float t1 = fmaf(-half_inv_h, r, 1.f);
+            const float t2 = t1 * t1;
+            const float Wt = t2 * t2 * fmaf(two_inv_h, r, 1.f);
+            acc.add((o[u].w == 0.f ? mrD0 : mrD1) * Wt);
+            if (kFilter) {  // the shape of this list entry, in the list's layout
+              const uint32_t t = out.total() - 1u;
+              if (t < (uint32_t)nw.cap) nw.wsh_f[nbr_slot(n, i, t)] = Wt;
+            }
+          }
         }
       }
-      if (kFilter && g < groups) {  // the group's kernel shapes, beside the list group
-        float4* dw = reinterpret_cast<float4*>(nw.wsh_f + nbr_slot(n, i, g << 3));
-        dw[0] = make_float4(wq[0], wq[1], wq[2], wq[3]);
-        dw[1] = make_float4(wq[4], wq[5], wq[6], wq[7]);
-      }
+      if (out.pend >= (uint32_t)kDrainAt) out.drain();
     }
-    if (cnt > (groups << 3)) {
-      latch(err, ERR_NEIGHBORS);
-      cnt = groups << 3;
-    }
+    cnt = out.finish();
+    if (out.overflow()) latch(err, ERR_NEIGHBORS);
     delta = acc.value();
   }
   nw.count[i] = cnt;
@@ -451,7 +614,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   // absolute position of i about the rotation axis (wall torque only)
   const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
-  const double zi = P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z;
+  const double zi = fold_z(P, P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z);
   const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
   // compensated sums across groups of 8 neighbours, plain FP32 sums inside
   // a group
@@ -615,7 +778,7 @@ __global__ void k_unsort_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* 
       const float4 of = b.off[k];
       pos[3 * o] = Q.lo[0] + (double)cell_x(c) * Q.cell[0] + (double)of.x;
       pos[3 * o + 1] = Q.lo[1] + (double)cell_y(c) * Q.cell[1] + (double)of.y;
-      pos[3 * o + 2] = Q.lo[2] + (double)cell_z(c) * Q.cell[2] + (double)of.z;
+      pos[3 * o + 2] = fold_z(Q, Q.lo[2] + (double)cell_z(c) * Q.cell[2] + (double)of.z);
     }
     if (vel) {
       const float4 v = b.vel[k];
@@ -648,44 +811,83 @@ __global__ void k_unsort_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* 
 
 }  // namespace
 
-cudaError_t launch_kick_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
-                                    const InstDev* inst, const InstState* ist, const CellWs& cw,
-                                    uint32_t* err, int mode, cudaStream_t s, const LaunchCfg& lc,
-                                    int* launches) {
-  k_kick_drift_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, ist, cw,
-                                                                        err, mode);
+cudaError_t launch_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                               const InstDev* inst, InstState* ist, uint32_t* err, int mode,
+                               cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  k_drift_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, ist, err, mode);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keys_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
+                              const InstState* ist, const CellWs& cw, uint32_t* err, int mode,
+                              cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  k_keys_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, inst, ist, cw, err, mode);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relist_keys_mixed(int64_t n, const MixBuf& b, const MixFields& f,
+                                     const InstDev* inst, const CellWs& cw, cudaStream_t s,
+                                     const LaunchCfg& lc) {
+  k_relist_keys_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, f, inst, cw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate(bool open, int32_t n_inst, const InstDev* inst, InstState* ist,
+                        uint32_t* err, int mode, cudaStream_t s, int* launches) {
+  if (open)
+    k_gate_force<<<1, 128, 0, s>>>(n_inst, ist, err);
+  else
+    k_gate_close<<<1, 128, 0, s>>>(n_inst, inst, ist, err, mode);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
-                                 const CellWs& cw, cudaStream_t s, const LaunchCfg& lc,
-                                 int* launches) {
-  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, cw);
+                                 const CellWs& cw, const uint32_t* gate, cudaStream_t s,
+                                 const LaunchCfg& lc, int* launches) {
+  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, cw, gate);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copyback_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
+                                  const MixFields& f, const InstState* ist, const uint32_t* gate,
+                                  cudaStream_t s, const LaunchCfg& lc, int* launches) {
+  k_copyback_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, f, ist, gate);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skin_list_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
+                                   const InstState* ist, const CellWs& cw, const NbrWs& nw,
+                                   uint32_t* err, int gated, cudaStream_t s, int* launches) {
+  k_skin_list_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, inst, ist, cw, nw, err,
+                                                                   gated);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
-                                 const InstDev* inst, const CellWs& cw, const NbrWs& nw,
-                                 uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
-                                 int* launches) {
+                                 const InstDev* inst, const NbrWs& nw, uint32_t* err,
+                                 cudaStream_t s, const LaunchCfg& lc, int* launches) {
   const unsigned g32 = (unsigned)((n + 31) / 32), g64 = (unsigned)((n + 63) / 64),
                  g128 = (unsigned)((n + 127) / 128);
   if (lc.any_filter) {
     if (lc.block_density == 32)
-      k_density_mixed<32, true><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<32, true><<<g32, 32, 0, s>>>(n, b, f, inst, nw, err);
     else if (lc.block_density == 64)
-      k_density_mixed<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<64, true><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
     else
-      k_density_mixed<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<128, true><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   } else {
     if (lc.block_density == 32)
-      k_density_mixed<32, false><<<g32, 32, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<32, false><<<g32, 32, 0, s>>>(n, b, f, inst, nw, err);
     else if (lc.block_density == 64)
-      k_density_mixed<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<64, false><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
     else
-      k_density_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, cw, nw, err);
+      k_density_mixed<128, false><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   }
   if (launches) ++*launches;
   return cudaGetLastError();

@@ -78,7 +78,7 @@ struct MixView {
     const int cz = (int)(c >> (kCellBitsX + kCellBitsY));
     r[0] = P.lo[0] + (double)cx * P.cell[0] + (double)o.x;
     r[1] = P.lo[1] + (double)cy * P.cell[1] + (double)o.y;
-    r[2] = P.lo[2] + (double)cz * P.cell[2] + (double)o.z;
+    r[2] = fold_z(P, P.lo[2] + (double)cz * P.cell[2] + (double)o.z);
   }
   __device__ __forceinline__ void vel(int64_t i, double* v) const {
     const float4 p = b.vel[i];
@@ -489,7 +489,74 @@ cudaError_t breakdown(int32_t n_inst, int64_t n, int64_t total_chunks, const Ins
   return cudaGetLastError();
 }
 
+// Neighbour-pair census: ordered pairs (fluid row i, listed neighbour j) by
+// species class, 0 both inviscid, 1 unlike fluid, 2 both viscous, 3 inviscid
+// and wall, 4 viscous and wall; exact integer counts carried in doubles, per
+// chunk, then per instance in chunk order.
+template <class View>
+__global__ void __launch_bounds__(kRedThreads)
+k_census_chunks(int32_t n_inst, int64_t n, const InstDev* __restrict__ inst, View V, NbrWs nw,
+                double* __restrict__ partials) {
+  __shared__ double sh[5 * kRedThreads];
+  const ChunkRange r = chunk_range(inst, n_inst, blockIdx.x);
+  uint32_t c[5] = {0u, 0u, 0u, 0u, 0u};
+  for (int64_t i = r.begin + threadIdx.x; i < r.end; i += kRedThreads) {
+    const int sp_i = V.species(i);
+    if (sp_i >= 2) continue;
+    const uint32_t cnt = min(nw.count[i], (uint32_t)nw.cap);
+    for (uint32_t t = 0; t < cnt; ++t) {
+      uint32_t j = nw.list[nbr_slot(n, i, t)] & kNbrIndexMask;
+      if ((int64_t)j >= n) j = 0;
+      const int sp_j = V.species(j);
+      const int k = sp_j >= 2 ? (sp_i == 0 ? 3 : 4) : (sp_i + sp_j == 0 ? 0 : (sp_i + sp_j == 1 ? 1 : 2));
+      c[k] += 1u;
+    }
+  }
+  for (int q = 0; q < 5; ++q) sh[q * kRedThreads + threadIdx.x] = (double)c[q];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 5; ++q) sh[q * kRedThreads + threadIdx.x] += sh[q * kRedThreads + threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5)
+    partials[(int64_t)blockIdx.x * kDiagFields + threadIdx.x] = sh[threadIdx.x * kRedThreads];
+}
+
+__global__ void k_census_final(int32_t n_inst, const InstDev* __restrict__ inst,
+                               const double* __restrict__ partials, double* __restrict__ out) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_inst) return;
+  const InstDev& P = inst[k];
+  double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t ch = 0; ch < P.n_chunks; ++ch)
+    for (int q = 0; q < 5; ++q) c[q] += partials[(P.chunk_base + ch) * kDiagFields + q];
+  for (int q = 0; q < 5; ++q) out[(int64_t)k * kDiagFields + q] = c[q];
+}
+
+template <class View>
+cudaError_t census(int32_t n_inst, int64_t n, int64_t total_chunks, const InstDev* inst,
+                   const View& V, const NbrWs& nw, double* partials, double* out,
+                   cudaStream_t s) {
+  k_census_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, n, inst, V, nw,
+                                                                       partials);
+  k_census_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, partials, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_census_fp64(int32_t n_inst, int64_t n, int64_t total_chunks,
+                               const InstDev* inst, const Fp64Buf& b, const Fp64Fields& f,
+                               const NbrWs& nw, double* partials, double* out, cudaStream_t s) {
+  return census(n_inst, n, total_chunks, inst, Fp64View{b, f}, nw, partials, out, s);
+}
+
+cudaError_t launch_census_mixed(int32_t n_inst, int64_t n, int64_t total_chunks,
+                                const InstDev* inst, const MixBuf& b, const MixFields& f,
+                                const NbrWs& nw, double* partials, double* out, cudaStream_t s) {
+  return census(n_inst, n, total_chunks, inst, MixView{b, f}, nw, partials, out, s);
+}
 
 cudaError_t launch_wall_torque_fp64(int32_t n_inst, int64_t total_chunks, const InstDev* inst,
                                     InstState* ist, const Fp64Buf& b, const Fp64Fields& f,

@@ -92,8 +92,9 @@ __device__ __forceinline__ float pair_r2(float dx, float dy, float dz) {
 template <bool kMixed, int kSeg>
 __global__ void __launch_bounds__(32 * kMaxSearchWarps, 3)
 k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restrict__ inst,
-              CellWs cw, NbrWs nw, uint32_t* err) {
+              CellWs cw, NbrWs nw, uint32_t* err, const InstState* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate && gate[blockIdx.y].rebuild == 0) return;  // the instance keeps its lists
   const int lane = threadIdx.x & 31;
   WarpSmem<kSeg>& sm = reinterpret_cast<WarpSmem<kSeg>*>(smem_raw)[threadIdx.x >> 5];
   const InstDev& P = inst[blockIdx.y];
@@ -139,7 +140,7 @@ k_cell_search(int64_t n, const float4* __restrict__ rec, const InstDev* __restri
   if (lane == 0) nw.ncand[g] = total;
   uint32_t* __restrict__ table = nw.cand + g * kMaxCand;
   const uint32_t pre_self = __shfl_sync(~0u, rpre, 13);  // the cell's own run
-  const float cut2 = kMixed ? P.cut2_f : P.cut2f_margin;
+  const float cut2 = kMixed ? P.skin_cut2_f : P.cut2f_margin;
 
   bool table_done = false;
   for (uint32_t tb = i0; tb < i1; tb += 32) {
@@ -269,9 +270,10 @@ template <bool kMixed>
 __global__ void __launch_bounds__(128)
 k_cell_search_tpp(int64_t n, const float4* __restrict__ rec,
                   const uint32_t* __restrict__ inst_of, const InstDev* __restrict__ inst,
-                  CellWs cw, NbrWs nw, uint32_t* err) {
+                  CellWs cw, NbrWs nw, uint32_t* err, const InstState* __restrict__ gate) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (gate && gate[inst_of[i]].rebuild == 0) return;  // the instance keeps its lists
   const InstDev& P = inst[inst_of[i]];
   const int S = P.slabs;
   const int64_t g = (int64_t)cw.skey[i] / S;  // grid cell over all instances
@@ -289,7 +291,7 @@ k_cell_search_tpp(int64_t n, const float4* __restrict__ rec,
   }
   uint32_t* __restrict__ table = nw.cand + g * kMaxCand;
   uint32_t* __restrict__ out = nw.mask + i;
-  const float cut2 = kMixed ? P.cut2_f : P.cut2f_margin;
+  const float cut2 = kMixed ? P.skin_cut2_f : P.cut2f_margin;
   uint32_t q = 0, word = 0, hits = 0, self_q = ~0u;
   bool over = false;
   for (int r = 0; r < 27 && !over; ++r) {
@@ -379,13 +381,13 @@ cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
                                const uint32_t* inst_of, const InstDev* inst, int32_t n_inst,
                                int64_t max_cells, const CellWs& cw, const NbrWs& nw,
                                uint32_t* err, cudaStream_t s, const LaunchCfg& lc,
-                               int* launches) {
+                               int* launches, const InstState* gate) {
   if (lc.search_warps == 0) {  // thread-per-particle mapping
     const unsigned blocks = (unsigned)((n + 127) / 128);
     if (mixed_form)
-      k_cell_search_tpp<true><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err);
+      k_cell_search_tpp<true><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err, gate);
     else
-      k_cell_search_tpp<false><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err);
+      k_cell_search_tpp<false><<<blocks, 128, 0, s>>>(n, rec, inst_of, inst, cw, nw, err, gate);
     if (launches) ++*launches;
     return cudaGetLastError();
   }
@@ -396,14 +398,14 @@ cudaError_t launch_cell_search(bool mixed_form, int64_t n, const float4* rec,
   const size_t smem = search_smem(warps, seg);
   if (seg == 256) {
     if (mixed_form)
-      k_cell_search<true, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+      k_cell_search<true, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err, gate);
     else
-      k_cell_search<false, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+      k_cell_search<false, 256><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err, gate);
   } else {
     if (mixed_form)
-      k_cell_search<true, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+      k_cell_search<true, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err, gate);
     else
-      k_cell_search<false, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err);
+      k_cell_search<false, 512><<<grid, 32 * warps, smem, s>>>(n, rec, inst, cw, nw, err, gate);
   }
   if (launches) ++*launches;
   return cudaGetLastError();

@@ -107,6 +107,12 @@ class Simulation:
     def launches_per_step(self) -> int:
         return B.sph_launches_per_step(self.ctx)
 
+    def pair_census(self, inst: int = 0):
+        return B.sph_pair_census(self.ctx, inst)
+
+    def list_builds(self, inst: int = 0) -> int:
+        return B.sph_list_builds(self.ctx, inst)
+
     # -- checkpoint / resume ----------------------------------------------
     def save_checkpoint(self, path: str | None = None):
         """The complete persistent state as a host uint8 array (also written
