@@ -51,13 +51,16 @@ UNIT = "particle-steps/s"
 # the pressure term alone; unlike species (walls count as viscous) pressure,
 # interfacial and local interaction with its torque; two viscous particles
 # pressure, shear and rotational with its torque.  The FP64 form's pair pass
-# runs one specialised loop per class and these are its counts; the mixed
-# form adds the cell offsets of the pair vector (3) and its compensated
-# sums (3 per pair), and its single loop evaluates every term for every pair
-# (96 operations), the difference being implementation work.
+# runs one specialised loop per class and these are its counts.  For the
+# mixed form the same terms cost 6 more (the pair vector from the cell
+# offsets: a subtraction and a fused multiply-add per axis where the FP64
+# form subtracts) plus its compensated sums (4 operations per sum per group
+# of 8 neighbours: 1.5 per pair for the force alone, 3 with the torque); its
+# pair pass, bound by L1 throughput and gather latency, runs one loop that
+# evaluates every term for every pair (96 operations), the rest being
+# implementation work (specialised loops measured slower there).
 FORCE_FLOPS_BY_CLASS = {"fp64": {"II": 23, "IX": 76, "VV": 79},
-                        "mixed": {"II": 29, "IX": 82, "VV": 85}}
-FORCE_FLOPS_PER_PAIR = {"fp64": 87, "mixed": 96}   # every term for every pair
+                        "mixed": {"II": 30.5, "IX": 85, "VV": 88}}
 # Density pass: operations per pair of the density sum (pair vector, r^2,
 # sqrt, Wendland W, accumulation; the mixed form adds the cell offsets and
 # the Kahan update).  W_ij = W_ji, so a pair is algorithmic work once.  The

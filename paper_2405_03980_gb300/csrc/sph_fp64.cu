@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "sph_kernels.h"
+#include "sph_partition.cuh"
 
 namespace sphgb {
 namespace {
@@ -180,6 +181,22 @@ __global__ void k_reorder_fp64(int64_t n, Fp64Buf src, Fp64Buf dst, CellWs cw, N
 // 3.0 -> 0x40080000).
 __device__ __forceinline__ bool inviscid(double w) { return __double2hiint(w) == 0; }
 __device__ __forceinline__ bool is_wall(double w) { return __double2hiint(w) >= 0x40000000; }
+// Species classes and wall-row zeroing of the FP64 state, for the partition.
+struct Fp64Species {
+  Fp64Buf b;
+  Fp64Fields f;
+  __device__ __forceinline__ int cls(int64_t i) const {  // 0 inviscid, 1 viscous, 2 wall
+    const double w = b.pos[i].w;
+    return inviscid(w) ? 0 : (is_wall(w) ? 2 : 1);
+  }
+  __device__ __forceinline__ void zero(int64_t i) const {
+    const dvec4 z = {0.0, 0.0, 0.0, 0.0};
+    f.acc[i] = z;
+    f.dspin[i] = z;
+    f.tw[i] = z;
+  }
+};
+
 // z period crossed by the pair (i, j): +1 if j's image lies one period above
 // i's cell row (i in the bottom row, cell code dz + 1 = 2), -1 if below (i in
 // the top row, code 0), else 0.  The code is c_i - c_j + 1 per axis.
@@ -640,148 +657,6 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
   if (!finite3(S.fx, S.fy, S.fz) || !finite3(tx, ty, tz)) latch(err, ERR_NONFINITE);
 }
 
-// ------------------------------------------------------ species partition
-
-// Stable partition of the fluid particles by species for the pair pass,
-// deterministic (no atomics): per tile of kPartTile sorted particles, the
-// counts of inviscid and viscous fluid; their exclusive scans over the tiles
-// (inviscid first); then each tile writes its particles' indices in order.
-// Wall rows, which the pair pass does not visit, get zero accelerations and
-// wall torque here.
-constexpr int kPartThreads = 256;
-constexpr int kPartPer = kPartTile / kPartThreads;  // 16 consecutive particles per thread
-
-__device__ __forceinline__ int fluid_class(double w) {  // 0 inviscid, 1 viscous, 2 wall
-  return inviscid(w) ? 0 : (is_wall(w) ? 2 : 1);
-}
-
-// Exclusive block scan of two counts at once (kPartThreads threads).
-__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t v, uint32_t& ea, uint32_t& ev,
-                                            uint32_t& ta, uint32_t& tv) {
-  __shared__ uint32_t wa[32], wv[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t ia = a, iv = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t xa = __shfl_up_sync(~0u, ia, o), xv = __shfl_up_sync(~0u, iv, o);
-    if (lane >= o) {
-      ia += xa;
-      iv += xv;
-    }
-  }
-  if (lane == 31) {
-    wa[warp] = ia;
-    wv[warp] = iv;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = kPartThreads / 32;
-    uint32_t sa = lane < nw ? wa[lane] : 0u, sv = lane < nw ? wv[lane] : 0u;
-    uint32_t ja = sa, jv = sv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t xa = __shfl_up_sync(~0u, ja, o), xv = __shfl_up_sync(~0u, jv, o);
-      if (lane >= o) {
-        ja += xa;
-        jv += xv;
-      }
-    }
-    if (lane < nw) {
-      wa[lane] = ja - sa;
-      wv[lane] = jv - sv;
-    }
-    if (lane == nw - 1) {
-      wa[31] = ja;
-      wv[31] = jv;
-    }
-  }
-  __syncthreads();
-  ea = wa[warp] + ia - a;
-  ev = wv[warp] + iv - v;
-  ta = wa[31];
-  tv = wv[31];
-}
-
-__global__ void __launch_bounds__(kPartThreads)
-k_part_count(int64_t n, Fp64Buf b, uint32_t* __restrict__ part) {
-  const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartPer;
-  uint32_t a = 0, v = 0;
-  for (int k = 0; k < kPartPer; ++k)
-    if (base + k < n) {
-      const int c = fluid_class(b.pos[base + k].w);
-      a += c == 0;
-      v += c == 1;
-    }
-  uint32_t ea, ev, ta, tv;
-  block_scan2(a, v, ea, ev, ta, tv);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = ta;
-    part[2 * blockIdx.x + 1] = tv;
-  }
-}
-
-// One block: the tile offsets (inviscid from 0, viscous after all inviscid)
-// in place, and the totals part[2 nt] = inviscid, part[2 nt + 1] = fluid.
-__global__ void __launch_bounds__(kPartThreads)
-k_part_scan(int64_t nt, uint32_t* __restrict__ part) {
-  __shared__ uint32_t carry[2];
-  if (threadIdx.x == 0) carry[0] = carry[1] = 0u;
-  __syncthreads();
-  for (int64_t t0 = 0; t0 < nt; t0 += kPartThreads) {
-    const int64_t t = t0 + threadIdx.x;
-    const uint32_t a = t < nt ? part[2 * t] : 0u, v = t < nt ? part[2 * t + 1] : 0u;
-    uint32_t ea, ev, ta, tv;
-    block_scan2(a, v, ea, ev, ta, tv);
-    const uint32_t ca = carry[0], cv = carry[1];
-    if (t < nt) {
-      part[2 * t] = ca + ea;
-      part[2 * t + 1] = cv + ev;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      carry[0] = ca + ta;
-      carry[1] = cv + tv;
-    }
-    __syncthreads();
-  }
-  // the viscous offsets start after every inviscid particle
-  const uint32_t n_inv = carry[0];
-  for (int64_t t = threadIdx.x; t < nt; t += kPartThreads) part[2 * t + 1] += n_inv;
-  if (threadIdx.x == 0) {
-    part[2 * nt] = n_inv;
-    part[2 * nt + 1] = n_inv + carry[1];
-  }
-}
-
-__global__ void __launch_bounds__(kPartThreads)
-k_part_scatter(int64_t n, Fp64Buf b, Fp64Fields f, const uint32_t* __restrict__ part,
-               uint32_t* __restrict__ order) {
-  const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartPer;
-  int cls[kPartPer];
-  uint32_t a = 0, v = 0;
-#pragma unroll
-  for (int k = 0; k < kPartPer; ++k) {
-    cls[k] = base + k < n ? fluid_class(b.pos[base + k].w) : 3;
-    a += cls[k] == 0;
-    v += cls[k] == 1;
-  }
-  uint32_t ea, ev, ta, tv;
-  block_scan2(a, v, ea, ev, ta, tv);
-  uint32_t oa = part[2 * blockIdx.x] + ea, ov = part[2 * blockIdx.x + 1] + ev;
-  const dvec4 z = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-  for (int k = 0; k < kPartPer; ++k) {
-    const int64_t i = base + k;
-    if (cls[k] == 0) order[oa++] = (uint32_t)i;
-    else if (cls[k] == 1) order[ov++] = (uint32_t)i;
-    else if (cls[k] == 2) {
-      f.acc[i] = z;
-      f.dspin[i] = z;
-      f.tw[i] = z;
-    }
-  }
-}
-
 // ----------------------------------------------------------- load / unload
 
 __global__ void k_load_fp64(int64_t n, Fp64Buf b, const double* __restrict__ pos,
@@ -891,10 +766,8 @@ cudaError_t launch_forces_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                int* launches) {
   // the species partition of the fluid particles, then the pair pass over it
   const int64_t nt = (n + kPartTile - 1) / kPartTile;
-  k_part_count<<<(unsigned)nt, kPartThreads, 0, s>>>(n, b, nw.part);
-  k_part_scan<<<1, kPartThreads, 0, s>>>(nt, nw.part);
-  k_part_scatter<<<(unsigned)nt, kPartThreads, 0, s>>>(n, b, f, nw.part, nw.order);
-  if (launches) *launches += 3;
+  cudaError_t e = launch_partition(n, Fp64Species{b, f}, nw, s, launches);
+  if (e != cudaSuccess) return e;
   const unsigned g256 = (unsigned)((n + 255) / 256), g128 = (unsigned)((n + 127) / 128),
                  g64 = (unsigned)((n + 63) / 64);
   // the pair pass carries only the options some instance uses

@@ -545,7 +545,7 @@ sph_status enqueue_build_mixed(sph_ctx* c, cudaStream_t s, int mode, int* launch
   sph_status st = enqueue_search(c, s, launches, c->ist);
   if (st != SPH_OK) return st;
   CK(launch_skin_list_mixed(c->n, c->mbuf[0], c->inst, c->ist, c->cw, c->nw, c->err, 1, s,
-                            launches));
+                            c->lc, launches));
   CK(launch_gate(false, c->n_inst, c->inst, c->ist, c->err, mode, s, launches));
   c->skin_valid = true;
   return SPH_OK;
@@ -571,7 +571,7 @@ sph_status enqueue_relist_mixed(sph_ctx* c, cudaStream_t s) {
   sph_status st = enqueue_search(c, s, nullptr);
   if (st != SPH_OK) return st;
   CK(launch_skin_list_mixed(c->n, c->mbuf[0], c->inst, c->ist, c->cw, c->nw, c->err, 0, s,
-                            nullptr));
+                            c->lc, nullptr));
   c->skin_valid = true;
   return SPH_OK;
 }

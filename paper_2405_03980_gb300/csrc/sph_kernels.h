@@ -120,7 +120,8 @@ cudaError_t launch_copyback_mixed(int64_t n, const MixBuf& src, const MixBuf& ds
 // gated: only the instances that rebuild (InstState::rebuild); 0: all.
 cudaError_t launch_skin_list_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
                                    const InstState* ist, const CellWs& cw, const NbrWs& nw,
-                                   uint32_t* err, int gated, cudaStream_t s, int* launches);
+                                   uint32_t* err, int gated, cudaStream_t s,
+                                   const LaunchCfg& lc, int* launches);
 cudaError_t launch_density_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                  const InstDev* inst, const NbrWs& nw, uint32_t* err,
                                  cudaStream_t s, const LaunchCfg& lc, int* launches);

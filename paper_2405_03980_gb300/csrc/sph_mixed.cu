@@ -373,30 +373,32 @@ k_skin_list_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
                   const InstState* __restrict__ ist, CellWs cw, NbrWs nw, uint32_t* err,
                   int gated) {
   __shared__ uint32_t smask[BLOCK * kMaxCandWords];
-  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t k = b.inst[i];
-  if (gated && !ist[k].rebuild) return;
-  const InstDev& P = inst[k];
-  uint32_t cnt = 0;
-  if (b.off[i].w != 3.f) {  // outer-wall particles keep no list
-    MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
-    const uint32_t groups = (uint32_t)nw.skin_cap >> 3;
-    uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
-      if (g < groups) {
-        uint4* dst = reinterpret_cast<uint4*>(nw.skin + nbr_slot(n, i, g << 3));
-        dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
-        dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
+  if (gated && gate_closed(err + kErrRebuild)) return;  // no instance rebuilds
+  for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * BLOCK) {
+    const uint32_t k = b.inst[i];
+    if (gated && !ist[k].rebuild) continue;
+    const InstDev& P = inst[k];
+    uint32_t cnt = 0;
+    if (b.off[i].w != 3.f) {  // outer-wall particles keep no list
+      MaskWalk mk(nw, n, i, (int64_t)cw.skey[i] / P.slabs, smask + threadIdx.x, BLOCK);
+      const uint32_t groups = (uint32_t)nw.skin_cap >> 3;
+      uint32_t e[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      for (uint32_t m, g = 0; (m = mk.next(e)) != 0u; ++g) {
+        if (g < groups) {
+          uint4* dst = reinterpret_cast<uint4*>(nw.skin + nbr_slot(n, i, g << 3));
+          dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
+          dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
+        }
+        cnt += m;
       }
-      cnt += m;
+      if (cnt > (groups << 3)) {
+        latch(err, ERR_NEIGHBORS);
+        cnt = groups << 3;
+      }
     }
-    if (cnt > (groups << 3)) {
-      latch(err, ERR_NEIGHBORS);
-      cnt = groups << 3;
-    }
+    nw.skin_count[i] = cnt;
   }
-  nw.skin_count[i] = cnt;
 }
 
 // -------------------------------------------------------------------- density
@@ -862,9 +864,10 @@ cudaError_t launch_copyback_mixed(int64_t n, const MixBuf& src, const MixBuf& ds
 
 cudaError_t launch_skin_list_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
                                    const InstState* ist, const CellWs& cw, const NbrWs& nw,
-                                   uint32_t* err, int gated, cudaStream_t s, int* launches) {
-  k_skin_list_mixed<64><<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n, b, inst, ist, cw, nw, err,
-                                                                   gated);
+                                   uint32_t* err, int gated, cudaStream_t s,
+                                   const LaunchCfg& lc, int* launches) {
+  k_skin_list_mixed<64><<<grid_for(n, 64, lc.sm_count, 16), 64, 0, s>>>(n, b, inst, ist, cw, nw,
+                                                                          err, gated);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
