@@ -105,17 +105,17 @@ SEARCH_ALGO_BYTES_PER_PARTICLE = {"fp64": 16, "mixed": 16}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (167.1, {"sph_search.cu": "538eb05fd38ea8ef",
-                                    "sph_internal.h": "bde2088e17d1f86d"}),
+    "k_cell_search<true>": (222.2, {"sph_search.cu": "6e75b40c14b1b6f1",
+                                    "sph_internal.h": "5c4c7d4112169ef2"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (554.0, {"sph_mixed.cu": "a2f6a0d29480f7cb",
-                                "sph_internal.h": "bde2088e17d1f86d"}),
-    "k_forces_mixed": (414.6, {"sph_mixed.cu": "a2f6a0d29480f7cb",
-                               "sph_internal.h": "bde2088e17d1f86d"}),
-    "k_density_fp64": (640.1, {"sph_fp64.cu": "5710bc8e809895dd",
-                               "sph_internal.h": "bde2088e17d1f86d"}),
-    "k_forces_fp64": (511.5, {"sph_fp64.cu": "5710bc8e809895dd",
-                              "sph_internal.h": "bde2088e17d1f86d"}),
+    "k_density_mixed": (770.7, {"sph_mixed.cu": "1020c0cf39dc7f66",
+                                "sph_internal.h": "5c4c7d4112169ef2"}),
+    "k_forces_mixed": (416.7, {"sph_mixed.cu": "1020c0cf39dc7f66",
+                               "sph_internal.h": "5c4c7d4112169ef2"}),
+    "k_density_fp64": (647.6, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
+                               "sph_internal.h": "5c4c7d4112169ef2"}),
+    "k_forces_fp64": (860.7, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
+                              "sph_internal.h": "5c4c7d4112169ef2"}),
 }
 
 
