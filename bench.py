@@ -112,7 +112,7 @@ DRAM_BYTES_PER_PARTICLE = {
                                 "sph_internal.h": "5c4c7d4112169ef2"}),
     "k_forces_mixed": (416.7, {"sph_mixed.cu": "1020c0cf39dc7f66",
                                "sph_internal.h": "5c4c7d4112169ef2"}),
-    "k_density_fp64": (647.6, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
+    "k_density_fp64": (647.2, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
                                "sph_internal.h": "5c4c7d4112169ef2"}),
     "k_forces_fp64": (860.7, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
                               "sph_internal.h": "5c4c7d4112169ef2"}),
