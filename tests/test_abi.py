@@ -81,6 +81,11 @@ def test_buffer_sizes_scale_and_validate(lib):
     # mixed precision within one batch is rejected
     q = B.params_from_dict(c.params, precision=B.SPH_MIXED)
     assert B.sph_state_bytes([p, q], [c.n, c.n]) == 0
+    # empty instances, and more particles than a 26-bit list index can name
+    assert B.sph_state_bytes(p, [0]) == 0
+    assert B.sph_workspace_bytes([p, p], [c.n, 0]) == 0
+    assert B.sph_state_bytes(p, [(1 << 26) + 1]) == 0
+    assert B.sph_state_bytes([p, p], [1 << 25, (1 << 25) + 1]) == 0
 
 
 def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
