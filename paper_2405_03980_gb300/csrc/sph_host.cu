@@ -428,7 +428,7 @@ sph_status plan(int32_t n_inst, const sph_params* params, const int64_t* counts,
     d.p_begin = pb;
     d.p_end = pb + counts[k];
     d.chunk_base = kb;
-    d.n_chunks = (counts[k] + kReduceChunk - 1) / kReduceChunk;
+    d.n_chunks = (counts[k] + kStateChunk - 1) / kStateChunk;
     cb += (int64_t)d.nx * d.ny * d.nz * d.slabs;
     pb += counts[k];
     kb += d.n_chunks;

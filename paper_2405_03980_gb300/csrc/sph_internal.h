@@ -17,7 +17,8 @@ struct alignas(16) dvec2 {
 };
 
 constexpr int kScanChunk = 4096;       // elements per block of the cell-count scan
-constexpr int kReduceChunk = 32768;    // particles per partial of the FP64 reductions
+constexpr int kReduceChunk = 32768;    // particles per partial of the plain-array diagnostics
+constexpr int kStateChunk = 8192;      // particles per partial of the state's FP64 reductions
 constexpr int kDiagFields = 24;        // doubles per diagnostics partial
 constexpr int kMaxInst = 65535;
 constexpr int kSlabs = 4;              // x-slabs per cell in the sort key

@@ -3,10 +3,11 @@
 // diagnostics (total mass M = M_s + M_n of Sec. 2.1, momentum, orbital and spin
 // angular momentum, energies).  Both state forms are read in FP64.
 //
-// Each instance's particle range is cut into fixed chunks of kReduceChunk
-// particles counted from the instance's first particle; one block reduces one
-// chunk in a fixed tree order and a second kernel adds the chunk partials of an
-// instance in chunk order.  The result therefore depends only on the
+// Each instance's particle range is cut into fixed chunks of kStateChunk
+// particles counted from the instance's first particle (small enough that
+// the chunks of a 20M-particle state fill the GPU in several even waves);
+// one block reduces one chunk in a fixed tree order and a second kernel adds
+// the chunk partials of an instance in a fixed order.  The result therefore depends only on the
 // instance's own sorted particles, not on launch shapes or on the other
 // instances of a batch.
 #include <math.h>
@@ -126,8 +127,8 @@ __device__ __forceinline__ ChunkRange chunk_range(const InstDev* inst, int32_t n
   const InstDev& P = inst[k];
   ChunkRange r;
   r.inst = k;
-  r.begin = P.p_begin + (c - P.chunk_base) * (int64_t)kReduceChunk;
-  r.end = r.begin + kReduceChunk;
+  r.begin = P.p_begin + (c - P.chunk_base) * (int64_t)kStateChunk;
+  r.end = r.begin + kStateChunk;
   if (r.end > P.p_end) r.end = P.p_end;
   return r;
 }
@@ -327,21 +328,31 @@ k_diag_chunks(int32_t n_inst, const InstDev* __restrict__ inst, View V, NbrWs nw
   if (t < 3) out[kSumFields + t] = mx[t][0];
 }
 
+// One warp per instance: lane l adds chunks l, l + 32, ... in order, then a
+// fixed butterfly combines the lanes (as for the wall torque).
 __global__ void k_diag_final(int32_t n_inst, const InstDev* __restrict__ inst,
                              const double* __restrict__ partials, double* __restrict__ out) {
-  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t k = blockIdx.x;
   if (k >= n_inst) return;
+  const int lane = threadIdx.x;
   const InstDev& P = inst[k];
   double s[kSumFields];
   for (int a = 0; a < kSumFields; ++a) s[a] = 0.0;
   double rmin = INFINITY, rmax = -INFINITY, vmax = 0.0;
-  for (int64_t c = 0; c < P.n_chunks; ++c) {
+  for (int64_t c = lane; c < P.n_chunks; c += 32) {
     const double* q = partials + (P.chunk_base + c) * kDiagFields;
     for (int a = 0; a < kSumFields; ++a) s[a] += q[a];
     rmin = fmin(rmin, q[kSumFields]);
     rmax = fmax(rmax, q[kSumFields + 1]);
     vmax = fmax(vmax, q[kSumFields + 2]);
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int a = 0; a < kSumFields; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  if (lane != 0) return;
   double* o = out + (int64_t)k * kDiagFields;
   for (int a = 0; a < kSumFields; ++a) o[a] = s[a];
   o[1] = P.m_s * s[1];
@@ -368,7 +379,7 @@ cudaError_t diag(int32_t n_inst, int64_t total_chunks, const InstDev* inst, cons
                  const NbrWs& nw, double* partials, double* out, cudaStream_t s) {
   k_diag_chunks<View><<<(unsigned)total_chunks, kRedThreads, 0, s>>>(n_inst, inst, V, nw,
                                                                      partials);
-  k_diag_final<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, inst, partials, out);
+  k_diag_final<<<n_inst, 32, 0, s>>>(n_inst, inst, partials, out);
   return cudaGetLastError();
 }
 
