@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(BLOCK)
 k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ inst, CellWs cw,
                NbrWs nw, uint32_t* err) {
   __shared__ uint32_t smask[BLOCK * kMaxCandWords];
-  __shared__ uint32_t stage[BLOCK * kStageStride];
+  __shared__ uint32_t stage[BLOCK * kStageWords];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -273,7 +273,7 @@ k_density_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ i
     const int cz_i = (int)((g - P.cell_base / P.slabs) / ((int64_t)P.nx * P.ny));
     const bool per = P.periodic_z != 0;
     MaskWalk mk(nw, n, i, g, smask + threadIdx.x, BLOCK);
-    ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
+    ListWriter out(nw, n, i, stage + threadIdx.x, BLOCK);
     // fluid rows without the filter: the inviscid neighbours are listed
     // first; the others are set aside as mask bits and listed after them by a
     // second walk (the pair pass then runs one specialised loop per part)

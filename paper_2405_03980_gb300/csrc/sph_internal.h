@@ -354,27 +354,32 @@ struct MaskKeep {
 // predicated store, no branch); drain(), called whenever 32 or more entries
 // are staged, writes the complete groups of 8 as full 32-byte sectors and
 // keeps the remainder.  Entries beyond nw.cap are counted but dropped.
+// Staged word k of thread t lives at st[k * stride] with st = stage + t and
+// stride = the block size (a multiple of 32), so the threads of a warp always
+// touch distinct banks, whatever their fill.
 constexpr int kDrainAt = 32;
 constexpr int kStageWords = 40;   // >= kDrainAt - 1 + the largest batch pushed
-constexpr int kStageStride = 41;  // odd stride spreads the threads over banks
 
 struct ListWriter {
   uint32_t* list;
   int64_t n, i;
   uint32_t* st;
+  uint32_t stride;       // words between a thread's staged entries
   uint32_t groups;       // cap / 8
   uint32_t pend = 0;     // staged entries not yet written
   uint32_t written = 0;  // groups written (or dropped beyond the capacity)
-  __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_)
-      : list(nw.list), n(n_), i(i_), st(st_), groups((uint32_t)nw.cap >> 3) {}
+  __device__ __forceinline__ ListWriter(const NbrWs& nw, int64_t n_, int64_t i_, uint32_t* st_,
+                                        uint32_t stride_)
+      : list(nw.list), n(n_), i(i_), st(st_), stride(stride_), groups((uint32_t)nw.cap >> 3) {}
   __device__ __forceinline__ void push(uint32_t e, bool keep) {
-    if (keep) st[pend++] = e;
+    if (keep) st[(pend++) * stride] = e;
   }
   __device__ __forceinline__ void write_group(uint32_t from) {
     if (written < groups) {
       uint4* dst = reinterpret_cast<uint4*>(list + nbr_slot(n, i, written << 3));
-      dst[0] = make_uint4(st[from], st[from + 1], st[from + 2], st[from + 3]);
-      dst[1] = make_uint4(st[from + 4], st[from + 5], st[from + 6], st[from + 7]);
+      const uint32_t* q = st + from * stride;
+      dst[0] = make_uint4(q[0], q[stride], q[2 * stride], q[3 * stride]);
+      dst[1] = make_uint4(q[4 * stride], q[5 * stride], q[6 * stride], q[7 * stride]);
     }
     ++written;
   }
@@ -382,7 +387,7 @@ struct ListWriter {
     const uint32_t g = pend >> 3;
     for (uint32_t k = 0; k < g; ++k) write_group(k << 3);
     const uint32_t rem = pend & 7u;
-    for (uint32_t r = 0; r < rem; ++r) st[r] = st[(g << 3) + r];
+    for (uint32_t r = 0; r < rem; ++r) st[r * stride] = st[((g << 3) + r) * stride];
     pend = rem;
   }
   __device__ __forceinline__ uint32_t total() const { return (written << 3) + pend; }

@@ -106,26 +106,23 @@ __device__ __forceinline__ bool normalize(float& o, int& c, float L, int lo, int
 // Pair vector r_i - r_j = (c_i - c_j) L + (o_i - o_j) from a neighbour-list
 // entry (whose top bits carry c_i - c_j + 1 per axis) and the two offsets;
 // exactly antisymmetric, and bit-identical to the candidate test that wrote
-// the entry.
-// The displacement code is decoded through a 64-entry shared table of the
-// unit displacements (-1, 0, +1 per axis); (+-1 or 0) x L is exact, so the
-// fused multiply-add gives the same bits as the candidate test's
-// (c_i - c_j) L + (o_i - o_j).
-__device__ __forceinline__ void fill_disp_table(float4* tab) {
-  for (int c = threadIdx.x; c < 64; c += blockDim.x) {
-    const int ex = (int)(c & 3) - 1, ey = (int)((c >> 2) & 3) - 1, ez = (int)(c >> 4) - 1;
-    tab[c] = make_float4(ex > 1 ? 0.f : (float)ex, ey > 1 ? 0.f : (float)ey,
-                         ez > 1 ? 0.f : (float)ez, 0.f);
-  }
+// the entry.  The unit displacement d of an axis is decoded on the integer
+// and FP32 pipes without a table: the float with the bits of 2^23 + (d + 1)
+// is exactly 2^23 + d + 1, and subtracting 2^23 + 1 leaves d exactly.
+// d L is exact, so the fused multiply-add gives the same bits as the
+// candidate test's (c_i - c_j) L + (o_i - o_j).  (A 64-entry table of unit
+// displacements in shared memory cost more: its bank-conflicted lookups
+// shared the L1 data path with the neighbour gathers.)
+__device__ __forceinline__ float unit_disp(uint32_t code, int axis) {
+  return __int_as_float(0x4B000000 | ((code >> (2 * axis)) & 3u)) - 8388609.0f;
 }
 
-__device__ __forceinline__ void entry_vec(const InstDev& P, const float4* tab, uint32_t ent,
-                                          const float4& oi, const float4& oj, float& dx, float& dy,
-                                          float& dz) {
-  const float4 e = tab[ent >> kNbrIndexBits];
-  dx = fmaf(e.x, P.cellf[0], oi.x - oj.x);
-  dy = fmaf(e.y, P.cellf[1], oi.y - oj.y);
-  dz = fmaf(e.z, P.cellf[2], oi.z - oj.z);
+__device__ __forceinline__ void entry_vec(const InstDev& P, uint32_t ent, const float4& oi,
+                                          const float4& oj, float& dx, float& dy, float& dz) {
+  const uint32_t c = ent >> kNbrIndexBits;
+  dx = fmaf(unit_disp(c, 0), P.cellf[0], oi.x - oj.x);
+  dy = fmaf(unit_disp(c, 1), P.cellf[1], oi.y - oj.y);
+  dz = fmaf(unit_disp(c, 2), P.cellf[2], oi.z - oj.z);
 }
 
 __device__ __forceinline__ bool finite3f(float a, float b, float c) {
@@ -422,10 +419,7 @@ template <int BLOCK, bool kFilter>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                 uint32_t* err) {
-  __shared__ uint32_t stage[BLOCK * kStageStride];
-  __shared__ float4 dtab[64];
-  fill_disp_table(dtab);
-  __syncthreads();
+  __shared__ uint32_t stage[BLOCK * kStageWords];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -440,7 +434,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
-    ListWriter out(nw, n, i, stage + threadIdx.x * kStageStride);
+    ListWriter out(nw, n, i, stage + threadIdx.x, BLOCK);
     const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
     const float mrD0 = P.mr_f[0] * P.aD_f, mrD1 = P.mr_f[1] * P.aD_f;
     const float cut2 = P.cut2_f;
@@ -459,7 +453,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
       for (uint32_t u = 0; u < 8; ++u) {
         if (u < m) {
           float dx, dy, dz;
-          entry_vec(P, dtab, e[u], oi, o[u], dx, dy, dz);
+          entry_vec(P, e[u], oi, o[u], dx, dy, dz);
           const float r2 = pair_r2f(dx, dy, dz);
           const bool keep = r2 < cut2;
           out.push(e[u], keep);
@@ -562,9 +556,6 @@ template <int BLOCK, int kOpt>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                uint32_t* err) {
-  __shared__ float4 dtab[64];
-  fill_disp_table(dtab);
-  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const float4 oi = b.off[i];
@@ -659,7 +650,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
         wj_n = b.spin[jn];
       }
       float dx, dy, dz;
-      entry_vec(P, dtab, ent, oi, oj, dx, dy, dz);
+      entry_vec(P, ent, oi, oj, dx, dy, dz);
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (!(r2 > 0.f)) continue;  // coincident particles: density only
       const float inv_r = rsqrtf(r2);

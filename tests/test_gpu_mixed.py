@@ -191,7 +191,7 @@ def test_mixed_vs_fp64_angular_momentum_2_4m_1000_steps():
 
 def test_reused_lists_keep_every_neighbour():
     """The mixed form keeps its neighbour lists across steps (default skin
-    0.5 dx): over 14 steps of the 8,960 cylinder it rebuilds them only when
+    0.3 dx): over 14 steps of the 8,960 cylinder it rebuilds them only when
     the drift exhausts the skin, fewer times than it steps, and after every
     other step its neighbour sets are those of the current positions: the
     oracle's brute-force sets, except for pairs within 1e-5 of the cutoff."""
@@ -218,7 +218,7 @@ def test_reused_lists_keep_every_neighbour():
 
 
 def test_reused_lists_agree_with_every_step_rebuilds():
-    """Keeping the lists (skin 0.5 dx) or rebuilding them every step (skin
+    """Keeping the lists (default skin 0.3 dx) or rebuilding them every step (skin
     < 0) changes only the rounding of the FP32 offsets, so the two
     trajectories agree to the mixed form's accuracy after 20 steps, and both
     stay within the one-step target of the oracle after one step."""
