@@ -105,17 +105,17 @@ SEARCH_ALGO_BYTES_PER_PARTICLE = {"fp64": 16, "mixed": 16}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (222.2, {"sph_search.cu": "6e75b40c14b1b6f1",
-                                    "sph_internal.h": "5c4c7d4112169ef2"}),
+    "k_cell_search<true>": (222.3, {"sph_search.cu": "6e75b40c14b1b6f1",
+                                    "sph_internal.h": "df052485beba063c"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (770.7, {"sph_mixed.cu": "1020c0cf39dc7f66",
-                                "sph_internal.h": "5c4c7d4112169ef2"}),
-    "k_forces_mixed": (416.7, {"sph_mixed.cu": "1020c0cf39dc7f66",
-                               "sph_internal.h": "5c4c7d4112169ef2"}),
-    "k_density_fp64": (647.2, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
-                               "sph_internal.h": "5c4c7d4112169ef2"}),
-    "k_forces_fp64": (860.7, {"sph_fp64.cu": "b1924d0e5f0ca2bd",
-                              "sph_internal.h": "5c4c7d4112169ef2"}),
+    "k_density_mixed": (770.6, {"sph_mixed.cu": "8c4fd18e166c939f",
+                                "sph_internal.h": "df052485beba063c"}),
+    "k_forces_mixed": (416.8, {"sph_mixed.cu": "8c4fd18e166c939f",
+                               "sph_internal.h": "df052485beba063c"}),
+    "k_density_fp64": (646.9, {"sph_fp64.cu": "b515673d74270fd5",
+                               "sph_internal.h": "df052485beba063c"}),
+    "k_forces_fp64": (860.4, {"sph_fp64.cu": "b515673d74270fd5",
+                              "sph_internal.h": "df052485beba063c"}),
 }
 
 

@@ -189,7 +189,10 @@ sph_status derive(const sph_params& p, InstDev& d) {
   if (p.precision == SPH_MIXED &&
       (d.nx > (1 << kCellBitsX) || d.ny > (1 << kCellBitsY) || d.nz > (1 << kCellBitsZ)))
     return SPH_ERR_GRID_OVERFLOW;
-  for (int a = 0; a < 3; ++a) d.cellf[a] = (float)d.cell[a];
+  for (int a = 0; a < 3; ++a) {
+    d.cellf[a] = (float)d.cell[a];
+    d.lof[a] = (float)d.lo[a];
+  }
   d.cut2_f = (float)d.cut2;
   d.inv_h_f = (float)d.inv_h;
   d.aD_f = (float)d.aD;

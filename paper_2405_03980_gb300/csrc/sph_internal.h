@@ -63,6 +63,7 @@ struct InstDev {
   int64_t n_chunks;
   // ---- FP32 copies for the mixed form ----
   float cellf[3];                 // cell side per axis
+  float lof[3];                   // grid origin lo per axis
   float cut2_f;                   // (2h)^2 rounded to float (strict < test)
   float inv_h_f, aD_f, cF_f;
   float m_f[2];                   // particle mass: [0] inviscid, [1] viscous/wall
