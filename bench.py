@@ -73,7 +73,8 @@ DENSITY_FLOPS_PER_PAIR = {"fp64": 18, "mixed": 29}
 # position record in, rho and P (and V, P/rho^2 for the pair pass) out.  Pair
 # pass: position, velocity, spin, V and P/rho^2 in, a and alpha out.
 ALGO_BYTES_PER_PARTICLE = {"k_density_mixed": 4 + 16 + 16, "k_density_fp64": 32 + 32,
-                           "k_forces_mixed": 4 + 48 + 32, "k_forces_fp64": 96 + 64}
+                           "k_forces_mixed": 4 + 48 + 32, "k_forces_mixed_x2": 4 + 48 + 32,
+                           "k_forces_fp64": 96 + 64}
 # Optional steps of Algorithm 1 (--extras).  The pressure filter streams each
 # fluid/inner-wall row's neighbour list and the kernel shapes the density
 # pass stored beside it (4 B + 4 B mixed, 4 B + 8 B FP64 per neighbour) and
@@ -110,8 +111,9 @@ DRAM_BYTES_PER_PARTICLE = {
     "k_cell_search<false>": (None, {}),
     "k_density_mixed": (770.6, {"sph_mixed.cu": "8c4fd18e166c939f",
                                 "sph_internal.h": "df052485beba063c"}),
-    "k_forces_mixed": (416.8, {"sph_mixed.cu": "8c4fd18e166c939f",
-                               "sph_internal.h": "df052485beba063c"}),
+    "k_forces_mixed": (None, {}),
+    "k_forces_mixed_x2": (417.0, {"sph_mixed.cu": "1230104bab475655",
+                                  "sph_internal.h": "df052485beba063c"}),
     "k_density_fp64": (646.9, {"sph_fp64.cu": "b515673d74270fd5",
                                "sph_internal.h": "df052485beba063c"}),
     "k_forces_fp64": (860.4, {"sph_fp64.cu": "b515673d74270fd5",
@@ -606,7 +608,11 @@ def run_ours(args, dist):
         byc = FORCE_FLOPS_BY_CLASS[f]
         fl_forces = sum(byc[k] * cls[k] for k in cls) + (
             COLLISION_FLOPS_PER_PAIR * uq if "collision" in extras else 0)
-        stages = [("forces", f"k_forces_{f}", fl_forces / max(uq, 1), uq,
+        # the mixed form's default pair pass takes two neighbours per step in
+        # packed FP32; with the collision model it runs the one-neighbour loop
+        fkern = ("k_forces_mixed_x2" if f == "mixed" and "collision" not in extras
+                 else f"k_forces_{f}")
+        stages = [("forces", fkern, fl_forces / max(uq, 1), uq,
                    "unique pairs with a fluid particle (" +
                    ", ".join(f"{cls[k]} {k} at {byc[k]}" for k in cls) + " flop)", unit),
                   ("density", f"k_density_{f}", DENSITY_FLOPS_PER_PAIR[f], uq,

@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+#include "sph_f32x2.cuh"
 #include "sph_kernels.h"
 
 namespace sphgb {
@@ -557,9 +558,10 @@ k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
 
 // ------------------------------------------------------------------ pair pass
 
-// kOpt: kOptLiteral if some instance uses the literal F_sn (coefficient of
-// v_ij), kOptCollision if some instance uses the collision model; the
-// default form (0) has neither and drops both at compile time.
+// The pair pass with the optional terms, one neighbour per step.  kOpt:
+// kOptLiteral if some instance uses the literal F_sn (coefficient of v_ij),
+// kOptCollision if some instance uses the collision model.  (The default
+// form, with neither, runs k_forces_mixed_x2 below.)
 template <int BLOCK, int kOpt>
 __global__ void __launch_bounds__(BLOCK)
 k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
@@ -738,6 +740,215 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   if (!finite3f(ax, ay, az) || !finite3f(bx, by, bz)) latch(err, ERR_NONFINITE);
 }
 
+// The pair pass of the default form (neither the literal F_sn nor the
+// collision model) with two neighbours of particle i per step, their FP32
+// arithmetic in packed pairs (f32x2: one instruction, two independent
+// operations each rounded as its scalar form), where the thread-per-pair
+// loop above issues one instruction per operation.  Every pair scalar is
+// formed in an order independent of (i, j) as there, so f_ji == -f_ij bit
+// for bit.  A neighbour slot past the list's end, or a coincident particle
+// (r = 0: density only), is evaluated on stand-in values and masked out.
+// The packed form needs more registers (146); bounding them at 128 keeps 16
+// warps per SM, the residency of the scalar loop, at the cost of a few spilled
+// loop constants: 8.26 -> 7.59 ms at 20.1M (at 146 registers and 12 warps the
+// pass was latency-bound and took 8.35 ms).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
+k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
+                  uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const float4 oi = b.off[i];
+  const int sp_i = (int)oi.w;
+  if (sp_i >= 2) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    f.acc[i] = z;
+    f.dspin[i] = z;
+    f.tw[i] = z;
+    return;
+  }
+  const InstDev& P = inst[b.inst[i]];
+  const uint32_t ci = b.cell[i];
+  const float4 vi = b.vel[i];   // w = V_i
+  const float4 wi = b.spin[i];  // w = P_i / rho_i^2
+  const int si = sp_i == 0 ? 0 : 1;
+  const float m_i = P.m_f[si];
+  const uint32_t fl = P.flags;
+  const float kP = (fl & SPH_TERM_P) ? 1.f : 0.f;
+  const float kT = (fl & SPH_TERM_T) ? P.C_T_f : 0.f;
+  const float kA = (fl & SPH_TERM_SH) ? P.A_f : 0.f;
+  const float kB = (fl & SPH_TERM_ROT) ? P.B_f : 0.f;
+  const float kN = (fl & SPH_TERM_SN) ? P.C_l_f : 0.f;
+  const bool hproj = (fl & SPH_HPROJ) != 0;
+  const bool inv_i = sp_i == 0;
+  // species factors and kernel constants as in k_forces_mixed
+  const float mX0 = inv_i ? 0.f : 1.f, mX1 = inv_i ? 1.f : 0.f, mV1 = inv_i ? 0.f : 1.f;
+  const float cF = P.cF_f, aD = P.aD_f;
+  const float cP0 = kP * (m_i * P.m_f[0]) * cF, cP1 = kP * (m_i * P.m_f[1]) * cF;
+  const float cT0 = kT * mX0 * cF, cT1 = kT * mX1 * cF;
+  const float cBA1 = mV1 != 0.f ? (kB - kA) * cF : 0.f;
+  const float cB0 = -kB * 0.f, cB1 = -kB * mV1 * cF;
+  const float cN0 = -kN * mX0 * aD, cN1 = -kN * mX1 * aD;
+  const double xi = P.lo[0] + (double)cell_x(ci) * P.cell[0] + (double)oi.x;
+  const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
+  const double zi = fold_z(P, P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z);
+  const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
+  // packed constants
+  const f2 OX = f2_splat(oi.x), OY = f2_splat(oi.y), OZ = f2_splat(oi.z);
+  const f2 LX = f2_splat(P.cellf[0]), LY = f2_splat(P.cellf[1]), LZ = f2_splat(P.cellf[2]);
+  const f2 VX = f2_splat(vi.x), VY = f2_splat(vi.y), VZ = f2_splat(vi.z);
+  const f2 VW = f2_splat(vi.w), WW = f2_splat(wi.w);
+  const f2 HX = f2_splat(0.5f * wi.x), HY = f2_splat(0.5f * wi.y), HZ = f2_splat(0.5f * wi.z);
+  const f2 HALF = f2_splat(0.5f), ONE = f2_splat(1.f), MAGIC = f2_splat(8388609.0f);
+  const f2 NHIH = f2_splat(-0.5f * P.inv_h_f), TIH = f2_splat(2.f * P.inv_h_f);
+  Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
+  float wx = 0.f, wy = 0.f, wz = 0.f;
+  const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
+  const uint4* __restrict__ groups = reinterpret_cast<const uint4*>(nw.list);
+  // records of the next two entries, loaded one step ahead; a slot past the
+  // list's end takes the first entry's records
+  uint4 ga = make_uint4(0u, 0u, 0u, 0u), gb = ga;
+  float4 oa_n, va_n, wa_n, ob_n, vb_n, wb_n;
+  auto fetch2 = [&](uint32_t ea, uint32_t eb, bool has_b) {
+    const uint32_t ja = checked_index(ea & kNbrIndexMask, n, err);
+    const uint32_t jb = has_b ? checked_index(eb & kNbrIndexMask, n, err) : ja;
+    oa_n = b.off[ja];
+    va_n = b.vel[ja];
+    wa_n = b.spin[ja];
+    ob_n = b.off[jb];
+    vb_n = b.vel[jb];
+    wb_n = b.spin[jb];
+  };
+  if (cnt > 0) {
+    ga = groups[2 * i];
+    gb = groups[2 * i + 1];
+    fetch2(ga.x, ga.y, cnt > 1);
+  }
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    if (t0 + 8 < cnt) {
+      const int64_t gi = 2 * ((int64_t)((t0 >> 3) + 1) * n + i);
+      ga = groups[gi];
+      gb = groups[gi + 1];
+    }
+    const uint32_t m = cnt - t0 < 8u ? cnt - t0 : 8u;
+    f2 GFX = 0ull, GFY = 0ull, GFZ = 0ull, GTX = 0ull, GTY = 0ull, GTZ = 0ull;
+#pragma unroll
+    for (uint32_t u = 0; u < 8; u += 2) {
+      if (u >= m) break;
+      const bool has_b = u + 1 < m;
+      const uint32_t ea = e[u], eb = has_b ? e[u + 1] : e[u];
+      const float4 oa = oa_n, va = va_n, wa = wa_n, ob = ob_n, vb = vb_n, wb = wb_n;
+      if (t0 + u + 2 < cnt) {
+        const uint32_t na = u < 6 ? e[u + 2] : ga.x;
+        const uint32_t nb = u < 6 ? e[u + 3] : ga.y;
+        fetch2(na, nb, t0 + u + 3 < cnt);
+      }
+      // pair vectors (c_i - c_j) L + (o_i - o_j), the unit displacement of
+      // each axis decoded as in entry_vec
+      const uint32_t ca = ea >> kNbrIndexBits, cb = eb >> kNbrIndexBits;
+      const f2 EX = f2_sub(f2_make(__int_as_float(0x4B000000 | (ca & 3u)),
+                                   __int_as_float(0x4B000000 | (cb & 3u))), MAGIC);
+      const f2 EY = f2_sub(f2_make(__int_as_float(0x4B000000 | ((ca >> 2) & 3u)),
+                                   __int_as_float(0x4B000000 | ((cb >> 2) & 3u))), MAGIC);
+      const f2 EZ = f2_sub(f2_make(__int_as_float(0x4B000000 | (ca >> 4)),
+                                   __int_as_float(0x4B000000 | (cb >> 4))), MAGIC);
+      const f2 dX = f2_fma(EX, LX, f2_sub(OX, f2_make(oa.x, ob.x)));
+      const f2 dY = f2_fma(EY, LY, f2_sub(OY, f2_make(oa.y, ob.y)));
+      const f2 dZ = f2_fma(EZ, LZ, f2_sub(OZ, f2_make(oa.z, ob.z)));
+      const f2 R2 = f2_fma(dZ, dZ, f2_fma(dY, dY, f2_mul(dX, dX)));
+      float r2a, r2b;
+      f2_split(R2, r2a, r2b);
+      const bool oka = r2a > 0.f, okb = has_b && r2b > 0.f;
+      const float ira = rsqrtf(oka ? r2a : 1.f), irb = rsqrtf(okb ? r2b : 1.f);
+      const f2 IR = f2_make(ira, irb);
+      const f2 R = f2_mul(f2_make(oka ? r2a : 1.f, okb ? r2b : 1.f), IR);
+      const f2 IR2 = f2_mul(IR, IR);
+      const f2 T1 = f2_fma(NHIH, R, ONE);  // 1 - q/2
+      const f2 T2 = f2_mul(T1, T1);
+      const f2 F = f2_mul(T2, T1);
+      const f2 W = f2_mul(f2_mul(T2, T2), f2_fma(TIH, R, ONE));
+      const bool visa = oa.w != 0.f, visb = ob.w != 0.f;
+      const f2 VV = f2_mul(VW, f2_make(va.w, vb.w));
+      const f2 vX = f2_sub(VX, f2_make(va.x, vb.x));
+      const f2 vY = f2_sub(VY, f2_make(va.y, vb.y));
+      const f2 vZ = f2_sub(VZ, f2_make(va.z, vb.z));
+      const f2 SX = f2_fma(HALF, f2_make(wa.x, wb.x), HX);
+      const f2 SY = f2_fma(HALF, f2_make(wa.y, wb.y), HY);
+      const f2 SZ = f2_fma(HALF, f2_make(wa.z, wb.z), HZ);
+      // u = v_ij + r_ij x s, each component one product added to the other's
+      // negative (the sign of -(dz sy) taken from the product, exactly)
+      const f2 uX = f2_fma(dY, SZ, f2_sub(vX, f2_mul(dZ, SY)));
+      const f2 uY = f2_fma(dZ, SX, f2_sub(vY, f2_mul(dX, SZ)));
+      const f2 uZ = f2_fma(dX, SY, f2_sub(vZ, f2_mul(dY, SX)));
+      const f2 DV = f2_fma(dZ, vZ, f2_fma(dY, vY, f2_mul(dX, vX)));
+      const f2 VF = f2_mul(VV, F);
+      const f2 aP = f2_mul(f2_make(visa ? cP1 : cP0, visb ? cP1 : cP0),
+                           f2_mul(f2_add(WW, f2_make(wa.w, wb.w)), F));
+      const f2 aT = f2_mul(f2_make(visa ? cT1 : cT0, visb ? cT1 : cT0), VF);
+      const f2 aV = f2_mul(f2_mul(VF, IR2),
+                           f2_mul(f2_make(visa ? cBA1 : 0.f, visb ? cBA1 : 0.f), DV));
+      const f2 bR = f2_mul(f2_make(visa ? cB1 : cB0, visb ? cB1 : cB0), VF);
+      const f2 bN = f2_mul(f2_make(visa ? cN1 : cN0, visb ? cN1 : cN0), f2_mul(VV, W));
+      const f2 MK = f2_make(oka ? 1.f : 0.f, okb ? 1.f : 0.f);
+      const f2 base = f2_add(aP, aV);
+      const f2 AL = f2_mul(f2_add(base, aT), MK);
+      const f2 ALZ = hproj ? f2_mul(base, MK) : AL;
+      const f2 BU = f2_mul(f2_add(bR, bN), MK);
+      const f2 pX = f2_fma(AL, dX, f2_mul(BU, uX));
+      const f2 pY = f2_fma(AL, dY, f2_mul(BU, uY));
+      const f2 pZ = f2_fma(ALZ, dZ, f2_mul(BU, uZ));
+      GFX = f2_add(GFX, pX);
+      GFY = f2_add(GFY, pY);
+      GFZ = f2_add(GFZ, pZ);
+      const f2 qX = f2_mul(BU, f2_sub(f2_mul(dY, uZ), f2_mul(dZ, uY)));
+      const f2 qY = f2_mul(BU, f2_sub(f2_mul(dZ, uX), f2_mul(dX, uZ)));
+      const f2 qZ = f2_mul(BU, f2_sub(f2_mul(dX, uY), f2_mul(dY, uX)));
+      GTX = f2_add(GTX, qX);
+      GTY = f2_add(GTY, qY);
+      GTZ = f2_add(GTZ, qZ);
+      if (oa.w >= 2.f || ob.w >= 2.f) {  // wall neighbours: torque about the axis
+        float p[2][3], q[2][3];
+        f2_split(pX, p[0][0], p[1][0]);
+        f2_split(pY, p[0][1], p[1][1]);
+        f2_split(pZ, p[0][2], p[1][2]);
+        f2_split(qX, q[0][0], q[1][0]);
+        f2_split(qY, q[0][1], q[1][1]);
+        f2_split(qZ, q[0][2], q[1][2]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if ((s == 0 ? oa.w : ob.w) >= 2.f) {
+            wx += fmaf(-0.5f, q[s][0], pyi * p[s][2] - pzi * p[s][1]);
+            wy += fmaf(-0.5f, q[s][1], pzi * p[s][0] - pxi * p[s][2]);
+            wz += fmaf(-0.5f, q[s][2], pxi * p[s][1] - pyi * p[s][0]);
+          }
+        }
+      }
+    }
+    // the group's two partial sums, then the compensated sums
+    float a0, a1;
+    f2_split(GFX, a0, a1);
+    fx.add(a0 + a1);
+    f2_split(GFY, a0, a1);
+    fy.add(a0 + a1);
+    f2_split(GFZ, a0, a1);
+    fz.add(a0 + a1);
+    f2_split(GTX, a0, a1);
+    tx.add(a0 + a1);
+    f2_split(GTY, a0, a1);
+    ty.add(a0 + a1);
+    f2_split(GTZ, a0, a1);
+    tz.add(a0 + a1);
+  }
+  const float inv_m = P.inv_m_f[si], inv_I = P.inv_I_f[si];
+  const float ax = fx.value(), ay = fy.value(), az = fz.value();
+  const float bx = -0.5f * tx.value(), by = -0.5f * ty.value(), bz = -0.5f * tz.value();
+  f.acc[i] = make_float4(ax * inv_m, ay * inv_m, az * inv_m, 0.f);
+  f.dspin[i] = make_float4(bx * inv_I, by * inv_I, bz * inv_I, 0.f);
+  f.tw[i] = make_float4(wx, wy, wz, 0.f);
+  if (!finite3f(ax, ay, az) || !finite3f(bx, by, bz)) latch(err, ERR_NONFINITE);
+}
+
 // ----------------------------------------------------------- load / unload
 
 __global__ void k_load_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
@@ -902,6 +1113,16 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                  g64 = (unsigned)((n + 63) / 64);
   // the pair pass carries only the options some instance uses
   const int opt = (lc.any_literal ? kOptLiteral : 0) | (lc.any_collision ? kOptCollision : 0);
+  if (opt == 0) {  // the default form: two neighbours per step in packed FP32
+    if (lc.block_forces == 256)
+      k_forces_mixed_x2<256><<<g256, 256, 0, s>>>(n, b, f, inst, nw, err);
+    else if (lc.block_forces == 64)
+      k_forces_mixed_x2<64><<<g64, 64, 0, s>>>(n, b, f, inst, nw, err);
+    else
+      k_forces_mixed_x2<128><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  }
   auto go = [&](auto kopt) {
     constexpr int O = decltype(kopt)::value;
     if (lc.block_forces == 256)
@@ -911,9 +1132,7 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
     else
       k_forces_mixed<128, O><<<g128, 128, 0, s>>>(n, b, f, inst, nw, err);
   };
-  if (opt == 0)
-    go(std::integral_constant<int, 0>());
-  else if (opt == kOptCollision)
+  if (opt == kOptCollision)
     go(std::integral_constant<int, kOptCollision>());
   else  // the literal F_sn, with or without collisions
     go(std::integral_constant<int, kOptLiteral | kOptCollision>());

@@ -21,6 +21,7 @@
 // FP64 form: an FP32 prefilter on rounded absolute positions (the periodic
 // image in z taken per run) against a widened bound, a superset of the FP64
 // neighbours; the density pass re-tests every candidate it is given in FP64.
+#include "sph_f32x2.cuh"
 #include "sph_kernels.h"
 
 namespace sphgb {
@@ -44,38 +45,6 @@ struct WarpSmem {
   alignas(16) float tz[32];
   alignas(16) uint32_t mask[kSegChunks * kMaskRow];  // hit mask of (chunk, target)
 };
-
-// Packed FP32 pairs (Blackwell f32x2): one instruction, two independent
-// operations, each rounded as its scalar counterpart.
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 f2_splat(float a) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
-  return r;
-}
-__device__ __forceinline__ void f2_split(f2 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 __device__ __forceinline__ void latch(uint32_t* err, uint32_t bit) {
   if ((*(volatile uint32_t*)err & bit) == 0u) atomicOr(err, bit);
