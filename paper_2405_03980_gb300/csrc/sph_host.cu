@@ -339,8 +339,7 @@ void carve(void* state, void* ws, int32_t n_inst, int64_t n, int64_t n_cells,
     for (int b = 0; b < 2; ++b) {
       c.mbuf[b].cell = s.take<uint32_t>(n);
       c.mbuf[b].off = s.take<float4>(n);
-      c.mbuf[b].vel = s.take<float4>(n);
-      c.mbuf[b].spin = s.take<float4>(n);
+      c.mbuf[b].vs = s.take<float4>(2 * n);
       c.mbuf[b].ref = s.take<dvec2>(n);
       c.mbuf[b].id = s.take<uint32_t>(n);
       c.mbuf[b].inst = s.take<uint32_t>(n);
@@ -1076,7 +1075,7 @@ struct CkptHeader {
   uint64_t reserved[2];
 };
 constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;  // 2: mixed velocity and spin in one record
 
 }  // namespace
 

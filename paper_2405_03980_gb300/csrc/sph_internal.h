@@ -129,11 +129,17 @@ struct Fp64Fields {
 struct MixBuf {
   uint32_t* cell;       // cx | cy << 11 | cz << 22 (cell coordinates in the instance)
   float4* off;          // offset in [0, cell side) per axis, species
-  float4* vel;          // vx, vy, vz, V
-  float4* spin;         // wx, wy, wz, Pr
+  // velocity (vx, vy, vz, V) and spin (wx, wy, wz, P / rho^2) of particle i
+  // side by side in one 32-byte record, vs[2i] and vs[2i + 1], so that a
+  // neighbour's two records arrive in one sector (one 256-bit load)
+  float4* vs;
   dvec2* ref;           // wall reference (phase-0) x, y in FP64
   uint32_t* id;
   uint32_t* inst;
+#ifdef __CUDACC__
+  __device__ __forceinline__ float4& vel(int64_t i) const { return vs[2 * i]; }
+  __device__ __forceinline__ float4& spin(int64_t i) const { return vs[2 * i + 1]; }
+#endif
 };
 
 struct MixFields {

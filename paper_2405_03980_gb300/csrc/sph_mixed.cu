@@ -126,6 +126,34 @@ __device__ __forceinline__ void entry_vec(const InstDev& P, uint32_t ent, const 
   dz = fmaf(unit_disp(c, 2), P.cellf[2], oi.z - oj.z);
 }
 
+// The velocity and spin records of neighbour j: its 32-byte record in one
+// 256-bit load through the read-only path (the pair pass does not write the
+// state; the record is 32-byte aligned: the state buffer is 256-byte aligned
+// and the records are carved from it in multiples of 256 bytes).
+__device__ __forceinline__ void load_vs(const MixBuf& b, uint32_t j, float4& v, float4& w) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w), "=f"(w.x), "=f"(w.y), "=f"(w.z), "=f"(w.w)
+      : "l"(b.vs + 2 * (int64_t)j));
+}
+
+// The same record loaded and stored whole by the kernels that update or move
+// it (plain coherent accesses).
+__device__ __forceinline__ void ld_vs(const MixBuf& b, int64_t i, float4& v, float4& w) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w), "=f"(w.x), "=f"(w.y), "=f"(w.z),
+                 "=f"(w.w)
+               : "l"(b.vs + 2 * i)
+               : "memory");
+}
+__device__ __forceinline__ void st_vs(const MixBuf& b, int64_t i, const float4& v,
+                                      const float4& w) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :
+               : "l"(b.vs + 2 * i), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "f"(w.x), "f"(w.y),
+                 "f"(w.z), "f"(w.w)
+               : "memory");
+}
+
 __device__ __forceinline__ bool finite3f(float a, float b, float c) {
   return isfinite(a) && isfinite(b) && isfinite(c);
 }
@@ -171,8 +199,8 @@ __global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* _
     const int sp = (int)o.w;
     if (sp < 2) {
       if (mode == 1) {
-        float4 v = b.vel[i];
-        float4 w = b.spin[i];
+        float4 v, w;
+        ld_vs(b, i, v, w);
         const float4 a = f.acc[i];
         const float4 al = f.dspin[i];
         v.x += P.hdt_f * a.x;
@@ -184,8 +212,7 @@ __global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* _
         o.x += P.dt_f * v.x;
         o.y += P.dt_f * v.y;
         o.z += P.dt_f * v.z;
-        b.vel[i] = v;
-        b.spin[i] = w;
+        st_vs(b, i, v, w);
         b.off[i] = o;
         if (!finite3f(v.x, v.y, v.z) || !finite3f(w.x, w.y, w.z)) latch(err, ERR_NONFINITE);
       }
@@ -196,8 +223,10 @@ __global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* _
       o.x = (float)((x - P.lo[0]) - (double)cell_x(cc) * P.cell[0]);
       o.y = (float)((y - P.lo[1]) - (double)cell_y(cc) * P.cell[1]);
       b.off[i] = o;
-      b.vel[i] = make_float4((float)(-P.Omega * y), (float)(P.Omega * x), 0.f, b.vel[i].w);
-      b.spin[i] = make_float4(0.f, 0.f, P.Omega_f, b.spin[i].w);
+      float4 v, w;
+      ld_vs(b, i, v, w);
+      st_vs(b, i, make_float4((float)(-P.Omega * y), (float)(P.Omega * x), 0.f, v.w),
+            make_float4(0.f, 0.f, P.Omega_f, w.w));
     }
     const float4 r = f.oref[i];
     const uint32_t cc = b.cell[i];
@@ -319,16 +348,15 @@ __global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __
     const float hdt = inst[b.inst[i]].hdt_f;
     const float4 a = f.acc[i];
     const float4 al = f.dspin[i];
-    float4 v = b.vel[i];
-    float4 w = b.spin[i];
+    float4 v, w;
+    ld_vs(b, i, v, w);
     v.x += hdt * a.x;
     v.y += hdt * a.y;
     v.z += hdt * a.z;
     w.x += hdt * al.x;
     w.y += hdt * al.y;
     w.z += hdt * al.z;
-    b.vel[i] = v;
-    b.spin[i] = w;
+    st_vs(b, i, v, w);
   }
 }
 
@@ -340,8 +368,9 @@ __global__ void k_reorder_mixed(int64_t n, MixBuf src, MixBuf dst, CellWs cw,
     const uint32_t j = checked_index(cw.perm[k], n, cw.err);
     dst.cell[k] = src.cell[j];
     dst.off[k] = src.off[j];
-    dst.vel[k] = src.vel[j];
-    dst.spin[k] = src.spin[j];
+    float4 v, w;
+    ld_vs(src, j, v, w);
+    st_vs(dst, k, v, w);
     dst.ref[k] = src.ref[j];
     dst.id[k] = src.id[j];
     dst.inst[k] = src.inst[j];
@@ -361,8 +390,9 @@ __global__ void k_copyback_mixed(int64_t n, MixBuf src, MixBuf dst, MixFields f,
     const uint32_t q = src.inst[k];
     dst.cell[k] = src.cell[k];
     dst.off[k] = o;
-    dst.vel[k] = src.vel[k];
-    dst.spin[k] = src.spin[k];
+    float4 v, w;
+    ld_vs(src, k, v, w);
+    st_vs(dst, k, v, w);
     dst.ref[k] = src.ref[k];
     dst.id[k] = src.id[k];
     dst.inst[k] = q;
@@ -496,8 +526,8 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   f.delta[i] = delta;
   f.P[i] = Pres;
   const float V = P.m_f[si] / rho;
-  b.vel[i].w = V;
-  b.spin[i].w = Pres / (rho * rho);
+  b.vel(i).w = V;
+  b.spin(i).w = Pres / (rho * rho);
   if (P.flags & SPH_PFILTER) f.vp[i] = sp == 3 ? make_float2(0.f, 0.f) : make_float2(V, Pres);
   if (!isfinite(delta) || !isfinite(Pres)) latch(err, ERR_NONFINITE);
 }
@@ -552,7 +582,7 @@ k_pfilter_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
   const float Pf = num.value() / den.value();
   const float rho = P.rho0_f * (1.f + f.delta[i]);
   f.P[i] = Pf;
-  b.spin[i].w = Pf / (rho * rho);
+  b.spin(i).w = Pf / (rho * rho);
   if (!isfinite(Pf)) latch(err, ERR_NONFINITE);
 }
 
@@ -579,8 +609,8 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
   }
   const InstDev& P = inst[b.inst[i]];
   const uint32_t ci = b.cell[i];
-  const float4 vi = b.vel[i];   // w = V_i
-  const float4 wi = b.spin[i];  // w = P_i / rho_i^2
+  float4 vi, wi;  // w: V_i and P_i / rho_i^2
+  load_vs(b, i, vi, wi);
   const int si = sp_i == 0 ? 0 : 1;
   const float m_i = P.m_f[si];
   const uint32_t fl = P.flags;
@@ -637,8 +667,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
     gb = groups[2 * i + 1];
     const uint32_t j0 = checked_index(ga.x & kNbrIndexMask, n, err);
     oj_n = b.off[j0];
-    vj_n = b.vel[j0];
-    wj_n = b.spin[j0];
+    load_vs(b, j0, vj_n, wj_n);
   }
   for (uint32_t t0 = 0; t0 < cnt; t0 += 8) {
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
@@ -656,8 +685,7 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
       if (t0 + u + 1 < cnt) {
         const uint32_t jn = checked_index((u < 7 ? e[u + 1] : ga.x) & kNbrIndexMask, n, err);
         oj_n = b.off[jn];
-        vj_n = b.vel[jn];
-        wj_n = b.spin[jn];
+        load_vs(b, jn, vj_n, wj_n);
       }
       float dx, dy, dz;
       entry_vec(P, ent, oi, oj, dx, dy, dz);
@@ -769,8 +797,8 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
   }
   const InstDev& P = inst[b.inst[i]];
   const uint32_t ci = b.cell[i];
-  const float4 vi = b.vel[i];   // w = V_i
-  const float4 wi = b.spin[i];  // w = P_i / rho_i^2
+  float4 vi, wi;  // w: V_i and P_i / rho_i^2
+  load_vs(b, i, vi, wi);
   const int si = sp_i == 0 ? 0 : 1;
   const float m_i = P.m_f[si];
   const uint32_t fl = P.flags;
@@ -813,11 +841,9 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
     const uint32_t ja = checked_index(ea & kNbrIndexMask, n, err);
     const uint32_t jb = has_b ? checked_index(eb & kNbrIndexMask, n, err) : ja;
     oa_n = b.off[ja];
-    va_n = b.vel[ja];
-    wa_n = b.spin[ja];
+    load_vs(b, ja, va_n, wa_n);
     ob_n = b.off[jb];
-    vb_n = b.vel[jb];
-    wb_n = b.spin[jb];
+    load_vs(b, jb, vb_n, wb_n);
   };
   if (cnt > 0) {
     ga = groups[2 * i];
@@ -969,8 +995,8 @@ __global__ void k_load_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ in
     if (!ok) latch(err, ERR_ESCAPED);
     b.cell[i] = pack_cell(c[0], c[1], c[2]);
     b.off[i] = o;
-    b.vel[i] = make_float4((float)vel[3 * i], (float)vel[3 * i + 1], (float)vel[3 * i + 2], 0.f);
-    b.spin[i] =
+    b.vel(i) = make_float4((float)vel[3 * i], (float)vel[3 * i + 1], (float)vel[3 * i + 2], 0.f);
+    b.spin(i) =
         make_float4((float)spin[3 * i], (float)spin[3 * i + 1], (float)spin[3 * i + 2], 0.f);
     b.ref[i] = dvec2{pos[3 * i], pos[3 * i + 1]};
     b.id[i] = (uint32_t)i;
@@ -993,13 +1019,13 @@ __global__ void k_unsort_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* 
       pos[3 * o + 2] = fold_z(Q, Q.lo[2] + (double)cell_z(c) * Q.cell[2] + (double)of.z);
     }
     if (vel) {
-      const float4 v = b.vel[k];
+      const float4 v = b.vel(k);
       vel[3 * o] = v.x;
       vel[3 * o + 1] = v.y;
       vel[3 * o + 2] = v.z;
     }
     if (spin) {
-      const float4 w = b.spin[k];
+      const float4 w = b.spin(k);
       spin[3 * o] = w.x;
       spin[3 * o + 1] = w.y;
       spin[3 * o + 2] = w.z;

@@ -82,13 +82,13 @@ struct MixView {
     r[2] = fold_z(P, P.lo[2] + (double)cz * P.cell[2] + (double)o.z);
   }
   __device__ __forceinline__ void vel(int64_t i, double* v) const {
-    const float4 p = b.vel[i];
+    const float4 p = b.vel(i);
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
   }
   __device__ __forceinline__ void spin(int64_t i, double* v) const {
-    const float4 p = b.spin[i];
+    const float4 p = b.spin(i);
     v[0] = p.x;
     v[1] = p.y;
     v[2] = p.z;
