@@ -106,18 +106,18 @@ SEARCH_ALGO_BYTES_PER_PARTICLE = {"fp64": 16, "mixed": 16}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (222.3, {"sph_search.cu": "6e75b40c14b1b6f1",
-                                    "sph_internal.h": "df052485beba063c"}),
+    "k_cell_search<true>": (222.3, {"sph_search.cu": "cf8572358b743c10",
+                                    "sph_internal.h": "f593d2c24216f1dc"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (770.6, {"sph_mixed.cu": "8c4fd18e166c939f",
-                                "sph_internal.h": "df052485beba063c"}),
+    "k_density_mixed": (770.2, {"sph_mixed.cu": "5b57170e10055fd1",
+                                "sph_internal.h": "f593d2c24216f1dc"}),
     "k_forces_mixed": (None, {}),
-    "k_forces_mixed_x2": (417.0, {"sph_mixed.cu": "1230104bab475655",
-                                  "sph_internal.h": "df052485beba063c"}),
-    "k_density_fp64": (646.9, {"sph_fp64.cu": "b515673d74270fd5",
-                               "sph_internal.h": "df052485beba063c"}),
-    "k_forces_fp64": (860.4, {"sph_fp64.cu": "b515673d74270fd5",
-                              "sph_internal.h": "df052485beba063c"}),
+    "k_forces_mixed_x2": (416.9, {"sph_mixed.cu": "5b57170e10055fd1",
+                                  "sph_internal.h": "f593d2c24216f1dc"}),
+    "k_density_fp64": (647.3, {"sph_fp64.cu": "b515673d74270fd5",
+                               "sph_internal.h": "f593d2c24216f1dc"}),
+    "k_forces_fp64": (860.6, {"sph_fp64.cu": "b515673d74270fd5",
+                              "sph_internal.h": "f593d2c24216f1dc"}),
 }
 
 
