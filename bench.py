@@ -749,7 +749,10 @@ def run_ours(args, dist):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": r["clocks"],
-            "gpu_launches": r["launches_per_step"] * args.steps,
+            # (mixed form: sph_step(k) runs k step graphs, each one launch short
+            # of sph_step(1)'s count, then one closing half kick)
+            "gpu_launches": ((r["launches_per_step"] - 1) * args.steps + 1 if best == "mixed"
+                             else r["launches_per_step"] * args.steps),
             "dominant_stage": dom,
         }
         print(json.dumps(line), flush=True)

@@ -316,7 +316,10 @@ SPH_API const char* sph_stage_name(int32_t stage);
 
 /* Number of kernel launches one sph_step(ctx, 1) enqueues (the mixed form's
  * list-build kernels are enqueued every step and return at once in the
- * steps that reuse the lists). */
+ * steps that reuse the lists).  Mixed form: sph_step(ctx, k) enqueues
+ * (L - 1) k + 1 of them, L this number: each step after the first applies the
+ * previous step's closing half kick inside its drift, and the call ends with
+ * the last step's (the same arithmetic as separate kicks, bit for bit). */
 SPH_API int32_t sph_launches_per_step(const sph_ctx* ctx);
 
 /* Neighbour-list builds of instance inst so far (synchronises): in the mixed

@@ -661,7 +661,8 @@ k_forces_fp64(int64_t n, Fp64Buf b, Fp64Fields f, const InstDev* __restrict__ in
 
 __global__ void k_load_fp64(int64_t n, Fp64Buf b, const double* __restrict__ pos,
                             const double* __restrict__ vel, const double* __restrict__ spin,
-                            const uint8_t* __restrict__ sp, const uint32_t* __restrict__ inst_of) {
+                            const uint8_t* __restrict__ sp, const InstDev* __restrict__ inst,
+                            int32_t n_inst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double s = (double)sp[i];
@@ -670,7 +671,7 @@ __global__ void k_load_fp64(int64_t n, Fp64Buf b, const double* __restrict__ pos
     b.spin[i] = dvec4{spin[3 * i], spin[3 * i + 1], spin[3 * i + 2], 0.0};
     b.ref[i] = dvec2{pos[3 * i], pos[3 * i + 1]};
     b.id[i] = (uint32_t)i;
-    b.inst[i] = inst_of[i];
+    b.inst[i] = instance_of(inst, n_inst, i);
   }
 }
 
@@ -818,9 +819,10 @@ cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
 
 cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
                              const double* vel, const double* spin, const uint8_t* sp,
-                             const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc) {
-  k_load_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, pos, vel, spin, sp,
-                                                                 inst_of);
+                             const InstDev* inst, int32_t n_inst, cudaStream_t s,
+                             const LaunchCfg& lc) {
+  k_load_fp64<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, pos, vel, spin, sp, inst,
+                                                                 n_inst);
   return cudaGetLastError();
 }
 

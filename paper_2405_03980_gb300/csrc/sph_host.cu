@@ -620,8 +620,10 @@ sph_status enqueue_density(sph_ctx* c, cudaStream_t s, int* launches, Marks* m =
   return SPH_OK;
 }
 
+// advance: a step's pair pass (then the closing half kick, unless kick is
+// false, and the wall phase advanced); 0: an evaluation at the current state.
 sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches,
-                          Marks* m = nullptr) {
+                          Marks* m = nullptr, bool kick = true) {
   const int k = c->cur;
   mark(m, s);
   if (mixed(c))
@@ -631,7 +633,7 @@ sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches
     CK(launch_forces_fp64(c->n, c->buf[k], c->f, c->inst, c->cw, c->nw, c->err, s, c->lc,
                           launches));
   mark(m, s);
-  if (advance) {
+  if (advance && kick) {
     if (mixed(c))
       CK(launch_kick_mixed(c->n, c->mbuf[k], c->mf, c->inst, s, c->lc, launches));
     else
@@ -650,13 +652,17 @@ sph_status enqueue_forces(sph_ctx* c, cudaStream_t s, int advance, int* launches
 
 // One kick-drift-kick step.  FP64 form: flips c->cur (the reorder target
 // becomes current).  Mixed form: the drift, the gated list build, then the
-// passes over the reused lists; c->cur stays 0.
-sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr) {
+// passes over the reused lists; c->cur stays 0.  The mixed step leaves its
+// closing half kick out: the next step's drift applies it first (fused_kick)
+// or enqueue_closing_kick does, so a run of steps passes over the velocities
+// once per step with the same bits as separate kicks.
+sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nullptr,
+                        bool fused_kick = false) {
   sph_status st;
   if (mixed(c)) {
     mark(m, s);
-    CK(launch_drift_mixed(c->n, c->mbuf[0], c->mf, c->inst, c->ist, c->err, 1, s, c->lc,
-                          launches));
+    CK(launch_drift_mixed(c->n, c->mbuf[0], c->mf, c->inst, c->ist, c->err, fused_kick ? 2 : 1, s,
+                          c->lc, launches));
     st = enqueue_build_mixed(c, s, 1, launches, m);
   } else {
     st = enqueue_cells(c, s, 1, launches, m);
@@ -665,18 +671,27 @@ sph_status enqueue_step(sph_ctx* c, cudaStream_t s, int* launches, Marks* m = nu
   if (st != SPH_OK) return st;
   st = enqueue_density(c, s, launches, m);
   if (st != SPH_OK) return st;
-  return enqueue_forces(c, s, 1, launches, m);
+  return enqueue_forces(c, s, 1, launches, m, !mixed(c));
 }
 
+// The closing half kick of the last step of a run (mixed form).
+sph_status enqueue_closing_kick(sph_ctx* c, cudaStream_t s, int* launches) {
+  CK(launch_kick_mixed(c->n, c->mbuf[0], c->mf, c->inst, s, c->lc, launches));
+  return SPH_OK;
+}
+
+// FP64 form: one graph per starting buffer.  Mixed form: graph[0] the first
+// step of a run, graph[1] a later one (its drift applies the previous step's
+// closing half kick); sph_step adds the last step's closing kick.
 sph_status capture_graphs(sph_ctx* c) {
   const int saved = c->cur;
-  for (int g = 0; g < (mixed(c) ? 1 : 2); ++g) {
-    c->cur = (saved + g) & 1;
-    const int start_cur = c->cur;
+  for (int g = 0; g < 2; ++g) {
+    c->cur = mixed(c) ? 0 : (saved + g) & 1;
+    const int start_cur = mixed(c) ? g : c->cur;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
-    sph_status st = enqueue_step(c, c->cap_stream, &launches);
+    sph_status st = enqueue_step(c, c->cap_stream, &launches, nullptr, mixed(c) && g == 1);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     if (st != SPH_OK || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -691,7 +706,8 @@ sph_status capture_graphs(sph_ctx* c) {
       return SPH_ERR_CUDA;
     }
     c->graph[start_cur] = exec;
-    c->launches_per_step = launches;
+    // launches of sph_step(ctx, 1) (mixed form: with its closing kick)
+    c->launches_per_step = launches + (mixed(c) ? 1 : 0);
   }
   c->cur = saved;
   return SPH_OK;
@@ -866,15 +882,11 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
     off += bytes;
     return SPH_OK;
   };
-  const void *dpos, *dvel, *dspin, *dsp, *dinst;
-  std::vector<uint32_t> inst_of((size_t)n);
-  for (int32_t k = 0; k < n_inst; ++k)
-    for (int64_t i = pl.inst[k].p_begin; i < pl.inst[k].p_end; ++i) inst_of[(size_t)i] = k;
+  const void *dpos, *dvel, *dspin, *dsp;
   if ((st = stage(pos, sizeof(double) * 3 * n, &dpos)) != SPH_OK) return fail(st);
   if ((st = stage(vel, sizeof(double) * 3 * n, &dvel)) != SPH_OK) return fail(st);
   if ((st = stage(spin, sizeof(double) * 3 * n, &dspin)) != SPH_OK) return fail(st);
   if ((st = stage(species, (size_t)n, &dsp)) != SPH_OK) return fail(st);
-  if ((st = stage(inst_of.data(), sizeof(uint32_t) * n, &dinst)) != SPH_OK) return fail(st);
   if (cudaMemcpyAsync(c->inst, pl.inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice,
                       s) != cudaSuccess)
     return fail(SPH_ERR_CUDA);
@@ -883,13 +895,12 @@ sph_status sph_init_batch(sph_ctx** out, int32_t n_inst, const sph_params* param
     return fail(SPH_ERR_CUDA);
   cudaError_t le;
   if (mixed(c))
-    le = launch_load_mixed(n, c->mbuf[0], c->inst, (const double*)dpos, (const double*)dvel,
-                           (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst,
-                           c->err, s, c->lc);
+    le = launch_load_mixed(n, c->mbuf[0], c->inst, n_inst, (const double*)dpos,
+                           (const double*)dvel, (const double*)dspin, (const uint8_t*)dsp, c->err,
+                           s, c->lc);
   else
     le = launch_load_fp64(n, c->buf[0], (const double*)dpos, (const double*)dvel,
-                          (const double*)dspin, (const uint8_t*)dsp, (const uint32_t*)dinst, s,
-                          c->lc);
+                          (const double*)dspin, (const uint8_t*)dsp, c->inst, n_inst, s, c->lc);
   if (le != cudaSuccess) return fail(SPH_ERR_CUDA);
   c->cur = 0;
   // initial evaluation: walls at phase 0, cells, density, forces (a_0, alpha_0)
@@ -973,9 +984,13 @@ sph_status sph_step(sph_ctx* c, int32_t nsteps) {
     sph_status st = capture_graphs(c);
     if (st != SPH_OK) return st;
   }
+  if (mixed(c)) {  // one state buffer; the closing half kick fused into the next step
+    for (int32_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(c->graph[t ? 1 : 0], c->stream));
+    return enqueue_closing_kick(c, c->stream, nullptr);
+  }
   for (int32_t t = 0; t < nsteps; ++t) {
     CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-    if (!mixed(c)) c->cur = 1 - c->cur;  // the mixed form keeps one state buffer
+    c->cur = 1 - c->cur;
   }
   return SPH_OK;
 }
@@ -1216,8 +1231,11 @@ sph_status sph_profile_steps(sph_ctx* c, int32_t nsteps, double* stage_ms, int32
   for (int32_t t = 0; t < nsteps && st == SPH_OK; ++t) {
     Marks m;
     m.ev = ev.data() + (size_t)t * (kStages + 1);
-    st = enqueue_step(c, c->stream, nullptr, &m);
+    st = enqueue_step(c, c->stream, nullptr, &m, t > 0);
   }
+  // (mixed form: the kicks between the steps ran inside the drifts, in the
+  // first stage; the last step's closing kick follows, unmeasured)
+  if (st == SPH_OK && mixed(c)) st = enqueue_closing_kick(c, c->stream, nullptr);
   if (st == SPH_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = SPH_ERR_CUDA;
   for (int k = 0; k < n_stages; ++k) stage_ms[k] = 0.0;
   for (int32_t t = 0; t < nsteps && st == SPH_OK; ++t)

@@ -235,6 +235,20 @@ struct NbrWs {
 constexpr int kErrRebuild = 1;
 
 #ifdef __CUDACC__
+// The instance that particle i (in input order) belongs to: instances hold
+// consecutive ranges [p_begin, p_end) in order, so a binary search over their
+// first particles finds it.
+__device__ __forceinline__ uint32_t instance_of(const InstDev* __restrict__ inst, int32_t n_inst,
+                                                int64_t i) {
+  int32_t lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (inst[mid].p_begin <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return (uint32_t)lo;
+}
+
 // z of an absolute position folded into the period [lo, lo + Hz) when z is
 // periodic (mixed form: between list builds an offset may carry a particle
 // past the period's end; it is folded when positions are formed).

@@ -81,10 +81,12 @@ cudaError_t launch_unsort_fp64(int64_t n, const Fp64Buf& b, const Fp64Fields& f,
                                double* pos, double* vel, double* spin, double* rho,
                                double* P, double* acc, double* dspin, cudaStream_t s,
                                const LaunchCfg& lc);
-// Scatter AoS input (input order) into the sorted-buffer layout (identity order).
+// Scatter AoS input (input order) into the sorted-buffer layout (identity order);
+// each particle's instance is found from the instances' particle ranges.
 cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
                              const double* vel, const double* spin, const uint8_t* sp,
-                             const uint32_t* inst_of, cudaStream_t s, const LaunchCfg& lc);
+                             const InstDev* inst, int32_t n_inst, cudaStream_t s,
+                             const LaunchCfg& lc);
 
 // ---- mixed-precision path (sph_mixed.cu) -------------------------------------
 // The mixed form keeps its neighbour lists across steps (a skin, InstDev::skin)
@@ -95,7 +97,8 @@ cudaError_t launch_load_fp64(int64_t n, const Fp64Buf& b, const double* pos,
 // compaction, then density over the reused lists, pressure filter, pair pass,
 // kick, wall torque, and the gate closed.
 // mode 0: walls placed at the current phase, no kick/drift; mode 1: half kick
-// + drift + walls at the next phase.
+// + drift + walls at the next phase; mode 2: as 1, after the previous step's
+// closing half kick (which the step graphs leave to the next step's drift).
 cudaError_t launch_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                const InstDev* inst, InstState* ist, uint32_t* err, int mode,
                                cudaStream_t s, const LaunchCfg& lc, int* launches);
@@ -134,9 +137,9 @@ cudaError_t launch_forces_mixed(int64_t n, const MixBuf& b, const MixFields& f,
 cudaError_t launch_kick_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                               const InstDev* inst, cudaStream_t s, const LaunchCfg& lc,
                               int* launches);
-cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, const double* pos,
-                              const double* vel, const double* spin, const uint8_t* sp,
-                              const uint32_t* inst_of, uint32_t* err, cudaStream_t s,
+cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, int32_t n_inst,
+                              const double* pos, const double* vel, const double* spin,
+                              const uint8_t* sp, uint32_t* err, cudaStream_t s,
                               const LaunchCfg& lc);
 cudaError_t launch_unsort_mixed(int64_t n, const MixBuf& b, const MixFields& f,
                                 const InstDev* inst, double* pos, double* vel, double* spin,

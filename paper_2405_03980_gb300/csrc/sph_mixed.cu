@@ -160,6 +160,19 @@ __device__ __forceinline__ bool finite3f(float a, float b, float c) {
 
 // ---------------------------------------------------------------- integrator
 
+// v += dt/2 a, w += dt/2 alpha with explicit rounding: the closing half kick
+// of a step, whether run alone (k_kick_mixed) or fused into the next step's
+// drift, gives the same bits.
+__device__ __forceinline__ void half_kick(float hdt, const float4& a, const float4& al, float4& v,
+                                          float4& w) {
+  v.x = __fmaf_rn(hdt, a.x, v.x);
+  v.y = __fmaf_rn(hdt, a.y, v.y);
+  v.z = __fmaf_rn(hdt, a.z, v.z);
+  w.x = __fmaf_rn(hdt, al.x, w.x);
+  w.y = __fmaf_rn(hdt, al.y, w.y);
+  w.z = __fmaf_rn(hdt, al.z, w.z);
+}
+
 // A gate word: kernels of the list build run only while it is non-zero
 // (null: always).
 __device__ __forceinline__ bool gate_closed(const uint32_t* gate) {
@@ -178,8 +191,10 @@ __device__ __forceinline__ void wall_xy(const InstDev& P, const InstState& S, co
   y = __dadd_rn(__dmul_rn(s, r0.x), __dmul_rn(cs, r0.y));
 }
 
-// Half kick and drift (mode 1), or the walls' placement alone (mode 0), with
-// every particle's cell held fixed: between list builds the offsets may leave
+// Half kick and drift (mode 1; mode 2: the previous step's closing half
+// kick, then this step's opening one, then the drift, so that a run of steps
+// passes over the velocities once per step), or the walls' placement alone
+// (mode 0), with every particle's cell held fixed: between list builds the offsets may leave
 // [0, L), which keeps the cell-displacement codes of the lists valid.  A
 // particle that departed more than half the skin from its build position
 // carried along by the vessel's rigid rotation since the build (rotation
@@ -198,27 +213,23 @@ __global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* _
     float4 o = b.off[i];
     const int sp = (int)o.w;
     if (sp < 2) {
-      if (mode == 1) {
+      if (mode >= 1) {
         float4 v, w;
         ld_vs(b, i, v, w);
         const float4 a = f.acc[i];
         const float4 al = f.dspin[i];
-        v.x += P.hdt_f * a.x;
-        v.y += P.hdt_f * a.y;
-        v.z += P.hdt_f * a.z;
-        w.x += P.hdt_f * al.x;
-        w.y += P.hdt_f * al.y;
-        w.z += P.hdt_f * al.z;
-        o.x += P.dt_f * v.x;
-        o.y += P.dt_f * v.y;
-        o.z += P.dt_f * v.z;
+        const int kicks = mode == 2 ? 2 : 1;  // the previous step's closing half kick first
+        for (int q = 0; q < kicks; ++q) half_kick(P.hdt_f, a, al, v, w);
+        o.x = __fmaf_rn(P.dt_f, v.x, o.x);
+        o.y = __fmaf_rn(P.dt_f, v.y, o.y);
+        o.z = __fmaf_rn(P.dt_f, v.z, o.z);
         st_vs(b, i, v, w);
         b.off[i] = o;
         if (!finite3f(v.x, v.y, v.z) || !finite3f(w.x, w.y, w.z)) latch(err, ERR_NONFINITE);
       }
     } else {
       double x, y;
-      wall_xy(P, ist[k], b.ref[i], mode, x, y);
+      wall_xy(P, ist[k], b.ref[i], mode >= 1 ? 1 : 0, x, y);
       const uint32_t cc = b.cell[i];
       o.x = (float)((x - P.lo[0]) - (double)cell_x(cc) * P.cell[0]);
       o.y = (float)((y - P.lo[1]) - (double)cell_y(cc) * P.cell[1]);
@@ -236,7 +247,7 @@ __global__ void k_drift_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* _
     const float cy = fmaf((float)cell_y(cc), P.cellf[1], P.lof[1]);
     if (k != kr) {
       double th = ist[k].theta;
-      if (mode == 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
+      if (mode >= 1) th = __dadd_rn(th, __dmul_rn(P.Omega, P.dt));
       sincosf((float)(th - ist[k].theta_ref), &sn, &cs);
       kr = k;
     }
@@ -350,12 +361,7 @@ __global__ void k_kick_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __
     const float4 al = f.dspin[i];
     float4 v, w;
     ld_vs(b, i, v, w);
-    v.x += hdt * a.x;
-    v.y += hdt * a.y;
-    v.z += hdt * a.z;
-    w.x += hdt * al.x;
-    w.y += hdt * al.y;
-    w.z += hdt * al.z;
+    half_kick(hdt, a, al, v, w);
     st_vs(b, i, v, w);
   }
 }
@@ -978,12 +984,12 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
 // ----------------------------------------------------------- load / unload
 
 __global__ void k_load_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
-                             const double* __restrict__ pos, const double* __restrict__ vel,
-                             const double* __restrict__ spin, const uint8_t* __restrict__ sp,
-                             const uint32_t* __restrict__ inst_of, uint32_t* err) {
+                             int32_t n_inst, const double* __restrict__ pos,
+                             const double* __restrict__ vel, const double* __restrict__ spin,
+                             const uint8_t* __restrict__ sp, uint32_t* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = inst_of[i];
+    const uint32_t k = instance_of(inst, n_inst, i);
     const InstDev& P = inst[k];
     int c[3];
     float4 o;
@@ -1182,12 +1188,12 @@ cudaError_t launch_kick_mixed(int64_t n, const MixBuf& b, const MixFields& f,
   return cudaGetLastError();
 }
 
-cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, const double* pos,
-                              const double* vel, const double* spin, const uint8_t* sp,
-                              const uint32_t* inst_of, uint32_t* err, cudaStream_t s,
+cudaError_t launch_load_mixed(int64_t n, const MixBuf& b, const InstDev* inst, int32_t n_inst,
+                              const double* pos, const double* vel, const double* spin,
+                              const uint8_t* sp, uint32_t* err, cudaStream_t s,
                               const LaunchCfg& lc) {
-  k_load_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, inst, pos, vel, spin, sp,
-                                                                  inst_of, err);
+  k_load_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, inst, n_inst, pos, vel,
+                                                                  spin, sp, err);
   return cudaGetLastError();
 }
 

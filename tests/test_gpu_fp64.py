@@ -239,18 +239,26 @@ def test_batch_equals_solo_runs_bitwise():
     batch.close()
 
 
-def test_rerun_is_deterministic():
+@pytest.mark.parametrize("precision", [B.SPH_FP64, B.SPH_MIXED])
+def test_rerun_is_deterministic(precision):
+    """Reruns and split step calls give the same bits.  (The mixed form's step
+    graphs leave each step's closing half kick to the next step's drift and
+    the call's end: one call of 6 steps, two of 3 and six of 1 must agree.)"""
     c = synth.workload("cyl_8960", seed=7)
-    a = sim_of(c)
+    a = sim_of(c, precision=precision)
     a.step(6)
-    b = sim_of(c)
+    b = sim_of(c, precision=precision)
     b.step(3)
     b.step(3)
-    sa, sb = a.state_arrays(), b.state_arrays()
+    d = sim_of(c, precision=precision)
+    for _ in range(6):
+        d.step(1)
+    sa, sb, sd = a.state_arrays(), b.state_arrays(), d.state_arrays()
     for f in sa:
         assert np.array_equal(sa[f], sb[f]), f
-    a.close()
-    b.close()
+        assert np.array_equal(sa[f], sd[f]), f
+    for s in (a, b, d):
+        s.close()
 
 
 def test_device_errors_are_latched_not_trapped():
