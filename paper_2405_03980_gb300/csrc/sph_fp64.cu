@@ -530,15 +530,20 @@ __device__ __forceinline__ void pair_loop(const PairCtx& C, const InstDev& P, co
         bR = vis_j ? C.cB1 * VF : 0.0;
         bN = (vis_j ? C.cN1 : C.cN0) * vj.w * W;
       }
-      double base = aP + aV;  // the z component drops aT under the projection
+      // (a class loop adds only the terms its class carries: no FP64 addition
+      // of a zero term, as the FP64 pipe bounds this loop)
+      double base = kPath == kPathIX ? aP : aP + aV;  // the z component drops aT
       // collision of an approaching pair closer than col_dist: the central
       // force m_i dv_i / dt = -(1 + e) mu_ij (r_ij . v_ij) / (r^2 dt) r_ij;
       // both tests on the bits (dv < 0: its sign bit; -0 adds nothing)
       if ((kOpt & kOptCollision) && r2b < C.col2b && __double2hiint(dv) < 0)
         base += P.cC[C.si + (vis_j ? 1 : 0)] * dv * (inv_r * inv_r);
-      const double al = base + aT;
+      const double al = kPath == kPathVV ? base : base + aT;
       const double alz = C.hproj ? base : al;
-      const double bu = C.literal ? bR : bR + bN;  // coefficient of u_ij
+      // coefficient of u_ij
+      const double bu = kPath == kPathIX ? (C.literal ? 0.0 : bN)
+                      : kPath == kPathVV ? bR
+                                         : (C.literal ? bR : bR + bN);
       // The pair force al r_ij + bu u_ij (+ bN v_ij) goes into the sums one
       // fused multiply-add per term, and so does the spin torque
       // -1/2 r_ij x (f_rot + f_sn) = -1/2 bu (r_ij x u_ij), whose factor
