@@ -106,18 +106,18 @@ SEARCH_ALGO_BYTES_PER_PARTICLE = {"fp64": 16, "mixed": 16}
 # only while the kernel's sources hash to the values recorded with it; after
 # any change the roofline reports traffic null until it is re-measured.
 DRAM_BYTES_PER_PARTICLE = {
-    "k_cell_search<true>": (222.3, {"sph_search.cu": "cf8572358b743c10",
-                                    "sph_internal.h": "f593d2c24216f1dc"}),
+    "k_cell_search<true>": (222.4, {"sph_search.cu": "cf8572358b743c10",
+                                    "sph_internal.h": "1756e1381f18b6ad"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (770.2, {"sph_mixed.cu": "5b57170e10055fd1",
-                                "sph_internal.h": "f593d2c24216f1dc"}),
+    "k_density_mixed": (770.1, {"sph_mixed.cu": "04d2bfef2dd83b9c",
+                                "sph_internal.h": "1756e1381f18b6ad"}),
     "k_forces_mixed": (None, {}),
-    "k_forces_mixed_x2": (416.9, {"sph_mixed.cu": "5b57170e10055fd1",
-                                  "sph_internal.h": "f593d2c24216f1dc"}),
-    "k_density_fp64": (647.3, {"sph_fp64.cu": "b515673d74270fd5",
-                               "sph_internal.h": "f593d2c24216f1dc"}),
-    "k_forces_fp64": (860.6, {"sph_fp64.cu": "b515673d74270fd5",
-                              "sph_internal.h": "f593d2c24216f1dc"}),
+    "k_forces_mixed_x2": (416.8, {"sph_mixed.cu": "04d2bfef2dd83b9c",
+                                  "sph_internal.h": "1756e1381f18b6ad"}),
+    "k_density_fp64": (646.8, {"sph_fp64.cu": "2b1a99c0f5cfa53b",
+                               "sph_internal.h": "1756e1381f18b6ad"}),
+    "k_forces_fp64": (860.5, {"sph_fp64.cu": "2b1a99c0f5cfa53b",
+                              "sph_internal.h": "1756e1381f18b6ad"}),
 }
 
 
