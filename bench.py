@@ -182,18 +182,40 @@ def ratio(traffic, algorithmic):
     return None if traffic is None or not algorithmic else traffic / algorithmic
 
 
-def measured_traffic(kernel, n_particles):
-    """Per-launch DRAM bytes of kernel at n_particles, or None when no capture
-    matches the current sources."""
+# What the same captures show binding each pass (its busiest unit); reported
+# beside the FMA-rate fraction under the same source-hash condition as the
+# traffic.
+BINDING = {
+    "k_forces_mixed_x2": "L1 data path of the neighbour gathers: L1 throughput 81 %, issue "
+                         "58 %, FMA pipe 45 % (ncu, 2,525,900-particle cylinder); each pair is "
+                         "evaluated from both sides",
+    "k_density_mixed": "L1 data path of the offset gathers: L1 throughput 84 %, issue 57 %, "
+                       "FMA pipe 26 % (ncu, 2,525,900-particle cylinder)",
+    "k_forces_fp64": "FP64 pipe 89 % busy (ncu, 2,525,900-particle cylinder); each pair is "
+                     "evaluated from both sides",
+    "k_density_fp64": "FP64 pipe 85 % busy (ncu, 2,525,900-particle cylinder)",
+}
+
+
+def sources_match(kernel):
+    """The kernel's sources hash to the values recorded with its capture."""
     import hashlib
     per, srcs = DRAM_BYTES_PER_PARTICLE.get(kernel, (None, {}))
     if per is None:
-        return None
+        return False
     for f, h in srcs.items():
         path = os.path.join(ROOT, "paper_2405_03980_gb300", "csrc", f)
         if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
-            return None
-    return per * n_particles
+            return False
+    return True
+
+
+def measured_traffic(kernel, n_particles):
+    """Per-launch DRAM bytes of kernel at n_particles, or None when no capture
+    matches the current sources."""
+    if not sources_match(kernel):
+        return None
+    return DRAM_BYTES_PER_PARTICLE[kernel][0] * n_particles
 
 
 def pair_classes(census):
@@ -674,6 +696,7 @@ def run_ours(args, dist):
                 "traffic_ratio": ratio(tr, ALGO_BYTES_PER_PARTICLE[kern] * n_part),
                 "peak_source": src,
                 "work": f"{fpp:.2f} {u} flop x {units} {what} per launch",
+                "binding": BINDING.get(kern) if sources_match(kern) else None,
                 "launch_ms": results[f]["stages"][stage]}
     dom_stage = max(("forces", "density", "cell_search"), key=lambda k: st[k])
     roof = roofs[best][dom_stage]
