@@ -113,6 +113,31 @@ def test_mixed_pair_forces_are_antisymmetric():
     sim.close()
 
 
+def test_packed_and_scalar_pair_passes_agree():
+    """The default form's pair pass takes two neighbours per step in packed
+    FP32; with the collision model on, the one-neighbour loop runs instead.
+    A collision distance far below the particle spacing makes that term
+    vanish, so the two kernels compute the same forces on the same state and
+    must agree to FP32 rounding (they sum in different orders)."""
+    c = synth.workload("cyl_8960", seed=5)
+    c2 = synth.workload("cyl_8960", seed=5)
+    c2.params = dict(c2.params, col_dist=1e-3, col_e=0.5,
+                     flags=B.SPH_FLAGS_DEFAULT | B.SPH_COLLISION)
+    a, b = sim_of(c), sim_of(c2)
+    fl = c.species < 2
+    for steps in (0, 3):
+        if steps:
+            a.step(steps)
+            b.step(steps)
+        sa, sb = a.state_arrays(), b.state_arrays()
+        for k in ("acc", "dspin"):
+            e = rel_l2(sa[k][fl], sb[k][fl])
+            print(steps, k, "packed vs one-neighbour pair pass, relative L2", e)
+            assert e < (1e-6 if steps == 0 else 5e-6), (steps, k, e)
+    a.close()
+    b.close()
+
+
 def test_mixed_batch_equals_solo_bitwise():
     cs = [synth.cylinder(R=r, H=h, Omega=om, f_v=fv, seed=s)
           for r, h, om, fv, s in [(5.2, 10, 0.12, 0.3, 11), (3.4, 8, 0.2, 0.02, 12)]]
