@@ -211,7 +211,11 @@ SPH_API sph_status sph_forces(sph_ctx* ctx);
 
 /* Advance nsteps kick-drift-kick steps (Algorithm 1 inner body), each one
  * kick+drift, wall rotation, sph_build_cells, sph_density, sph_forces, kick.
- * The step is replayed from CUDA graphs captured on the first call. */
+ * The step is replayed from CUDA graphs captured on the first call.  (Mixed
+ * form: within one call each step's closing half kick runs inside the next
+ * step's drift, the last one at the end of the call, with the same bits as
+ * separate kicks: the state between calls is the same however nsteps is
+ * split.) */
 SPH_API sph_status sph_step(sph_ctx* ctx, int32_t nsteps);
 
 /* FP64 diagnostics of instance inst (synchronises). */
