@@ -827,14 +827,13 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
   const double yi = P.lo[1] + (double)cell_y(ci) * P.cell[1] + (double)oi.y;
   const double zi = fold_z(P, P.lo[2] + (double)cell_z(ci) * P.cell[2] + (double)oi.z);
   const float pxi = (float)xi, pyi = (float)yi, pzi = (float)zi;
-  // packed constants
-  const f2 OX = f2_splat(oi.x), OY = f2_splat(oi.y), OZ = f2_splat(oi.z);
+  // packed constants; the differences with i's own records are formed as two
+  // scalar operations each (the same roundings), which keeps those records
+  // out of packed registers and the kernel within its register bound
   const f2 LX = f2_splat(P.cellf[0]), LY = f2_splat(P.cellf[1]), LZ = f2_splat(P.cellf[2]);
-  const f2 VX = f2_splat(vi.x), VY = f2_splat(vi.y), VZ = f2_splat(vi.z);
-  const f2 VW = f2_splat(vi.w), WW = f2_splat(wi.w);
-  const f2 HX = f2_splat(0.5f * wi.x), HY = f2_splat(0.5f * wi.y), HZ = f2_splat(0.5f * wi.z);
-  const f2 HALF = f2_splat(0.5f), ONE = f2_splat(1.f), MAGIC = f2_splat(8388609.0f);
+  const f2 ONE = f2_splat(1.f), MAGIC = f2_splat(8388609.0f);
   const f2 NHIH = f2_splat(-0.5f * P.inv_h_f), TIH = f2_splat(2.f * P.inv_h_f);
+  const float hwx = 0.5f * wi.x, hwy = 0.5f * wi.y, hwz = 0.5f * wi.z;
   Kahan fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, tx{0.f, 0.f}, ty{0.f, 0.f}, tz{0.f, 0.f};
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const uint32_t cnt = checked_count(nw.count[i], nw.cap, err);
@@ -885,9 +884,9 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
                                    __int_as_float(0x4B000000 | ((cb >> 2) & 3u))), MAGIC);
       const f2 EZ = f2_sub(f2_make(__int_as_float(0x4B000000 | (ca >> 4)),
                                    __int_as_float(0x4B000000 | (cb >> 4))), MAGIC);
-      const f2 dX = f2_fma(EX, LX, f2_sub(OX, f2_make(oa.x, ob.x)));
-      const f2 dY = f2_fma(EY, LY, f2_sub(OY, f2_make(oa.y, ob.y)));
-      const f2 dZ = f2_fma(EZ, LZ, f2_sub(OZ, f2_make(oa.z, ob.z)));
+      const f2 dX = f2_fma(EX, LX, f2_make(oi.x - oa.x, oi.x - ob.x));
+      const f2 dY = f2_fma(EY, LY, f2_make(oi.y - oa.y, oi.y - ob.y));
+      const f2 dZ = f2_fma(EZ, LZ, f2_make(oi.z - oa.z, oi.z - ob.z));
       const f2 R2 = f2_fma(dZ, dZ, f2_fma(dY, dY, f2_mul(dX, dX)));
       float r2a, r2b;
       f2_split(R2, r2a, r2b);
@@ -897,17 +896,18 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
       const f2 R = f2_mul(f2_make(oka ? r2a : 1.f, okb ? r2b : 1.f), IR);
       const f2 IR2 = f2_mul(IR, IR);
       const f2 T1 = f2_fma(NHIH, R, ONE);  // 1 - q/2
+      const f2 Q2 = f2_fma(TIH, R, ONE);
       const f2 T2 = f2_mul(T1, T1);
       const f2 F = f2_mul(T2, T1);
-      const f2 W = f2_mul(f2_mul(T2, T2), f2_fma(TIH, R, ONE));
+      const f2 W = f2_mul(f2_mul(T2, T2), Q2);
       const bool visa = oa.w != 0.f, visb = ob.w != 0.f;
-      const f2 VV = f2_mul(VW, f2_make(va.w, vb.w));
-      const f2 vX = f2_sub(VX, f2_make(va.x, vb.x));
-      const f2 vY = f2_sub(VY, f2_make(va.y, vb.y));
-      const f2 vZ = f2_sub(VZ, f2_make(va.z, vb.z));
-      const f2 SX = f2_fma(HALF, f2_make(wa.x, wb.x), HX);
-      const f2 SY = f2_fma(HALF, f2_make(wa.y, wb.y), HY);
-      const f2 SZ = f2_fma(HALF, f2_make(wa.z, wb.z), HZ);
+      const f2 VV = f2_make(vi.w * va.w, vi.w * vb.w);
+      const f2 vX = f2_make(vi.x - va.x, vi.x - vb.x);
+      const f2 vY = f2_make(vi.y - va.y, vi.y - vb.y);
+      const f2 vZ = f2_make(vi.z - va.z, vi.z - vb.z);
+      const f2 SX = f2_make(fmaf(0.5f, wa.x, hwx), fmaf(0.5f, wb.x, hwx));
+      const f2 SY = f2_make(fmaf(0.5f, wa.y, hwy), fmaf(0.5f, wb.y, hwy));
+      const f2 SZ = f2_make(fmaf(0.5f, wa.z, hwz), fmaf(0.5f, wb.z, hwz));
       // u = v_ij + r_ij x s, each component one product added to the other's
       // negative (the sign of -(dz sy) taken from the product, exactly)
       const f2 uX = f2_fma(dY, SZ, f2_sub(vX, f2_mul(dZ, SY)));
@@ -916,7 +916,7 @@ k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ 
       const f2 DV = f2_fma(dZ, vZ, f2_fma(dY, vY, f2_mul(dX, vX)));
       const f2 VF = f2_mul(VV, F);
       const f2 aP = f2_mul(f2_make(visa ? cP1 : cP0, visb ? cP1 : cP0),
-                           f2_mul(f2_add(WW, f2_make(wa.w, wb.w)), F));
+                           f2_mul(f2_make(wi.w + wa.w, wi.w + wb.w), F));
       const f2 aT = f2_mul(f2_make(visa ? cT1 : cT0, visb ? cT1 : cT0), VF);
       const f2 aV = f2_mul(f2_mul(VF, IR2),
                            f2_mul(f2_make(visa ? cBA1 : 0.f, visb ? cBA1 : 0.f), DV));
