@@ -782,10 +782,9 @@ k_forces_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ ins
 // formed in an order independent of (i, j) as there, so f_ji == -f_ij bit
 // for bit.  A neighbour slot past the list's end, or a coincident particle
 // (r = 0: density only), is evaluated on stand-in values and masked out.
-// The packed form needs more registers (146); bounding them at 128 keeps 16
-// warps per SM, the residency of the scalar loop, at the cost of a few spilled
-// loop constants: 8.26 -> 7.59 ms at 20.1M (at 146 registers and 12 warps the
-// pass was latency-bound and took 8.35 ms).
+// The packed form wants more registers (140) than the scalar loop; bounding
+// them at 128 keeps the scalar loop's 16 warps per SM at the cost of a few
+// spilled loop constants (with 12 warps the pass waited on its gathers).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
 k_forces_mixed_x2(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
