@@ -1062,10 +1062,13 @@ cudaError_t launch_drift_mixed(int64_t n, const MixBuf& b, const MixFields& f,
   return cudaGetLastError();
 }
 
+// (The gated streaming kernels of the list build run on grids of 8 blocks
+// per SM, striding over the particles: a step that keeps its lists pays a
+// few microseconds for each instead of about twelve.)
 cudaError_t launch_keys_mixed(int64_t n, const MixBuf& b, const InstDev* inst,
                               const InstState* ist, const CellWs& cw, uint32_t* err, int mode,
                               cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  k_keys_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, b, inst, ist, cw, err, mode);
+  k_keys_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, b, inst, ist, cw, err, mode);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -1090,7 +1093,7 @@ cudaError_t launch_gate(bool open, int32_t n_inst, const InstDev* inst, InstStat
 cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
                                  const CellWs& cw, const uint32_t* gate, cudaStream_t s,
                                  const LaunchCfg& lc, int* launches) {
-  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, cw, gate);
+  k_reorder_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, cw, gate);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -1098,7 +1101,7 @@ cudaError_t launch_reorder_mixed(int64_t n, const MixBuf& src, const MixBuf& dst
 cudaError_t launch_copyback_mixed(int64_t n, const MixBuf& src, const MixBuf& dst,
                                   const MixFields& f, const InstState* ist, const uint32_t* gate,
                                   cudaStream_t s, const LaunchCfg& lc, int* launches) {
-  k_copyback_mixed<<<grid_for(n, 256, lc.sm_count, 32), 256, 0, s>>>(n, src, dst, f, ist, gate);
+  k_copyback_mixed<<<grid_for(n, 256, lc.sm_count, 8), 256, 0, s>>>(n, src, dst, f, ist, gate);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
