@@ -13,10 +13,12 @@
  * Arrays of vectors are xyz-interleaved (3n doubles).
  *
  * Parity status: every function below is pinned by tests/test_oracle_pins.py
- * (kernel normalisation by quadrature, lattice rest density, momentum and
- * angular-momentum conservation, rigid-rotation zero viscous force, continuum
- * limit of the viscous/spin terms, energy conservation, brute-force neighbour
- * sets against a k-d tree, time reversibility of the integrator).  The
+ * (kernel normalisation by quadrature, lattice rest density, also with
+ * unequal species masses, momentum and angular-momentum conservation,
+ * rigid-rotation zero viscous force, also next to the rotating walls,
+ * continuum limit of the viscous/spin terms, energy conservation, the
+ * diagnostics' energies against the momenta of uniform states, brute-force
+ * neighbour sets against a k-d tree, time reversibility of the integrator).  The
  * interfacial force is pinned in sign, projection, reaction and scale: on a
  * lattice split by a species interface its summed force per unit area is
  * the closed form of the kernel's second moment, -C_T/2 in the continuum.

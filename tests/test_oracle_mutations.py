@@ -46,6 +46,30 @@ MUTATIONS = {
     "collision_not_on_walls": ("+ f[4][0] + f[5][0],", "+ f[4][0],"),
     "unit_vector_index": ("double e[3] = {d[0] / r, d[1] / r, d[2] / r};",
                           "double e[3] = {d[0] / r, d[2] / r, d[1] / r};"),
+    "eos_exponent_off_by_one": ("pow(rho / p->rho0, p->alpha_P) - p->beta_P;",
+                                "pow(rho / p->rho0, p->alpha_P - 1) - p->beta_P;"),
+    "rot_drops_normal_projection": ("double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];",
+                                    "double eu = 0.0 * u[0];"),
+    "shear_kernel_not_gradient": ("double s = -A * Vi * Vj * F * ev;",
+                                  "double s = -A * Vi * Vj * W * ev;"),
+    "local_interaction_gradient": ("double s = -p->C_l * Vi * Vj * W;",
+                                   "double s = -p->C_l * Vi * Vj * F;"),
+    "torque_without_local_interaction": (
+        "fs[0] += f[4][0];\n        fs[1] += f[4][1];\n        fs[2] += f[4][2];",
+        "fs[0] += 0.0;\n        fs[1] += 0.0;\n        fs[2] += 0.0;"),
+    "kinetic_energy_factor": ("out->E_kin += 0.5 * m * v2;", "out->E_kin += m * v2;"),
+    "spin_energy_mass_for_inertia": ("out->E_rot += 0.5 * I *", "out->E_rot += 0.5 * m *"),
+    "spin_momentum_mass_for_inertia": ("out->L_spin[a] += I * w[a];",
+                                       "out->L_spin[a] += m * w[a];"),
+    "wall_spin_half_rate": ("spin[3 * i + 2] = p->Omega;", "spin[3 * i + 2] = 0.5 * p->Omega;"),
+    "mass_ratio_inverted": ("return species == 0 ? p->mass_ratio * mn : mn;",
+                            "return species == 0 ? mn / p->mass_ratio : mn;"),
+    "density_row_mass": (
+        "if (q2 < c2) r += (species[j] == 0 ? m_s : m_n) * orc_W(p, sqrt(q2));",
+        "if (q2 < c2) r += (species[i] == 0 ? m_s : m_n) * orc_W(p, sqrt(q2));"),
+    "pressure_volumes_for_masses": (
+        "double s = mi * mj * (Pri + P[j] / (rho[j] * rho[j])) * F;",
+        "double s = Vi * Vj * (Pri + P[j] / (rho[j] * rho[j])) * F;"),
 }
 
 

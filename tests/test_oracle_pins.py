@@ -86,6 +86,14 @@ def test_rest_density_on_unjittered_lattice():
     sp2 = np.zeros(len(pos), np.uint8)
     rho2, _ = oracle.density(p2, pos, sp2)
     assert rho2[interior] == pytest.approx(5.0 * rho[interior], rel=1e-14)
+    # one inviscid particle among viscous ones: its neighbours bring m_n each
+    # and only the self term carries m_s, so rho = rho0 + (m_s - m_n) W(0)
+    c = int(np.argmin((pos ** 2).sum(1)))
+    sp3 = np.ones(len(pos), np.uint8)
+    sp3[c] = 0
+    rho3, _ = oracle.density(p2, pos, sp3)
+    m_s, m_n = oracle.mass(p2, 0), oracle.mass(p2, 1)
+    assert rho3[c] == pytest.approx(1.0 + (m_s - m_n) * oracle.W(p2, 0.0), rel=1e-13)
 
 
 def test_neighbours_match_kdtree_with_periodic_z():
@@ -200,6 +208,60 @@ def test_angular_momentum_constant_over_kdk_steps():
     assert np.allclose(d1["mom"], d0["mom"], atol=1e-11)
     assert d1["mass"] == d0["mass"]
     assert d0["mass"] == pytest.approx(d0["mass_s"] + d0["mass_n"], rel=1e-15)
+
+
+def test_spin_energy_is_half_spin_times_spin_momentum():
+    """For one spin w0 shared by every fluid particle, E_rot = 1/2 sum I w0^2
+    and L_spin = sum I w0, so E_rot = 1/2 w0 . L_spin whatever the inertia;
+    likewise E_kin = 1/2 v0 . P for one velocity v0."""
+    c = synth.workload("cyl_8960")
+    p = oracle.make_params(dict(c.params, mass_ratio=3.0))
+    w0 = np.array([0.2, -0.1, 0.35])
+    v0 = np.array([0.05, 0.3, -0.2])
+    spin = np.tile(w0, (c.n, 1))
+    vel = np.tile(v0, (c.n, 1))
+    rho, _ = oracle.density(p, c.pos, c.species)
+    d = oracle.diagnostics(p, c.pos, vel, spin, c.species, rho)
+    assert d["E_rot"] == pytest.approx(0.5 * np.dot(w0, d["L_spin"]), rel=1e-12)
+    assert d["E_kin"] == pytest.approx(0.5 * np.dot(v0, d["mom"]), rel=1e-12)
+    assert d["E_rot"] > 0.0 and d["E_kin"] > 0.0
+
+
+def test_rigid_rotation_with_placed_walls_has_no_rotational_stress():
+    """The rotating walls move as a rigid body (Sec. 3): placed by the oracle at
+    any phase they carry v = Omega z x r and the spin Omega z, so a fluid in
+    rigid co-rotation next to them feels no shear, rotational or local
+    interaction force and no spin torque."""
+    c = synth.workload("cyl_8960")
+    Om = c.params["Omega"]
+    p = oracle.make_params(dict(c.params, C_l=2.0),
+                           flags=oracle.TERM_SH | oracle.TERM_ROT | oracle.TERM_SN)
+    pos = np.ascontiguousarray(c.pos.copy())
+    vel = np.ascontiguousarray(np.cross([0.0, 0.0, Om], pos))
+    spin = np.ascontiguousarray(np.tile([0.0, 0.0, Om], (c.n, 1)))
+    wall = c.species >= 2
+    vel[wall] = 0.0
+    spin[wall] = 0.0
+    oracle.place_walls(p, c.species, c.pos[:, :2], 0.7, pos, vel, spin)
+    # rotate the fluid by the same phase: the whole vessel is one rigid body
+    ct, st = math.cos(0.7), math.sin(0.7)
+    fl = ~wall
+    x, y = c.pos[fl, 0].copy(), c.pos[fl, 1].copy()
+    pos[fl, 0], pos[fl, 1] = ct * x - st * y, st * x + ct * y
+    vel[fl] = np.cross([0.0, 0.0, Om], pos[fl])
+    assert np.allclose(spin[wall], [0.0, 0.0, Om], rtol=0, atol=0)
+    rho, P = oracle.density(p, pos, c.species)
+    r_xy = np.hypot(pos[:, 0], pos[:, 1])
+    rows = np.nonzero(fl & (r_xy > r_xy[fl].max() - 2.6))[0]  # fluid next to the walls
+    acc, dsp, _ = oracle.forces(p, pos, vel, spin, c.species, rho, P, rows=rows)
+    # the same rows with the walls' spin dropped feel O(1) forces
+    spin2 = spin.copy()
+    spin2[wall] = 0.0
+    acc2, dsp2, _ = oracle.forces(p, pos, vel, spin2, c.species, rho, P, rows=rows)
+    ref = np.abs(acc2[rows]).max() + np.abs(dsp2[rows]).max()
+    assert ref > 1e-3
+    assert np.abs(acc[rows]).max() < 1e-9 * ref
+    assert np.abs(dsp[rows]).max() < 1e-9 * ref
 
 
 def test_rigid_rotation_has_no_viscous_or_local_force():
