@@ -70,6 +70,28 @@ MUTATIONS = {
     "pressure_volumes_for_masses": (
         "double s = mi * mj * (Pri + P[j] / (rho[j] * rho[j])) * F;",
         "double s = Vi * Vj * (Pri + P[j] / (rho[j] * rho[j])) * F;"),
+    "internal_energy_exponent": ("(pow(rho / p->rho0, a - 1.0) - 1.0)",
+                                 "(pow(rho / p->rho0, a) - 1.0)"),
+    "internal_energy_background_sign": ("p->beta_P * (1.0 / rho - 1.0 / p->rho0);",
+                                        "p->beta_P * (1.0 / p->rho0 - 1.0 / rho);"),
+    "orbital_momentum_order": ("cross(r, v, L);", "cross(v, r, L);"),
+    "momentum_without_mass": ("out->mom[a] += m * v[a];", "out->mom[a] += v[a];"),
+    "wall_impulse_one_sided": ("J_wall[a] += hdt * (T_old[a] + T_wall_sum[a]);",
+                               "J_wall[a] += p->dt * T_wall_sum[a];"),
+    "shear_sign": ("double s = -A * Vi * Vj * F * ev;", "double s = A * Vi * Vj * F * ev;"),
+    "rotational_sign": ("double s = -B * Vi * Vj * F;", "double s = B * Vi * Vj * F;"),
+    "spin_velocity_full_spin_sum": (
+        "{vij[0] + 0.5 * dxw[0], vij[1] + 0.5 * dxw[1], vij[2] + 0.5 * dxw[2]}",
+        "{vij[0] + dxw[0], vij[1] + dxw[1], vij[2] + dxw[2]}"),
+    "diag_inertia_without_dx2": ("double I = p->inertia_coef * m * p->dx * p->dx;",
+                                 "double I = p->inertia_coef * m * p->dx;"),
+    "torque_inertia_without_dx2": ("double Ii = p->inertia_coef * mi * p->dx * p->dx;",
+                                   "double Ii = p->inertia_coef * mi * p->dx;"),
+    "first_kick_full_step": (
+        "vel[3 * i + a] += hdt * acc[3 * i + a];\n"
+        "      spin[3 * i + a] += hdt * dspin[3 * i + a];\n      pos[3 * i + a]",
+        "vel[3 * i + a] += p->dt * acc[3 * i + a];\n"
+        "      spin[3 * i + a] += hdt * dspin[3 * i + a];\n      pos[3 * i + a]"),
 }
 
 

@@ -21,8 +21,8 @@ from paper_2405_03980_gb300 import synth
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _params(h_over_dx=1.3, periodic_z=1, Hz=20.0, **kw):
-    p = synth.workload_params(10.0, Hz, 0.1, h_over_dx=h_over_dx)
+def _params(h_over_dx=1.3, periodic_z=1, Hz=20.0, dx=1.0, **kw):
+    p = synth.workload_params(10.0, Hz, 0.1, dx=dx, h_over_dx=h_over_dx)
     p.update(periodic_z=periodic_z, box_lo=(-50.0, -50.0, 0.0), box_hi=(50.0, 50.0, Hz))
     p.update(kw)
     return p
@@ -193,10 +193,16 @@ def test_angular_momentum_orbital_plus_spin_free_cluster():
     assert np.abs(res[:2]).max() > 1e-6 * scale
 
 
-def test_angular_momentum_constant_over_kdk_steps():
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_angular_momentum_constant_over_kdk_steps(dx):
+    """Orbital plus spin momentum is constant over KDK steps; at dx != 1 the
+    spin inertia m dx^2 (a length squared, so the spin momentum is counted in
+    the same units as r x m v) must be the same in the torque update and in
+    the reported L_spin, or the sum drifts."""
     pos, vel, spin, sp = _block(5, 5, 5, seed=5)
-    pos = pos - pos.mean(0)
-    prm = _params(periodic_z=0, C_T=0.3, C_l=0.5, dt=0.01)
+    pos = (pos - pos.mean(0)) * dx
+    vel = vel * dx
+    prm = _params(periodic_z=0, C_T=0.3, C_l=0.5, dt=0.01, dx=dx)
     s = oracle.Sim(prm, pos, vel, spin, sp, flags=oracle.TERMS_ALL)
     d0 = s.diagnostics()
     L0 = np.add(d0["L_orb"], d0["L_spin"])
