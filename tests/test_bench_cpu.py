@@ -1,7 +1,7 @@
 """Host-side accounting of bench.py, checked by hand on small numbers: the
 unique-pair classes from the ordered census, the per-class flop counts, the
-step's lower bound, the CPU baseline's full-step estimate and the source-hash
-guard of the recorded DRAM traffic."""
+step's lower bound, the CPU baseline's full-step estimate, the source-hash
+guard of the recorded DRAM traffic and the end-to-end leg's job length."""
 import os
 import sys
 
@@ -73,3 +73,16 @@ def test_traffic_needs_matching_sources(monkeypatch):
             assert bench.measured_traffic(k, 2000) == pytest.approx(2 * bench.measured_traffic(k, 1000))
     assert bench.ratio(None, 5.0) is None
     assert bench.ratio(10.0, 5.0) == pytest.approx(2.0)
+
+
+def test_e2e_runs_the_workloads_whole_job():
+    # the 19.6M cylinder's job is 200 steps, the 2.4M cylinder's 1000
+    assert bench.e2e_steps("cyl_20100112", 20) == 200
+    assert bench.e2e_steps("cyl_2525900", 20) == 1000
+    # never fewer steps than the device-timed run, and an explicit count wins
+    assert bench.e2e_steps("cyl_20100112", 500) == 500
+    assert bench.e2e_steps("cyl_20100112", 20, override=7) == 7
+    # a workload without a stated job length runs the device-timed steps
+    assert bench.e2e_steps("paper_2534800", 20) == 20
+    for name in bench.JOB_STEPS:
+        assert name in synth.WORKLOADS or name.startswith("ensemble")
