@@ -445,6 +445,55 @@ k_skin_list_mixed(int64_t n, MixBuf b, const InstDev* __restrict__ inst,
 
 // -------------------------------------------------------------------- density
 
+// The list builder with a float per kept entry (the kernel shape the
+// pressure filter reads) staged beside it, with the entries' stride, and
+// written group by group to the same slots of wl as full sectors.
+struct ShapedListWriter : ListWriter {
+  float* wl;
+  float* sw;
+  __device__ __forceinline__ ShapedListWriter(const NbrWs& nw, int64_t n_, int64_t i_,
+                                              uint32_t* st_, float* sw_, uint32_t stride_)
+      : ListWriter(nw, n_, i_, st_, stride_), wl(nw.wsh_f), sw(sw_) {}
+  __device__ __forceinline__ void push(uint32_t e, float w) {
+    st[pend * stride] = e;
+    sw[pend * stride] = w;
+    ++pend;
+  }
+  __device__ __forceinline__ void write_group(uint32_t from) {
+    if (written < groups) {
+      const int64_t slot = nbr_slot(n, i, written << 3);
+      const float* r = sw + from * stride;
+      float4* dw = reinterpret_cast<float4*>(wl + slot);
+      dw[0] = make_float4(r[0], r[stride], r[2 * stride], r[3 * stride]);
+      dw[1] = make_float4(r[4 * stride], r[5 * stride], r[6 * stride], r[7 * stride]);
+    }
+    ListWriter::write_group(from);
+  }
+  __device__ __forceinline__ void drain() {
+    const uint32_t g = pend >> 3;
+    for (uint32_t k = 0; k < g; ++k) write_group(k << 3);
+    const uint32_t rem = pend & 7u;
+    for (uint32_t r = 0; r < rem; ++r) {
+      st[r * stride] = st[((g << 3) + r) * stride];
+      sw[r * stride] = sw[((g << 3) + r) * stride];
+    }
+    pend = rem;
+  }
+  __device__ __forceinline__ uint32_t finish() {
+    drain();
+    const uint32_t t = total();
+    if (pend) write_group(0);
+    return t < (groups << 3) ? t : (groups << 3);
+  }
+};
+
+template <bool kShaped>
+__device__ __forceinline__ auto make_writer(const NbrWs& nw, int64_t n, int64_t i, uint32_t* st,
+                                            float* sw, uint32_t stride) {
+  if constexpr (kShaped) return ShapedListWriter(nw, n, i, st, sw, stride);
+  else return ListWriter(nw, n, i, st, stride);
+}
+
 // r^2 of a pair vector with an explicit rounding sequence: the same bits as
 // the neighbour search's test, so that a list rebuilt every step (skin 0)
 // keeps exactly the search's neighbours.
@@ -459,12 +508,18 @@ __device__ __forceinline__ float pair_r2f(float dx, float dy, float dz) {
 // The list is read one 32-byte group of 8 entries at a time, and the 8
 // offset records are loaded together before the 8 pairs are tested.
 // kFilter: some instance uses the pressure filter; the kernel shape of every
-// list entry is then stored beside the list (nw.wsh_f) for the filter.
+// list entry is then stored beside the list (nw.wsh_f) for the filter, staged
+// with the entries and written with them as full sectors (drained at 16
+// entries, so that the two stagings take the shared memory of one).
 template <int BLOCK, bool kFilter>
 __global__ void __launch_bounds__(BLOCK)
 k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ inst, NbrWs nw,
                 uint32_t* err) {
-  __shared__ uint32_t stage[BLOCK * kStageWords];
+  constexpr int kDrain = kFilter ? 16 : kDrainAt;
+  constexpr int kWords = kFilter ? 24 : kStageWords;
+  static_assert(kWords >= kDrain - 1 + 8, "staging holds a drain's remainder and a batch");
+  __shared__ uint32_t stage[BLOCK * kWords];
+  __shared__ float wstage[kFilter ? BLOCK * kWords : 1];
   const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
   const InstDev& P = inst[b.inst[i]];
@@ -479,7 +534,8 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
     // delta = sum_j (m_j/rho0) W_ij + (m_i/rho0) W(0) - 1, Kahan-compensated,
     // starting from the self term minus one carried as a float pair
     Kahan acc{P.self_hi[si], -P.self_lo[si]};
-    ListWriter out(nw, n, i, stage + threadIdx.x, BLOCK);
+    using Writer = typename std::conditional<kFilter, ShapedListWriter, ListWriter>::type;
+    Writer out = make_writer<kFilter>(nw, n, i, stage + threadIdx.x, wstage + threadIdx.x, BLOCK);
     const float half_inv_h = 0.5f * P.inv_h_f, two_inv_h = 2.f * P.inv_h_f;
     const float mrD0 = P.mr_f[0] * P.aD_f, mrD1 = P.mr_f[1] * P.aD_f;
     const float cut2 = P.cut2_f;
@@ -501,7 +557,7 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
           entry_vec(P, e[u], oi, o[u], dx, dy, dz);
           const float r2 = pair_r2f(dx, dy, dz);
           const bool keep = r2 < cut2;
-          out.push(e[u], keep);
+          if constexpr (!kFilter) out.push(e[u], keep);
           if (keep) {
             // r = r2 / sqrt(r2) from the approximate reciprocal square root
             const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
@@ -510,14 +566,11 @@ k_density_mixed(int64_t n, MixBuf b, MixFields f, const InstDev* __restrict__ in
             const float t2 = t1 * t1;
             const float Wt = t2 * t2 * fmaf(two_inv_h, r, 1.f);
             acc.add((o[u].w == 0.f ? mrD0 : mrD1) * Wt);
-            if (kFilter) {  // the shape of this list entry, in the list's layout
-              const uint32_t t = out.total() - 1u;
-              if (t < (uint32_t)nw.cap) nw.wsh_f[nbr_slot(n, i, t)] = Wt;
-            }
+            if constexpr (kFilter) out.push(e[u], Wt);  // with the shape of this entry
           }
         }
       }
-      if (out.pend >= (uint32_t)kDrainAt) out.drain();
+      if (out.pend >= (uint32_t)kDrain) out.drain();
     }
     cnt = out.finish();
     if (out.overflow()) latch(err, ERR_NEIGHBORS);
