@@ -125,10 +125,10 @@ DRAM_BYTES_PER_PARTICLE = {
     "k_cell_search<true>": (222.4, {"sph_search.cu": "cf8572358b743c10",
                                     "sph_internal.h": "1756e1381f18b6ad"}),
     "k_cell_search<false>": (None, {}),
-    "k_density_mixed": (770.2, {"sph_mixed.cu": "a759cb071911e683",
+    "k_density_mixed": (769.9, {"sph_mixed.cu": "701e6e1044459c54",
                                 "sph_internal.h": "1756e1381f18b6ad"}),
     "k_forces_mixed": (None, {}),
-    "k_forces_mixed_x2": (417.0, {"sph_mixed.cu": "a759cb071911e683",
+    "k_forces_mixed_x2": (416.8, {"sph_mixed.cu": "701e6e1044459c54",
                                   "sph_internal.h": "1756e1381f18b6ad"}),
     "k_density_fp64": (646.8, {"sph_fp64.cu": "2b1a99c0f5cfa53b",
                                "sph_internal.h": "1756e1381f18b6ad"}),
