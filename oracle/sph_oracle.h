@@ -14,7 +14,9 @@
  *
  * Parity status: every function below is pinned by tests/test_oracle_pins.py
  * (kernel normalisation by quadrature, lattice rest density, also with
- * unequal species masses, momentum and angular-momentum conservation,
+ * unequal species masses, momentum and angular-momentum conservation
+ * (also at a lattice spacing other than 1, which fixes the dx^2 of the spin
+ * inertia in both the torque update and the diagnostics),
  * rigid-rotation zero viscous force, also next to the rotating walls,
  * continuum limit of the viscous/spin terms, energy conservation, the
  * diagnostics' energies against the momenta of uniform states, brute-force
