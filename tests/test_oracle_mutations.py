@@ -4,6 +4,7 @@ fails against the broken copy."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -92,23 +93,61 @@ MUTATIONS = {
         "      spin[3 * i + a] += hdt * dspin[3 * i + a];\n      pos[3 * i + a]",
         "vel[3 * i + a] += p->dt * acc[3 * i + a];\n"
         "      spin[3 * i + a] += hdt * dspin[3 * i + a];\n      pos[3 * i + a]"),
+    "wall_velocity_reversed": (
+        "vel[3 * i] = -p->Omega * y;\n    vel[3 * i + 1] = p->Omega * x;",
+        "vel[3 * i] = p->Omega * y;\n    vel[3 * i + 1] = -p->Omega * x;"),
+    "wall_phase_half_rate": ("*theta += p->Omega * p->dt;", "*theta += 0.5 * p->Omega * p->dt;"),
+    "no_periodic_wrap_in_drift": ("if (pos[3 * i + 2] >= p->Hz) pos[3 * i + 2] -= p->Hz;",
+                                  "if (0) pos[3 * i + 2] -= p->Hz;"),
+    "wall_ignores_reference_z": ("pos[3 * i + 2] = wall_ref[3 * i + 2];", "pos[3 * i + 2] = 0.0;"),
+    "collision_dt_multiplied": ("* ev / p->dt;", "* ev * p->dt;"),
+    "pair_delta_reversed": ("d[0] = ri[0] - rj[0];", "d[0] = rj[0] - ri[0];"),
+    "wall_neighbour_inviscid_mass_forces": ("double mj = species[j] == 0 ? m_s : m_n;",
+                                            "double mj = species[j] != 1 ? m_s : m_n;"),
+    "wall_neighbour_inviscid_mass_density": (
+        "if (q2 < c2) r += (species[j] == 0 ? m_s : m_n) * orc_W(p, sqrt(q2));",
+        "if (q2 < c2) r += (species[j] != 1 ? m_s : m_n) * orc_W(p, sqrt(q2));"),
+    "wall_neighbour_inviscid_volume_filter": ("double Vj = (species[j] == 0 ? m_s : m_n) / rho[j];",
+                                              "double Vj = (species[j] != 1 ? m_s : m_n) / rho[j];"),
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutant(base, src, hdr, name):
+    """Build the oracle with one planted mistake and run the pins against it:
+    (pytest's return code, the end of its output)."""
     old, new = MUTATIONS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, name
-    mutated = tmp_path / "sph_oracle.c"
-    mutated.write_text(src.replace(old, new))
-    hdr = os.path.join(ROOT, "oracle", "sph_oracle.h")
-    (tmp_path / "sph_oracle.h").write_text(open(hdr).read())
-    so = tmp_path / "liborc_mut.so"
+    d = base / name
+    d.mkdir()
+    (d / "sph_oracle.c").write_text(src.replace(old, new))
+    (d / "sph_oracle.h").write_text(hdr)
+    so = d / "liborc_mut.so"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-                    "-ffp-contract=off", "-o", str(so), str(mutated), "-lm"], check=True)
+                    "-ffp-contract=off", "-o", str(so), str(d / "sph_oracle.c"), "-lm"],
+                   check=True)
     env = dict(os.environ, SPH_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 1, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutant built and run once, several at a time (two OpenMP threads
+    each), so that the whole list costs about one pin run per pair of cores."""
+    base = tmp_path_factory.mktemp("mutants")
+    src = open(SRC).read()
+    hdr = open(os.path.join(ROOT, "oracle", "sph_oracle.h")).read()
+    names = [k for k in sorted(MUTATIONS) if src.count(MUTATIONS[k][0]) == 1]
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(workers) as ex:
+        res = list(ex.map(lambda k: _run_mutant(base, src, hdr, k), names))
+    return dict(zip(names, res))
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, outcomes):
+    old, _ = MUTATIONS[name]
+    assert open(SRC).read().count(old) == 1, name
+    rc, out = outcomes[name]
+    assert rc == 1, f"mutation {name} survived the pins:\n{out}"

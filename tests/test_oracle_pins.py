@@ -94,6 +94,15 @@ def test_rest_density_on_unjittered_lattice():
     rho3, _ = oracle.density(p2, pos, sp3)
     m_s, m_n = oracle.mass(p2, 0), oracle.mass(p2, 1)
     assert rho3[c] == pytest.approx(1.0 + (m_s - m_n) * oracle.W(p2, 0.0), rel=1e-13)
+    # walls are particles of the normal fluid (Sec. 3): as neighbours, inner
+    # and outer walls alike bring m_n, and a lattice of inner walls alone sits
+    # at rho0 whatever the species mass ratio
+    sp4 = np.where(np.arange(len(pos)) % 2 == 0, 2, 3).astype(np.uint8)
+    sp4[c] = 0
+    rho4, _ = oracle.density(p2, pos, sp4)
+    assert rho4[c] == pytest.approx(1.0 + (m_s - m_n) * oracle.W(p2, 0.0), rel=1e-13)
+    rho5, _ = oracle.density(p2, pos, np.full(len(pos), 2, np.uint8))
+    assert np.allclose(rho5[interior], 1.0, rtol=0, atol=4e-15)
 
 
 def test_neighbours_match_kdtree_with_periodic_z():
@@ -214,6 +223,50 @@ def test_angular_momentum_constant_over_kdk_steps(dx):
     assert np.allclose(d1["mom"], d0["mom"], atol=1e-11)
     assert d1["mass"] == d0["mass"]
     assert d0["mass"] == pytest.approx(d0["mass_s"] + d0["mass_n"], rel=1e-15)
+
+
+def test_walls_act_on_the_fluid_as_viscous_particles():
+    """Walls are particles of the normal fluid (Sec. 3): on a fluid particle a
+    wall neighbour acts as a viscous particle with the same position,
+    velocity, spin, density and pressure would, in every pair term, also at
+    unequal species masses."""
+    c = synth.workload("cyl_8960")
+    p = oracle.make_params(dict(c.params, mass_ratio=3.0, C_T=0.3, C_l=0.5))
+    rng = np.random.Generator(np.random.PCG64(21))
+    spin = c.spin + rng.normal(0.0, 0.05, size=c.spin.shape)
+    rho, P = oracle.density(p, c.pos, c.species)
+    fluid = np.nonzero(c.species < 2)[0]
+    acc, dsp, _ = oracle.forces(p, c.pos, c.vel, spin, c.species, rho, P, rows=fluid)
+    as_viscous = np.where(c.species >= 2, 1, c.species).astype(np.uint8)
+    acc2, dsp2, _ = oracle.forces(p, c.pos, c.vel, spin, as_viscous, rho, P, rows=fluid)
+    # a good share of the fluid rows has wall neighbours
+    assert (np.hypot(c.pos[fluid, 0], c.pos[fluid, 1]) > c.R - 2.0 * p.h).sum() > 1000
+    assert np.allclose(acc2[fluid], acc[fluid], rtol=1e-13, atol=1e-13 * np.abs(acc).max())
+    assert np.allclose(dsp2[fluid], dsp[fluid], rtol=1e-13, atol=1e-13 * np.abs(dsp).max())
+    # likewise in the pressure filter's weights (outer walls stay out of it)
+    Pn = P + rng.normal(0.0, 0.1 * p.p0, size=P.shape)
+    Pf = oracle.pressure_filter(p, c.pos, c.species, rho, Pn, rows=fluid)
+    inner_as_viscous = np.where(c.species == 2, 1, c.species).astype(np.uint8)
+    Pf2 = oracle.pressure_filter(p, c.pos, inner_as_viscous, rho, Pn, rows=fluid)
+    assert np.allclose(Pf2[fluid], Pf[fluid], rtol=1e-13, atol=1e-13 * p.p0)
+    assert not np.allclose(Pf[fluid], Pn[fluid])
+
+
+def test_drift_keeps_positions_in_the_z_period():
+    """z is periodic (the slip top and bottom of Sec. 3): a particle that
+    drifts across z = H re-enters at z = 0, so the state stays in [0, H)."""
+    Hz = 4.0
+    pos, vel, spin, sp = _block(4, 4, 4, seed=7)
+    vel[:, 2] += 3.0  # 0.15 per step: most particles cross z = H in 10 steps
+    prm = _params(Hz=Hz, periodic_z=1, dt=0.05)
+    s = oracle.Sim(prm, pos, vel, spin, sp, flags=oracle.TERMS_ALL)
+    s.step(10)
+    assert np.all((s.pos[:, 2] >= 0.0) & (s.pos[:, 2] < Hz))
+    # the particles whose free flight ends well past z = H (a quarter of them)
+    # are found near the bottom of the period
+    crossed = pos[:, 2] + 10 * 0.05 * vel[:, 2] >= Hz + 0.25
+    assert crossed.sum() >= len(pos) // 4
+    assert np.all(s.pos[crossed, 2] < 2.0)
 
 
 def test_spin_energy_is_half_spin_times_spin_momentum():
