@@ -109,6 +109,18 @@ MUTATIONS = {
         "if (q2 < c2) r += (species[j] != 1 ? m_s : m_n) * orc_W(p, sqrt(q2));"),
     "wall_neighbour_inviscid_volume_filter": ("double Vj = (species[j] == 0 ? m_s : m_n) / rho[j];",
                                               "double Vj = (species[j] != 1 ? m_s : m_n) / rho[j];"),
+    "alpha_D_2d_constant": ("return 21.0 / (16.0 * ORC_PI * p->h * p->h * p->h);",
+                            "return 7.0 / (4.0 * ORC_PI * p->h * p->h);"),
+    "W_missing_2q_term": ("return alpha_D(p) * t2 * t2 * (2.0 * q + 1.0);",
+                          "return alpha_D(p) * t2 * t2 * (q + 1.0);"),
+    "F_t_squared": ("return 5.0 * alpha_D(p) * t * t * t / (p->h * p->h);",
+                    "return 5.0 * alpha_D(p) * t * t / (p->h * p->h);"),
+    "F_over_h_not_h2": ("return 5.0 * alpha_D(p) * t * t * t / (p->h * p->h);",
+                        "return 5.0 * alpha_D(p) * t * t * t / p->h;"),
+    "torque_y_full": ("t[1] *= -0.5;", "t[1] *= -1.0;"),
+    "lattice_sum_short": ("int m = (int)ceil(2.0 * p->h / p->dx) + 1;",
+                          "int m = (int)floor(2.0 * p->h / p->dx) - 1;"),
+    "min_image_half_period_wrong": ("double half = 0.5 * p->Hz;", "double half = p->Hz;"),
 }
 
 
